@@ -1,0 +1,84 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the tests.
+
+This module holds no step of the solver: it only draws the initial distributions and
+wall data of the workloads below from numpy's seeded generator. Both the CUDA path and
+the oracle receive the identical arrays.
+
+Initial state: the continuum Maxwellian rho/(2 pi T)^{3/2} exp(-|v|^2/(2T)) sampled at
+the velocity nodes v = (i - N/2 + 1) 2L/N, multiplied by (1 + a U[-1, 1]) per (cell, node),
+with rho = 1, zero velocity and amplitude a = 1e-3.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MAXWELL_B0 = 1.0 / (4.0 * np.pi)
+
+
+def _nodes(N: int, L: float) -> np.ndarray:
+    return (np.arange(N) - N // 2 + 1) * (2.0 * L / N)
+
+
+def sampled_maxwellian(N: int, L: float, rho: float = 1.0, u=(0.0, 0.0, 0.0), T: float = 1.0) -> np.ndarray:
+    """Continuum Maxwellian sampled at the velocity nodes, shape (N, N, N)."""
+    v = _nodes(N, L)
+    d1 = (v - u[0])[:, None, None]
+    d2 = (v - u[1])[None, :, None]
+    d3 = (v - u[2])[None, None, :]
+    return rho / (2.0 * np.pi * T) ** 1.5 * np.exp(-(d1 * d1 + d2 * d2 + d3 * d3) / (2.0 * T))
+
+
+def initial_state(J: int, N: int, L: float, T: float = 1.5, rho: float = 1.0, noise: float = 1e-3,
+                  seed: int = 0) -> np.ndarray:
+    """f0[j] = M(rho, 0, T) (1 + noise U[-1, 1]), shape (J, N, N, N), float64."""
+    rng = np.random.default_rng(seed)
+    M = sampled_maxwellian(N, L, rho, (0.0, 0.0, 0.0), T)
+    u = rng.uniform(-1.0, 1.0, size=(J, N, N, N))
+    return np.ascontiguousarray(M[None] * (1.0 + noise * u))
+
+
+@dataclass
+class Workload:
+    """A 1-D planar heat-transfer problem between diffuse walls."""
+
+    name: str
+    J: int
+    N: int
+    L: float
+    eps: float
+    T_left: float
+    T_right: float
+    x_lo: float = 0.0
+    x_hi: float = 1.0
+    b0: float = MAXWELL_B0
+    T_init: float = 1.5
+    seed: int = 0
+    iterations: int = 0        # fixed SGS iteration count (0: run to tolerance)
+    tol: float = 1e-8
+    precision: str = "fp64"
+
+    @property
+    def total_mass(self) -> float:
+        # noise-free initial density 1 times the domain length
+        return 1.0 * (self.x_hi - self.x_lo)
+
+    def initial_state(self) -> np.ndarray:
+        return initial_state(self.J, self.N, self.L, T=self.T_init, seed=self.seed)
+
+
+def heat_16cells_16v() -> Workload:
+    """16 cells on [0, 1], 16^3 velocities on [-6, 6]^3, eps = 1, walls T = 1 and 2, 20 SGS iterations."""
+    return Workload("heat1d_J16_N16_eps1", J=16, N=16, L=6.0, eps=1.0, T_left=1.0, T_right=2.0, T_init=1.5,
+                    iterations=20)
+
+
+def heat_64cells_32v(seed: int = 0) -> Workload:
+    """64 cells on [0, 1], 32^3 velocities on [-8, 8]^3, eps = 0.01, seeded wall temperatures
+    T_L ~ U[0.8, 1.2], T_R ~ U[1.5, 2.5]; initial temperature (T_L + T_R)/2; to residual 1e-8."""
+    rng = np.random.default_rng(seed)
+    TL = float(rng.uniform(0.8, 1.2))
+    TR = float(rng.uniform(1.5, 2.5))
+    return Workload("heat1d_J64_N32_eps0.01", J=64, N=32, L=8.0, eps=0.01, T_left=TL, T_right=TR,
+                    T_init=0.5 * (TL + TR), seed=seed, tol=1e-8)
