@@ -1,0 +1,168 @@
+/*
+ * sgs.h - C ABI of the GB300 (sm_103a) SGS-PFP solver for the steady Boltzmann equation
+ *
+ *     v . grad_x f = Q[f, f] / eps                                   (eq. (1))
+ *
+ * discretised by first-order upwind finite volumes in x (eqs. (7)-(11), slopes s = 0),
+ * a periodic velocity grid with N^3 points on [-L, L]^3 and the Fourier spectral
+ * collision operator in its steady-state-preserving form (eq. (16)), and solved by
+ * symmetric Gauss-Seidel sweeps (eq. (29)) whose per-cell problem (eq. (20)) is solved by
+ * the fixed-point iteration preconditioned with its small-eps limit (eqs. (24)-(26)),
+ * optionally inside nonlinear multigrid V-cycles (eq. (30)).
+ *
+ * Conventions shared by every call
+ *   - Velocity index i in [0, N): v = (i - N/2 + 1) * 2L/N; a cell's distribution is
+ *     N^3 contiguous doubles [i1][i2][i3] (i3 fastest); v1 is the x-direction velocity.
+ *   - A field (f, Q, P, rhs) holds all instances: instance q's cells start at the element
+ *     offset given by sgs_layout(), cells contiguous, each N^3 doubles.
+ *   - Every pointer named "device" is CUDA device memory owned by the caller, 16-byte
+ *     aligned, never freed or retained by the library beyond the call (the workspace
+ *     excepted: it stays bound until sgs_destroy). Storage is FP64 in every precision mode.
+ *   - Every compute call is asynchronous on the given cudaStream_t (passed as void*, NULL =
+ *     legacy default stream) and enqueues kernels only: no allocation, no host sync. Such
+ *     calls may be captured in a CUDA graph.
+ *   - Return value: SGS_OK (0) or a negative SGS_ERR_* detected on the host before anything
+ *     is enqueued. Conditions found on the device (Newton failure, inner cap, non-finite
+ *     values, wait timeout) set bits of a per-instance status word read by
+ *     sgs_read_status(). No call traps or aborts.
+ */
+#ifndef SGS_H
+#define SGS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGS_OK 0
+#define SGS_ERR_ARG (-1)         /* invalid argument or problem description */
+#define SGS_ERR_UNSUPPORTED (-2) /* valid but not implemented (e.g. 2-D space) */
+#define SGS_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define SGS_ERR_WORKSPACE (-4)   /* no or too small workspace bound */
+#define SGS_ERR_NOMEM (-5)       /* host allocation failed */
+
+/* Device status bits (per instance, OR-ed). */
+#define SGS_ST_NEWTON_FAIL 1u       /* a discrete-Maxwellian Newton solve did not converge */
+#define SGS_ST_INNER_CAP 2u         /* a cell solve stopped at inner_max */
+#define SGS_ST_NONPOSITIVE 4u       /* density or temperature <= 0 met in a cell */
+#define SGS_ST_NONFINITE 8u         /* NaN/Inf met */
+#define SGS_ST_TIMEOUT 16u          /* a bounded device wait gave up */
+
+enum sgs_collision { SGS_MAXWELL = 0, SGS_HARD_SPHERE = 1, SGS_BGK = 2 };
+enum sgs_bc_kind { SGS_DIFFUSE = 0, SGS_INFLOW = 1 };
+enum sgs_precision { SGS_FP64 = 0, SGS_FP32 = 1 };
+enum sgs_inner_method { SGS_PFP = 0, SGS_FP = 1 };
+
+/* Boundary data of one side: a diffuse wall at temperature T moving with tangential
+ * velocity u (eq. (31)), or an inflow Maxwellian (rho, u, T) for incoming velocities. */
+typedef struct {
+  int kind;
+  double rho;
+  double u[3];
+  double T;
+} sgs_bc;
+
+/* One steady problem instance (1-D space, 3-D velocity). */
+typedef struct {
+  int space_dim;      /* must be 1 */
+  int nx;             /* cells, >= 1 */
+  double x_lo, x_hi;  /* domain */
+  int nv;             /* N: velocity points per dimension, one of 8, 12, 16, 20, 24, 28, 32 */
+  double v_max;       /* L; the support radius is R = 2L / (3 sqrt 2 + 1) (Section 4.2) */
+  int collision;      /* SGS_MAXWELL (B = b0), SGS_HARD_SPHERE (B = b0 |q|), SGS_BGK (P = 0) */
+  double b0;          /* kernel constant; 1/(4 pi) gives nu = rho for Maxwell molecules */
+  double eps;         /* Knudsen number, > 0 */
+  sgs_bc bc[2];       /* bc[0] at x_lo, bc[1] at x_hi */
+  double total_mass;  /* C of eq. (32); <= 0 disables the rescale */
+  int precision;      /* arithmetic of the collision sum: SGS_FP64 or SGS_FP32 */
+  double inner_tol;   /* cell-equation residual tolerance (discrete L2 norm), e.g. 1e-8 */
+  int inner_max;      /* cap on PFP/FP updates per cell visit, e.g. 200 */
+  int inner_fixed;    /* > 0: exactly this many updates per visit (no tolerance test) */
+  double newton_tol;  /* exponent-change tolerance of the Maxwellian Newton, e.g. 1e-10 */
+  int newton_max;     /* e.g. 50 */
+  int inner_method;   /* SGS_PFP (eqs. (24)-(25)) or SGS_FP (eq. (22)) */
+} sgs_problem;
+
+/* Counters accumulated on the device since setup or the last sgs_reset_stats(). */
+typedef struct {
+  unsigned int status;          /* OR of every instance's status bits */
+  unsigned long long visits;    /* cell visits (cell updates) */
+  unsigned long long inner_iters;
+  unsigned long long newton_iters;
+  unsigned long long newton_solves;
+  unsigned long long fallbacks; /* step 1 skipped (existence test, eq. (26), or Newton failure) */
+} sgs_stats;
+
+typedef struct sgs_handle sgs_handle;
+
+/* Validates n_inst problems (all with the same nv and precision), builds the velocity
+ * grid, the Fourier weights G (closed form of the radial integral) and the per-step weight
+ * blocks on the host, and reports the device workspace size the caller must allocate and
+ * bind. No device memory is allocated here. */
+int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t* workspace_bytes);
+
+/* Binds a caller-owned device buffer of at least workspace_bytes (256-byte aligned) and
+ * uploads the tables (synchronous). Must precede every compute call. */
+int sgs_bind_workspace(sgs_handle* h, void* device_ptr, size_t bytes);
+
+/* Element offset of instance inst's first cell in every field, its cell count and N. */
+int sgs_layout(const sgs_handle* h, int inst, size_t* f_offset, int* n_cells, int* nv);
+/* Total elements of one field (all instances). */
+size_t sgs_field_elems(const sgs_handle* h);
+
+/* Collision step for every cell (eqs. (16), (28)):
+ *   moments and discrete Maxwellian M (eqs. (13)-(14)), Q = Q^FSM[f,f] - Q^FSM[M,M]
+ *   computed as the single symmetric bilinear sum Q_s(f - M, f + M), and
+ *   P = Q - nu (M - f). f, Q (device, nullable), P (device, nullable). */
+int sgs_collide(sgs_handle* h, const double* f, double* Q, double* P, void* stream);
+
+/* One SGS scan (eq. (29)) over every instance, forward (x_lo -> x_hi) or backward, in a
+ * single persistent launch (one thread-block cluster per instance, no host round trip).
+ * f (device) is updated in place; P (device) from the preceding sgs_collide; rhs (device,
+ * nullable) is the b of R(f) = b (multigrid / defect correction). */
+int sgs_sweep_forward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream);
+int sgs_sweep_backward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream);
+
+/* Uniform rescale of each instance to its total mass (eq. (32)); no-op where <= 0. */
+int sgs_rescale(sgs_handle* h, double* f, void* stream);
+
+/* Outer residual R = T(f) - Q/eps - rhs (Section 4 stopping rule), res[q] (device,
+ * n_inst doubles) = sqrt(dx sum_j sum_k w R^2) per instance. Q from sgs_collide(f). */
+int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, void* stream);
+
+/* Collision step in a chosen arithmetic (SGS_FP32 needs a handle set up with precision
+ * SGS_FP32, whose workspace then carries both weight tables). Same fields as sgs_collide. */
+int sgs_collide_prec(sgs_handle* h, const double* f, double* Q, double* P, int precision, void* stream);
+
+/* One full SGS iteration (eq. (29)): [collide], forward scan, collide, backward scan,
+ * rescale. Q and P are caller-owned device fields.
+ *   flags & SGS_IT_P_VALID: P already holds P[f] of the incoming f (skips the first collide).
+ *   flags & SGS_IT_EVAL:    afterwards Q, P hold Q[f], P[f] of the new f and, when res
+ *                           (device, n_inst doubles) is not NULL, res the outer residual.
+ * With both flags set, consecutive calls cost two collision evaluations per iteration. */
+#define SGS_IT_P_VALID 1
+#define SGS_IT_EVAL 2
+int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, int flags, double* res, void* stream);
+
+/* One FAS V-cycle (eq. (30)) on every instance: levels >= 2 grids with H = 2h (each level's
+ * cell count must be even), pre/post SGS smoothing iterations, coarse_iters iterations on
+ * the coarsest grid. Coarse fields live in the workspace. */
+int sgs_vcycle(sgs_handle* h, double* f, int levels, int pre, int post, int coarse_iters, void* stream);
+
+/* Synchronises the stream and reads the accumulated status and counters. */
+int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream);
+int sgs_reset_stats(sgs_handle* h, void* stream);
+
+void sgs_destroy(sgs_handle* h);
+const char* sgs_strerror(int code);
+
+/* Host-only helper (no GPU needed): the Fourier weight G(a, b) of the collision integral
+ * for integer squared norms a2 = a^2, b2 = b^2, as tabulated by sgs_setup from its closed
+ * form (Section 2.2, Fourier spectral method; weight conventions as in sgs_collide). */
+double sgs_host_weight(int nv, double v_max, int collision, double b0, long long a2, long long b2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGS_H */

@@ -1,0 +1,190 @@
+// Outer residual (Section 4 stopping rule), mass rescale (eq. (32)) and the multigrid
+// transfer operators (eq. (30)). All reductions are fixed-order (per-cell partials, then a
+// per-instance sum in cell order) so results are run-to-run deterministic.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sgs {
+
+// Block sum of one double; result valid in thread 0.
+__device__ inline double block_sum(double x, double* sh /*[32]*/) {
+  double v[1] = {x};
+  warp_allsum<1>(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v[0];
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[k];
+  __syncthreads();
+  return t;
+}
+
+// Outgoing mass flux of each wall: side 0 sums w v1 f_0 over v1 < 0, side 1 sums w v1
+// f_{J-1} over v1 > 0. flux[2 q + side].
+__global__ void __launch_bounds__(256) k_wall_flux(const InstDev* inst, const double* __restrict__ f, int N,
+                                                    double dv, double* flux) {
+  __shared__ double sh[32];
+  int q = blockIdx.x >> 1, side = blockIdx.x & 1;
+  const InstDev& I = inst[q];
+  int K = N * N * N;
+  const double* fa = f + I.f_off + (long long)(side ? I.J - 1 : 0) * K;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    double v1 = node(e / (N * N), N, dv);
+    if ((side == 0 && v1 < 0.0) || (side == 1 && v1 > 0.0)) acc += v1 * fa[e];
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) flux[blockIdx.x] = dv * dv * dv * t;
+}
+
+// Per-cell sum of w R^2, R = (v1^+ (f_j - f_{j-1}) + v1^- (f_{j+1} - f_j))/dx - Q_j/eps - b_j,
+// with wall ghosts rho_w * Mhat built from the same f. Optionally stores R.
+__global__ void __launch_bounds__(256) k_residual_cells(AuxArgs a, const double* __restrict__ f,
+                                                         const double* __restrict__ Q, const double* __restrict__ rhs,
+                                                         const double* flux, double* part, double* Rout) {
+  __shared__ double sh[32];
+  int c = blockIdx.x;
+  int q = a.cell_inst[c];
+  const InstDev& I = a.inst[q];
+  int N = a.N, K = N * N * N;
+  long long base = a.cell_off[c];
+  int j = (int)((base - I.f_off) / K);
+  double w = a.dv * a.dv * a.dv;
+  double inv_dx = 1.0 / I.dx, inv_eps = 1.0 / I.eps;
+  double rho_l = I.bc_kind[0] == SGS_INFLOW ? I.bc_rho[0] : -flux[2 * q] / I.wall_denom[0];
+  double rho_r = I.bc_kind[1] == SGS_INFLOW ? I.bc_rho[1] : -flux[2 * q + 1] / I.wall_denom[1];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    int i1 = e / (N * N), i2 = (e / N) % N, i3 = e % N;
+    double v1 = node(i1, N, a.dv);
+    double fj = f[base + e];
+    double fl = j == 0 ? rho_l * I.wall[0][0][i1] * I.wall[0][1][i2] * I.wall[0][2][i3] : f[base - K + e];
+    double fr = j == I.J - 1 ? rho_r * I.wall[1][0][i1] * I.wall[1][1][i2] * I.wall[1][2][i3] : f[base + K + e];
+    double R = (fmax(v1, 0.0) * (fj - fl) + fmin(v1, 0.0) * (fr - fj)) * inv_dx - Q[base + e] * inv_eps;
+    if (rhs) R -= rhs[base + e];
+    if (Rout) Rout[base + e] = R;
+    acc += R * R;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[c] = w * t;
+}
+
+__global__ void k_residual_final(const InstDev* inst, int n_inst, const double* part, double* res) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_inst) return;
+  const InstDev& I = inst[q];
+  double s = 0.0;
+  for (int j = 0; j < I.J; j++) s += part[I.cell0 + j];
+  res[q] = sqrt(I.dx * s);
+}
+
+cudaError_t launch_residual_impl(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
+                                 double* R, cudaStream_t st) {
+  double* flux = a.scratch;                  // [2 n_inst]
+  double* part = a.scratch + 2 * a.n_inst;   // [C]
+  k_wall_flux<<<2 * a.n_inst, 256, 0, st>>>(a.inst, f, a.N, a.dv, flux);
+  k_residual_cells<<<a.C, 256, 0, st>>>(a, f, Q, rhs, flux, part, R);
+  if (res) k_residual_final<<<(a.n_inst + 127) / 128, 128, 0, st>>>(a.inst, a.n_inst, part, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
+                            cudaStream_t st) {
+  return launch_residual_impl(a, f, Q, rhs, res, nullptr, st);
+}
+
+cudaError_t launch_residual_field(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* R,
+                                  cudaStream_t st) {
+  return launch_residual_impl(a, f, Q, rhs, nullptr, R, st);
+}
+
+// ---------------------------------------------------------------------------------------
+// Mass rescale: mass[c] = w sum f, then f *= C / (dx sum_j mass[j]) per instance.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_cell_mass(AuxArgs a, const double* __restrict__ f, double* mass) {
+  __shared__ double sh[32];
+  int c = blockIdx.x;
+  int K = a.N * a.N * a.N;
+  const double* fc = f + a.cell_off[c];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) acc += fc[e];
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) mass[c] = a.dv * a.dv * a.dv * t;
+}
+
+__global__ void __launch_bounds__(256) k_rescale_apply(AuxArgs a, double* f, const double* mass) {
+  __shared__ double lam_s;
+  int c = blockIdx.x;
+  int q = a.cell_inst[c];
+  const InstDev& I = a.inst[q];
+  if (!(I.total_mass > 0.0)) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int j = 0; j < I.J; j++) s += mass[I.cell0 + j];
+    lam_s = I.total_mass / (I.dx * s);
+  }
+  __syncthreads();
+  double lam = lam_s;
+  int K = a.N * a.N * a.N;
+  double* fc = f + a.cell_off[c];
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < K; e += gridDim.y * blockDim.x) fc[e] *= lam;
+}
+
+cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st) {
+  double* mass = a.scratch + 2 * a.n_inst + a.C;  // [C]
+  k_cell_mass<<<a.C, 256, 0, st>>>(a, f, mass);
+  k_rescale_apply<<<dim3(a.C, 4), 256, 0, st>>>(a, f, mass);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Multigrid transfers on one instance's contiguous cells (K doubles per cell).
+// ---------------------------------------------------------------------------------------
+__global__ void k_restrict(const double* __restrict__ fine, double* __restrict__ coarse, long long K, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i < n; i += (long long)gridDim.x * blockDim.x) {
+    long long jc = i / K, k = i % K;
+    coarse[i] = 0.5 * (fine[(2 * jc) * K + k] + fine[(2 * jc + 1) * K + k]);
+  }
+}
+
+__global__ void k_prolong_add(double* __restrict__ fine, const double* __restrict__ fc, const double* __restrict__ fc0,
+                              long long K, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i < n; i += (long long)gridDim.x * blockDim.x) {
+    long long jc = i / K, k = i % K;
+    double d = fc[i] - fc0[i];
+    fine[(2 * jc) * K + k] += d;
+    fine[(2 * jc + 1) * K + k] += d;
+  }
+}
+
+__global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i < n; i += (long long)gridDim.x * blockDim.x) y[i] = a * y[i] + b * x[i];
+}
+
+static int blocks_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? b : 152 * 16);
+}
+
+cudaError_t launch_restrict(const double* fine, double* coarse, long long K, int Jc, cudaStream_t st) {
+  long long n = K * Jc;
+  k_restrict<<<blocks_for(n), 256, 0, st>>>(fine, coarse, K, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(double* fine, const double* fc, const double* fc0, long long K, int Jc, cudaStream_t st) {
+  long long n = K * Jc;
+  k_prolong_add<<<blocks_for(n), 256, 0, st>>>(fine, fc, fc0, K, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st) {
+  k_axpby<<<blocks_for(n), 256, 0, st>>>(y, x, a, b, n);
+  return cudaGetLastError();
+}
+
+}  // namespace sgs

@@ -1,0 +1,679 @@
+// Collision step (eqs. (13)-(16), (28)) for every cell of every instance.
+//
+// Q = Q^FSM[f,f] - Q^FSM[M,M] is evaluated as the single symmetric bilinear sum
+//   Q_s(a, b)_k = sum_{l+m=k} beta_s(l, m) ahat_l bhat_m,   a = f - M, b = f + M,
+//   beta_s(l, m) = G(|l+m|, |l-m|) - (G(2|l|, 0) + G(2|m|, 0)) / 2,
+// which equals the two-evaluation form exactly (Q_s is symmetric and Q_s(f,f) = Q^FSM[f,f])
+// and carries no cancellation between two large terms at small eps.
+//
+// Data flow per launch sequence:
+//   k_moments        f -> moments, discrete Maxwellian theta, nu            (FP64)
+//   k_dft_i3/i2/i1   f -+ M -> ahat, bhat in the spectral layout [group][k1][k2][k3][lane]
+//   k_sum            ahat, bhat, weight blocks -> partial qhat per work unit
+//   k_sum_reduce     partials -> qhat (fixed order, FP64 accumulation), Hermitian mirror
+//   k_idft_k1/k2/k3  qhat -> Q(v), P = Q - nu (M - f)
+// A spectral group packs 32 cells, one per warp lane, so every weight is warp-uniform.
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sgs {
+
+// ---------------------------------------------------------------------------------------
+// Moments and discrete Maxwellian of every cell.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_moments(const double* __restrict__ f, CellTables ct, int N, double dv,
+                                                  double newton_tol, int newton_max, double* __restrict__ theta,
+                                                  double* __restrict__ nu, Counters* cnt) {
+  __shared__ double vv[kMaxN];
+  __shared__ double part[8][5];
+  int c = blockIdx.x;
+  int K = N * N * N;
+  const double* fc = f + ct.cell_off[c];
+  if (threadIdx.x < N) vv[threadIdx.x] = node(threadIdx.x, N, dv);
+  __syncthreads();
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    int i3 = e % N, i2 = (e / N) % N, i1 = e / (N * N);
+    double x = fc[e];
+    double a = vv[i1], b = vv[i2], d = vv[i3];
+    s[0] += x;
+    s[1] += x * a;
+    s[2] += x * b;
+    s[3] += x * d;
+    s[4] += x * (a * a + b * b + d * d);
+  }
+  warp_allsum<5>(s);
+  int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int q = 0; q < 5; q++) part[wid][q] = s[q];
+  __syncthreads();
+  if (wid != 0) return;
+  double w = dv * dv * dv;
+  double m[5];
+  for (int q = 0; q < 5; q++) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += part[k][q];
+    m[q] = w * t;
+  }
+  const InstDev& I = ct.inst[ct.cell_inst[c]];
+  double th[5] = {0, 0, 0, 0, 0};
+  MaxwEval ev;
+  int it = -1;
+  if (continuum_guess(m, th)) it = maxwellian_newton(N, dv, w, false, 0.0, m, th, newton_tol, newton_max, ev);
+  double rho = m[0];
+  double T = (m[4] / rho - (m[1] * m[1] + m[2] * m[2] + m[3] * m[3]) / (rho * rho)) / 3.0;
+  double nuv = 4.0 * kPi * I.b0 * rho;
+  if (I.collision == SGS_HARD_SPHERE) nuv *= 4.0 * sqrt(T / kPi);
+  if (lane == 0) {
+    for (int q = 0; q < 5; q++) theta[5 * c + q] = th[q];
+    nu[c] = nuv;
+    unsigned bits = 0;
+    if (it < 0) bits |= SGS_ST_NEWTON_FAIL;
+    if (!(rho > 0.0) || !(T > 0.0)) bits |= SGS_ST_NONPOSITIVE;
+    if (!(rho == rho) || !(T == T)) bits |= SGS_ST_NONFINITE;
+    if (bits) atomicOr(&cnt[ct.cell_inst[c]].status, bits);
+  }
+}
+
+// Per-block factors E_d[i] of the discrete Maxwellian of cell c (E_1 carries exp(alpha)).
+__device__ inline void maxwell_factors(const double* theta, int c, int N, double dv, double* E /*[3][kMaxN]*/) {
+  if (threadIdx.x < 3 * N) {
+    int d = threadIdx.x / N, i = threadIdx.x % N;
+    const double* th = theta + 5 * c;
+    double v = node(i, N, dv);
+    double x = th[1 + d] * v - th[4] * v * v;
+    if (d == 0) x += th[0];
+    E[d * kMaxN + i] = exp(x);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Forward DFT, fhat_k = N^-3 sum_v f(v) exp(-i 2 pi k j / N), one index at a time.
+// Pass 1 (index 3) forms a = f - M and b = f + M in FP64 and transforms them in T.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_dft_i3(const double* __restrict__ f, CellTables ct, const double* theta,
+                                                 SpecBufs<T> sb, int N, double dv) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int n = N - 1;
+  T* cs = (T*)smraw;             // [n][N] cos
+  T* sn = cs + n * N;            // [n][N] sin
+  T* sa = sn + n * N;            // [N][N] a slab (i2, i3)
+  T* sbb = sa + N * N;           // [N][N] b slab
+  __shared__ double E[3 * kMaxN];
+  int c = blockIdx.x, i1 = blockIdx.y;
+  maxwell_factors(theta, c, N, dv, E);
+  for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
+    cs[t] = (T)sb.tw_cos[t];
+    sn[t] = (T)sb.tw_sin[t];
+  }
+  __syncthreads();
+  const double* fc = f + ct.cell_off[c] + (long long)i1 * N * N;
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    int i2 = t / N, i3 = t % N;
+    double M = E[i1] * E[kMaxN + i2] * E[2 * kMaxN + i3];
+    double x = fc[t];
+    sa[t] = (T)(x - M);
+    sbb[t] = (T)(x + M);
+  }
+  __syncthreads();
+  typedef typename CplxOf<T>::type CT;
+  CT* oa = sb.st1a + ((long long)c * N + i1) * N * n;
+  CT* ob = sb.st1b + ((long long)c * N + i1) * N * n;
+  for (int t = threadIdx.x; t < N * n; t += blockDim.x) {
+    int i2 = t / n, k3 = t % n;
+    T ar = 0, ai = 0, br = 0, bi = 0;
+    for (int i3 = 0; i3 < N; i3++) {
+      T co = cs[k3 * N + i3], si = sn[k3 * N + i3];
+      T a = sa[i2 * N + i3], b = sbb[i2 * N + i3];
+      ar += a * co;
+      ai -= a * si;
+      br += b * co;
+      bi -= b * si;
+    }
+    oa[t] = make_cplx(ar, ai);
+    ob[t] = make_cplx(br, bi);
+  }
+}
+
+// Pass 2 (index 2): [c][i1][i2][k3] -> [c][i1][k2][k3].
+template <typename T>
+__global__ void __launch_bounds__(256) k_dft_i2(SpecBufs<T> sb, int N) {
+  typedef typename CplxOf<T>::type CT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int n = N - 1;
+  T* cs = (T*)smraw;
+  T* sn = cs + n * N;
+  CT* xa = (CT*)(sn + n * N);  // [N][n]
+  CT* xb = xa + N * n;
+  int c = blockIdx.x, i1 = blockIdx.y;
+  for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
+    cs[t] = (T)sb.tw_cos[t];
+    sn[t] = (T)sb.tw_sin[t];
+  }
+  const CT* ia = sb.st1a + ((long long)c * N + i1) * N * n;
+  const CT* ib = sb.st1b + ((long long)c * N + i1) * N * n;
+  for (int t = threadIdx.x; t < N * n; t += blockDim.x) {
+    xa[t] = ia[t];
+    xb[t] = ib[t];
+  }
+  __syncthreads();
+  CT* oa = sb.st2a + ((long long)c * N + i1) * n * n;
+  CT* ob = sb.st2b + ((long long)c * N + i1) * n * n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int k2 = t / n, k3 = t % n;
+    T ar = 0, ai = 0, br = 0, bi = 0;
+    for (int i2 = 0; i2 < N; i2++) {
+      T co = cs[k2 * N + i2], si = -sn[k2 * N + i2];
+      CT a = xa[i2 * n + k3], b = xb[i2 * n + k3];
+      ar += a.x * co - a.y * si;
+      ai += a.x * si + a.y * co;
+      br += b.x * co - b.y * si;
+      bi += b.x * si + b.y * co;
+    }
+    oa[t] = make_cplx(ar, ai);
+    ob[t] = make_cplx(br, bi);
+  }
+}
+
+// Pass 3 (index 1): [c][i1][k2][k3] -> spectral layout [g][k1][k2][k3][lane], times N^-3.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dft_i1(SpecBufs<T> sb, int N) {
+  typedef typename CplxOf<T>::type CT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int n = N - 1;
+  T* cs = (T*)smraw;
+  T* sn = cs + n * N;
+  CT* xa = (CT*)(sn + n * N);  // [N][n] (i1, k3)
+  CT* xb = xa + N * n;
+  int c = blockIdx.x, k2 = blockIdx.y;
+  for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
+    cs[t] = (T)sb.tw_cos[t];
+    sn[t] = (T)sb.tw_sin[t];
+  }
+  for (int t = threadIdx.x; t < N * n; t += blockDim.x) {
+    int i1 = t / n, k3 = t % n;
+    long long src = (((long long)c * N + i1) * n + k2) * n + k3;
+    xa[t] = sb.st2a[src];
+    xb[t] = sb.st2b[src];
+  }
+  __syncthreads();
+  T scale = (T)(1.0 / ((double)N * N * N));
+  int g = c / kLanes, lane = c % kLanes;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int k1 = t / n, k3 = t % n;
+    T ar = 0, ai = 0, br = 0, bi = 0;
+    for (int i1 = 0; i1 < N; i1++) {
+      T co = cs[k1 * N + i1], si = -sn[k1 * N + i1];
+      CT a = xa[i1 * n + k3], b = xb[i1 * n + k3];
+      ar += a.x * co - a.y * si;
+      ai += a.x * si + a.y * co;
+      br += b.x * co - b.y * si;
+      bi += b.x * si + b.y * co;
+    }
+    long long o = ((((long long)g * n + k1) * n + k2) * n + k3) * kLanes + lane;
+    sb.ahat[o] = make_cplx(ar * scale, ai * scale);
+    sb.bhat[o] = make_cplx(br * scale, bi * scale);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Direct spectral sum. Work unit = one output row (k1, k2) of the Hermitian half and a
+// range of m1; a step = one (m1, m2) with its weight block W[(m3, k3) valid pairs]
+// precomputed at setup in exactly the loop order below. Each warp owns one group of 32
+// cells (lane = cell) and accumulates the 2H+1 outputs k3 of the row in registers; the
+// rows ahat[(k1-m1, k2-m2, .)] and bhat[(m1, m2, .)] and the weight block of the next
+// step are brought in by bulk copies into shared memory while the current step computes.
+// FP32 keeps both rows in registers (full unroll, weights read as warp-uniform shared
+// loads); FP64 reads them from shared memory.
+// ---------------------------------------------------------------------------------------
+template <typename T, int H>
+__global__ void __launch_bounds__(128) k_sum(SumArgs<T> a) {
+  typedef typename CplxOf<T>::type CT;
+  constexpr int n = 2 * H + 1;
+  constexpr int NP = 3 * H * H + 3 * H + 1;
+  constexpr int VEC = 16 / (int)sizeof(T);
+  constexpr int PW = (NP + VEC - 1) / VEC * VEC;
+  constexpr bool kRegs = sizeof(T) == 4;
+  constexpr int kRowBufs = kRegs ? 1 : 2;
+  typedef typename VecOf<T>::type VT;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* Wb = (T*)smraw;                                   // [2][PW]
+  CT* rows = (CT*)(smraw + 2 * PW * sizeof(T));        // [kRowBufs][NW][2][n][32]
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int s_err;
+
+  const int NW = blockDim.x >> 5;
+  const int4 ud = a.units[blockIdx.x];  // k1, k2, m1_lo, m1_hi
+  const long long step0 = a.unit_step0[blockIdx.x];
+  const int k1 = ud.x, k2 = ud.y, m1lo = ud.z, m1hi = ud.w;
+  const int m2lo = max(-H, k2 - H), m2hi = min(H, k2 + H);
+  const int nm2 = m2hi - m2lo + 1;
+  const int S = (m1hi - m1lo + 1) * nm2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g0 = blockIdx.y * NW;
+  const int ng = min(NW, a.G - g0);
+  const uint32_t row_bytes = n * kLanes * sizeof(CT);
+  const uint32_t stage_bytes = PW * sizeof(T) + ng * 2 * row_bytes;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    s_err = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int s) {
+    int m1 = m1lo + s / nm2, m2 = m2lo + s % nm2;
+    int b = s & 1;
+    mbar_arrive_expect_tx(&bar[b], stage_bytes);
+    bulk_g2s(Wb + b * PW, a.W + (step0 + s) * PW, PW * sizeof(T), &bar[b]);
+    int rb = kRegs ? 0 : b;
+    for (int w = 0; w < ng; w++) {
+      long long ga = (((long long)(g0 + w) * n + (k1 - m1 + H)) * n + (k2 - m2 + H)) * n * kLanes;
+      long long gb = (((long long)(g0 + w) * n + (m1 + H)) * n + (m2 + H)) * n * kLanes;
+      CT* dst = rows + ((rb * NW + w) * 2) * n * kLanes;
+      bulk_g2s(dst, a.ahat + ga, row_bytes, &bar[b]);
+      bulk_g2s(dst + n * kLanes, a.bhat + gb, row_bytes, &bar[b]);
+    }
+  };
+
+  if (threadIdx.x == 0 && S > 0) issue(0);
+
+  T accr[n], acci[n];
+#pragma unroll
+  for (int i = 0; i < n; i++) accr[i] = acci[i] = (T)0;
+
+  const bool active = warp < ng;
+  int fail_b = 0, fail_par = 0;
+  for (int s = 0; s < S; s++) {
+    const int b = s & 1;
+    if (!mbar_wait(&bar[b], (s >> 1) & 1, a.spin_max)) {
+      s_err = 1;
+      fail_b = b;
+      fail_par = (s >> 1) & 1;
+    }
+    const VT* W4 = (const VT*)(Wb + b * PW);
+    if (kRegs) {
+      CT Ar[n], Br[n];
+      const CT* rw = rows + (warp * 2) * n * kLanes;
+      if (active) {
+#pragma unroll
+        for (int i = 0; i < n; i++) {
+          Ar[i] = rw[i * kLanes + lane];
+          Br[i] = rw[(n + i) * kLanes + lane];
+        }
+      }
+      __syncthreads();
+      if (s_err) break;
+      if (threadIdx.x == 0 && s + 1 < S) issue(s + 1);
+      if (active) {
+        VT wv;
+        int p = 0;
+#pragma unroll
+        for (int m3 = -H; m3 <= H; m3++) {
+          const CT bv = Br[m3 + H];
+#pragma unroll
+          for (int k3 = (m3 - H > -H ? m3 - H : -H); k3 <= (m3 + H < H ? m3 + H : H); k3++) {
+            if (p % VEC == 0) wv = W4[p / VEC];
+            const T w = vec_get(wv, p % VEC);
+            p++;
+            const CT av = Ar[k3 - m3 + H];
+            const T br = w * bv.x, bi = w * bv.y;
+            accr[k3 + H] = fma(av.x, br, accr[k3 + H]);
+            accr[k3 + H] = fma(-av.y, bi, accr[k3 + H]);
+            acci[k3 + H] = fma(av.x, bi, acci[k3 + H]);
+            acci[k3 + H] = fma(av.y, br, acci[k3 + H]);
+          }
+        }
+      }
+    } else {
+      __syncthreads();
+      if (s_err) break;
+      if (threadIdx.x == 0 && s + 1 < S) issue(s + 1);
+      if (active) {
+        const CT* rw = rows + ((b * NW + warp) * 2) * n * kLanes;
+        VT wv;
+        int p = 0;
+#pragma unroll
+        for (int m3 = -H; m3 <= H; m3++) {
+          const CT bv = rw[(n + m3 + H) * kLanes + lane];
+#pragma unroll
+          for (int k3 = (m3 - H > -H ? m3 - H : -H); k3 <= (m3 + H < H ? m3 + H : H); k3++) {
+            if (p % VEC == 0) wv = W4[p / VEC];
+            const T w = vec_get(wv, p % VEC);
+            p++;
+            const CT av = rw[(k3 - m3 + H) * kLanes + lane];
+            const T br = w * bv.x, bi = w * bv.y;
+            accr[k3 + H] = fma(av.x, br, accr[k3 + H]);
+            accr[k3 + H] = fma(-av.y, bi, accr[k3 + H]);
+            acci[k3 + H] = fma(av.x, bi, acci[k3 + H]);
+            acci[k3 + H] = fma(av.y, br, acci[k3 + H]);
+          }
+        }
+      }
+    }
+  }
+  if (s_err) {
+    // A copy did not land within the spin limit: report, then wait (bounded) for that
+    // phase so no copy is still writing this block's shared memory when it exits.
+    if (threadIdx.x == 0) {
+      atomicOr(&a.cnt[0].status, SGS_ST_TIMEOUT);
+      mbar_wait(&bar[fail_b], fail_par, a.spin_max);
+    }
+    return;
+  }
+  if (active) {
+    CT* out = a.partial + ((long long)blockIdx.x * a.G + (g0 + warp)) * n * kLanes;
+#pragma unroll
+    for (int i = 0; i < n; i++) out[i * kLanes + lane] = make_cplx(accr[i], acci[i]);
+  }
+}
+
+// Fixed-order sum of a row's unit partials (FP64 accumulation), written to qhat at (k1, k2,
+// k3) and conjugated at (-k1, -k2, -k3); row (0, 0) is computed in full and not mirrored.
+template <typename T>
+__global__ void k_sum_reduce(RedArgs<T> a) {
+  typedef typename CplxOf<T>::type CT;
+  int row = blockIdx.x, g = blockIdx.y;
+  int n = a.n, H = (n - 1) / 2;
+  int k1 = a.row_k[row].x, k2 = a.row_k[row].y;
+  int u0 = a.row_start[row], u1 = a.row_start[row + 1];
+  for (int t = threadIdx.x; t < n * kLanes; t += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int q = u0; q < u1; q++) {
+      int u = a.row_units[q];
+      CT v = a.partial[((long long)u * a.G + g) * n * kLanes + t];
+      sr += (double)v.x;
+      si += (double)v.y;
+    }
+    int k3i = t / kLanes, lane = t % kLanes;
+    long long o = ((((long long)g * n + (k1 + H)) * n + (k2 + H)) * n + k3i) * kLanes + lane;
+    a.qhat[o] = make_cplx((T)sr, (T)si);
+    if (k1 != 0 || k2 != 0) {
+      long long om = ((((long long)g * n + (H - k1)) * n + (H - k2)) * n + (n - 1 - k3i)) * kLanes + lane;
+      a.qhat[om] = make_cplx((T)sr, (T)(-si));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Inverse DFT, q(v) = Re sum_k qhat_k exp(+i 2 pi k j / N).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_idft_k1(SpecBufs<T> sb, int N) {
+  typedef typename CplxOf<T>::type CT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int n = N - 1;
+  T* cs = (T*)smraw;
+  T* sn = cs + n * N;
+  CT* x = (CT*)(sn + n * N);  // [k1][k3]
+  int c = blockIdx.x, k2 = blockIdx.y;
+  int g = c / kLanes, lane = c % kLanes;
+  for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
+    cs[t] = (T)sb.tw_cos[t];
+    sn[t] = (T)sb.tw_sin[t];
+  }
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int k1 = t / n, k3 = t % n;
+    x[t] = sb.qhat[((((long long)g * n + k1) * n + k2) * n + k3) * kLanes + lane];
+  }
+  __syncthreads();
+  CT* o = sb.st2a + (long long)c * N * n * n;  // [i1][k2][k3]
+  for (int t = threadIdx.x; t < N * n; t += blockDim.x) {
+    int i1 = t / n, k3 = t % n;
+    T re = 0, im = 0;
+    for (int k1 = 0; k1 < n; k1++) {
+      T co = cs[k1 * N + i1], si = sn[k1 * N + i1];
+      CT q = x[k1 * n + k3];
+      re += q.x * co - q.y * si;
+      im += q.x * si + q.y * co;
+    }
+    o[((long long)i1 * n + k2) * n + k3] = make_cplx(re, im);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_idft_k2(SpecBufs<T> sb, int N) {
+  typedef typename CplxOf<T>::type CT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int n = N - 1;
+  T* cs = (T*)smraw;
+  T* sn = cs + n * N;
+  CT* x = (CT*)(sn + n * N);  // [k2][k3]
+  int c = blockIdx.x, i1 = blockIdx.y;
+  for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
+    cs[t] = (T)sb.tw_cos[t];
+    sn[t] = (T)sb.tw_sin[t];
+  }
+  const CT* src = sb.st2a + ((long long)c * N + i1) * n * n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) x[t] = src[t];
+  __syncthreads();
+  CT* o = sb.st1a + ((long long)c * N + i1) * N * n;  // [i2][k3]
+  for (int t = threadIdx.x; t < N * n; t += blockDim.x) {
+    int i2 = t / n, k3 = t % n;
+    T re = 0, im = 0;
+    for (int k2 = 0; k2 < n; k2++) {
+      T co = cs[k2 * N + i2], si = sn[k2 * N + i2];
+      CT q = x[k2 * n + k3];
+      re += q.x * co - q.y * si;
+      im += q.x * si + q.y * co;
+    }
+    o[t] = make_cplx(re, im);
+  }
+}
+
+// Last pass: real part along index 3, then Q and P = Q - nu (M - f) in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* __restrict__ f, CellTables ct,
+                                                  const double* theta, const double* nu, double* Q, double* P,
+                                                  int N, double dv) {
+  typedef typename CplxOf<T>::type CT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int n = N - 1;
+  T* cs = (T*)smraw;
+  T* sn = cs + n * N;
+  CT* x = (CT*)(sn + n * N);  // [i2][k3]
+  __shared__ double E[3 * kMaxN];
+  int c = blockIdx.x, i1 = blockIdx.y;
+  maxwell_factors(theta, c, N, dv, E);
+  for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
+    cs[t] = (T)sb.tw_cos[t];
+    sn[t] = (T)sb.tw_sin[t];
+  }
+  const CT* src = sb.st1a + ((long long)c * N + i1) * N * n;
+  for (int t = threadIdx.x; t < N * n; t += blockDim.x) x[t] = src[t];
+  __syncthreads();
+  long long base = ct.cell_off[c] + (long long)i1 * N * N;
+  double nuc = nu[c];
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    int i2 = t / N, i3 = t % N;
+    T re = 0;
+    for (int k3 = 0; k3 < n; k3++) {
+      CT q = x[i2 * n + k3];
+      re += q.x * cs[k3 * N + i3] - q.y * sn[k3 * N + i3];
+    }
+    double q = (double)re;
+    if (Q) Q[base + t] = q;
+    if (P) {
+      double M = E[i1] * E[kMaxN + i2] * E[2 * kMaxN + i3];
+      P[base + t] = q - nuc * (M - f[base + t]);
+    }
+  }
+}
+
+// BGK mode (eq. (12)): Q = nu (M - f), P = 0.
+__global__ void __launch_bounds__(256) k_collide_bgk(const double* __restrict__ f, CellTables ct,
+                                                      const double* theta, const double* nu, double* Q, double* P,
+                                                      int N, double dv) {
+  __shared__ double E[3 * kMaxN];
+  int c = blockIdx.x, i1 = blockIdx.y;
+  maxwell_factors(theta, c, N, dv, E);
+  __syncthreads();
+  long long base = ct.cell_off[c] + (long long)i1 * N * N;
+  double nuc = nu[c];
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    int i2 = t / N, i3 = t % N;
+    double M = E[i1] * E[kMaxN + i2] * E[2 * kMaxN + i3];
+    if (Q) Q[base + t] = nuc * (M - f[base + t]);
+    if (P) P[base + t] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Setup: weight blocks W[step][p] = beta_s for the (m3, k3) pairs of each (k1, k2, m1, m2)
+// step, in the loop order of k_sum, from the tables G[a2][b2] and Lo[m2] = G(2|m|, 0).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_build_weights(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
+                                const double* G, long long nb, const double* Lo, T* W) {
+  int u = blockIdx.x;
+  if (u >= n_units) return;
+  int4 ud = units[u];
+  int k1 = ud.x, k2 = ud.y;
+  int m2lo = max(-H, k2 - H), m2hi = min(H, k2 + H);
+  int nm2 = m2hi - m2lo + 1;
+  int S = (ud.w - ud.z + 1) * nm2;
+  int np = 3 * H * H + 3 * H + 1;
+  for (int s = blockIdx.y; s < S; s += gridDim.y) {
+    int m1 = ud.z + s / nm2, m2 = m2lo + s % nm2;
+    T* out = W + (unit_step0[u] + s) * PW;
+    for (int p = threadIdx.x; p < PW; p += blockDim.x) {
+      if (p >= np) {
+        out[p] = (T)0;
+        continue;
+      }
+      // invert p -> (m3, k3) in the k_sum loop order
+      int q = p, m3 = -H, k3 = 0;
+      for (m3 = -H; m3 <= H; m3++) {
+        int lo = max(-H, m3 - H), hi = min(H, m3 + H);
+        int cnt = hi - lo + 1;
+        if (q < cnt) {
+          k3 = lo + q;
+          break;
+        }
+        q -= cnt;
+      }
+      long long a2 = (long long)k1 * k1 + (long long)k2 * k2 + (long long)k3 * k3;
+      long long d1 = k1 - 2 * m1, d2 = k2 - 2 * m2, d3 = k3 - 2 * m3;
+      long long b2 = d1 * d1 + d2 * d2 + d3 * d3;
+      long long l1 = k1 - m1, l2 = k2 - m2, l3 = k3 - m3;
+      long long ll = l1 * l1 + l2 * l2 + l3 * l3;
+      long long mm = (long long)m1 * m1 + (long long)m2 * m2 + (long long)m3 * m3;
+      double w = G[a2 * nb + b2] - 0.5 * (Lo[ll] + Lo[mm]);
+      out[p] = (T)w;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side launchers.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+static size_t dft_smem(int N, int extra_cplx, int extra_real) {
+  typedef typename CplxOf<T>::type CT;
+  int n = N - 1;
+  return 2 * n * N * sizeof(T) + extra_cplx * sizeof(CT) + extra_real * sizeof(T);
+}
+
+template <typename T, int H>
+static cudaError_t launch_sum_t(const SumArgs<T>& a, int NW, int n_units, cudaStream_t st) {
+  typedef typename CplxOf<T>::type CT;
+  constexpr int n = 2 * H + 1;
+  constexpr int NP = 3 * H * H + 3 * H + 1;
+  constexpr int VEC = 16 / (int)sizeof(T);
+  constexpr int PW = (NP + VEC - 1) / VEC * VEC;
+  constexpr int kRowBufs = sizeof(T) == 4 ? 1 : 2;
+  size_t smem = 2 * PW * sizeof(T) + (size_t)kRowBufs * NW * 2 * n * kLanes * sizeof(CT);
+  cudaError_t e = cudaFuncSetAttribute(k_sum<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(n_units, (a.G + NW - 1) / NW);
+  k_sum<T, H><<<grid, NW * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+int sum_pad(int H, int elem_bytes) {
+  int NP = 3 * H * H + 3 * H + 1, VEC = 16 / elem_bytes;
+  return (NP + VEC - 1) / VEC * VEC;
+}
+
+template <typename T>
+cudaError_t launch_sum(const SumArgs<T>& a, int H, int NW, int n_units, cudaStream_t st) {
+  if (NW < 1 || NW > 4) return cudaErrorInvalidValue;
+  switch (H) {
+    case 3: return launch_sum_t<T, 3>(a, NW, n_units, st);
+    case 5: return launch_sum_t<T, 5>(a, NW, n_units, st);
+    case 7: return launch_sum_t<T, 7>(a, NW, n_units, st);
+    case 9: return launch_sum_t<T, 9>(a, NW, n_units, st);
+    case 11: return launch_sum_t<T, 11>(a, NW, n_units, st);
+    case 13: return launch_sum_t<T, 13>(a, NW, n_units, st);
+    case 15: return launch_sum_t<T, 15>(a, NW, n_units, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_collide_spectral(const double* f, double* Q, double* P, const CollideCtx<T>& x, cudaStream_t st) {
+  int N = x.N, n = N - 1, C = x.C;
+  cudaError_t e;
+  size_t sm1 = dft_smem<T>(N, 0, 2 * N * N);
+  e = cudaFuncSetAttribute(k_dft_i3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  if (e != cudaSuccess) return e;
+  k_dft_i3<T><<<dim3(C, N), 256, sm1, st>>>(f, x.ct, x.theta, x.sb, N, x.dv);
+  size_t sm2 = dft_smem<T>(N, 2 * N * n, 0);
+  e = cudaFuncSetAttribute(k_dft_i2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  if (e != cudaSuccess) return e;
+  k_dft_i2<T><<<dim3(C, N), 256, sm2, st>>>(x.sb, N);
+  e = cudaFuncSetAttribute(k_dft_i1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  if (e != cudaSuccess) return e;
+  // groups beyond the last cell keep the zeros written at bind time
+  k_dft_i1<T><<<dim3(C, n), 256, sm2, st>>>(x.sb, N);
+  e = launch_sum<T>(x.sum, x.H, x.NW, x.n_units, st);
+  if (e != cudaSuccess) return e;
+  k_sum_reduce<T><<<dim3(x.red.n_rows, x.red.G), 256, 0, st>>>(x.red);
+  size_t sm3 = dft_smem<T>(N, n * n, 0);
+  e = cudaFuncSetAttribute(k_idft_k1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+  if (e != cudaSuccess) return e;
+  k_idft_k1<T><<<dim3(C, n), 256, sm3, st>>>(x.sb, N);
+  e = cudaFuncSetAttribute(k_idft_k2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+  if (e != cudaSuccess) return e;
+  k_idft_k2<T><<<dim3(C, N), 256, sm3, st>>>(x.sb, N);
+  size_t sm4 = dft_smem<T>(N, N * n, 0);
+  e = cudaFuncSetAttribute(k_idft_k3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
+  if (e != cudaSuccess) return e;
+  k_idft_k3<T><<<dim3(C, N), 256, sm4, st>>>(x.sb, f, x.ct, x.theta, x.nu, Q, P, N, x.dv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const double* f, const CellTables& ct, int C, int N, double dv, double tol, int maxit,
+                           double* theta, double* nu, Counters* cnt, cudaStream_t st) {
+  k_moments<<<C, 256, 0, st>>>(f, ct, N, dv, tol, maxit, theta, nu, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collide_bgk(const double* f, const CellTables& ct, int C, int N, double dv, const double* theta,
+                               const double* nu, double* Q, double* P, cudaStream_t st) {
+  k_collide_bgk<<<dim3(C, N), 256, 0, st>>>(f, ct, theta, nu, Q, P, N, dv);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_build_weights(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
+                                 const double* G, long long nb, const double* Lo, T* W, cudaStream_t st) {
+  k_build_weights<T><<<dim3(n_units, 8), 256, 0, st>>>(units, unit_step0, n_units, H, PW, G, nb, Lo, W);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_collide_spectral<double>(const double*, double*, double*, const CollideCtx<double>&,
+                                                     cudaStream_t);
+template cudaError_t launch_collide_spectral<float>(const double*, double*, double*, const CollideCtx<float>&,
+                                                    cudaStream_t);
+template cudaError_t launch_build_weights<double>(const int4*, const long long*, int, int, int, const double*,
+                                                  long long, const double*, double*, cudaStream_t);
+template cudaError_t launch_build_weights<float>(const int4*, const long long*, int, int, int, const double*,
+                                                 long long, const double*, float*, cudaStream_t);
+
+}  // namespace sgs

@@ -1,0 +1,138 @@
+// Launch interfaces between the host API (sgs_api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sgs {
+
+template <typename T>
+struct CplxOf;
+template <>
+struct CplxOf<double> {
+  typedef double2 type;
+};
+template <>
+struct CplxOf<float> {
+  typedef float2 type;
+};
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<double> {
+  typedef double2 type;
+};
+template <>
+struct VecOf<float> {
+  typedef float4 type;
+};
+__device__ __forceinline__ double vec_get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+__device__ __forceinline__ float vec_get(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+int sum_pad(int H, int elem_bytes);
+__host__ __device__ inline double2 make_cplx(double a, double b) { return make_double2(a, b); }
+__host__ __device__ inline float2 make_cplx(float a, float b) { return make_float2(a, b); }
+
+// Cell list of the collision step (all instances, same N).
+struct CellTables {
+  const InstDev* inst;
+  const long long* cell_off;  // element offset of each cell's distribution
+  const int* cell_inst;       // instance of each cell
+};
+
+template <typename T>
+struct SpecBufs {
+  typedef typename CplxOf<T>::type CT;
+  const double* tw_cos;  // [n][N] cos(2 pi k j / N), k = row - h, j = i - N/2 + 1
+  const double* tw_sin;  // [n][N] sin(2 pi k j / N)
+  CT *st1a, *st1b;       // [C][N][N][n]
+  CT *st2a, *st2b;       // [C][N][n][n]
+  CT *ahat, *bhat;       // [G][n][n][n][32]
+  CT* qhat;              // [G][n][n][n][32]
+};
+
+template <typename T>
+struct SumArgs {
+  typedef typename CplxOf<T>::type CT;
+  const int4* units;            // k1, k2, m1_lo, m1_hi
+  const long long* unit_step0;  // first step of each unit in the weight table
+  const T* W;                   // [steps][PW]
+  const CT* ahat;
+  const CT* bhat;
+  CT* partial;                  // [units][G][n][32]
+  int G;
+  Counters* cnt;
+  long long spin_max;
+};
+
+template <typename T>
+struct RedArgs {
+  typedef typename CplxOf<T>::type CT;
+  const int2* row_k;      // (k1, k2) of each half-space row
+  const int* row_start;   // CSR over row_units
+  const int* row_units;
+  const CT* partial;
+  CT* qhat;
+  int n, G, n_rows;
+};
+
+template <typename T>
+struct CollideCtx {
+  int N, C, H, NW, n_units;
+  double dv;
+  CellTables ct;
+  const double* theta;
+  const double* nu;
+  SpecBufs<T> sb;
+  SumArgs<T> sum;
+  RedArgs<T> red;
+};
+
+struct SweepArgs {
+  const InstDev* inst;
+  int n_inst;
+  double* f;
+  const double* P;
+  const double* rhs;
+  const double* nu;       // per global cell
+  Counters* cnt;          // per instance
+  int N;
+  double dv;
+  int dir;                // +1 forward, -1 backward
+};
+
+struct AuxArgs {
+  const InstDev* inst;
+  int n_inst, N, C;
+  double dv;
+  const long long* cell_off;
+  const int* cell_inst;
+  double* scratch;        // per-cell partials, per-instance values
+};
+
+cudaError_t launch_moments(const double* f, const CellTables& ct, int C, int N, double dv, double tol, int maxit,
+                           double* theta, double* nu, Counters* cnt, cudaStream_t st);
+cudaError_t launch_collide_bgk(const double* f, const CellTables& ct, int C, int N, double dv, const double* theta,
+                               const double* nu, double* Q, double* P, cudaStream_t st);
+template <typename T>
+cudaError_t launch_collide_spectral(const double* f, double* Q, double* P, const CollideCtx<T>& x, cudaStream_t st);
+template <typename T>
+cudaError_t launch_build_weights(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
+                                 const double* G, long long nb, const double* Lo, T* W, cudaStream_t st);
+
+cudaError_t launch_sweep(const SweepArgs& a, int cluster, int tpb, cudaStream_t st);
+int sweep_cluster_for(int N);
+
+cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st);
+cudaError_t launch_residual(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
+                            cudaStream_t st);
+cudaError_t launch_restrict(const double* fine, double* coarse, long long K, int Jc, cudaStream_t st);
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st);
+cudaError_t launch_prolong_add(double* fine, const double* fc, const double* fc0, long long K, int Jc,
+                               cudaStream_t st);
+cudaError_t launch_residual_field(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* R,
+                                  cudaStream_t st);
+
+}  // namespace sgs

@@ -1,0 +1,626 @@
+// Host side of the C ABI declared in include/sgs.h: problem validation, velocity-grid and
+// Fourier-weight tables, work planning of the spectral sum, workspace layout and the
+// enqueueing of kernels on the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace sgs;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// ---------------------------------------------------------------------------------------
+// Fourier weight of the collision integral, closed form of
+//   G(a, b) = 16 pi^2 int_0^{2R} rho^2 B(rho) sinc(c a rho) sinc(c b rho) drho,  c = pi/(2L),
+// for B = b0 (Maxwell molecules) and B = b0 rho (hard spheres); a, b given by their
+// squares (integers). Products of sines integrate in closed form.
+// ---------------------------------------------------------------------------------------
+double radial_I0(double om, double R) {  // int_0^R cos(om x) dx
+  return om == 0.0 ? R : std::sin(om * R) / om;
+}
+double radial_I1(double om, double R) {  // int_0^R x cos(om x) dx
+  if (om == 0.0) return 0.5 * R * R;
+  double s = std::sin(0.5 * om * R);
+  return R * std::sin(om * R) / om - 2.0 * s * s / (om * om);
+}
+double radial_sin2(double A, double R) {  // int_0^R x^2 sin(A x) / A dx  (A > 0): the b = 0 case, Maxwell
+  return (std::sin(A * R) / (A * A) - R * std::cos(A * R) / A) / A;
+}
+double radial_sin3(double A, double R) {  // int_0^R x^2 sin(A x) / A dx (A > 0): the b = 0 case, hard spheres
+  double AR = A * R, hh = std::sin(0.5 * AR);
+  return (-R * R * std::cos(AR) / A + 2.0 * R * std::sin(AR) / (A * A) - 4.0 * hh * hh / (A * A * A)) / A;
+}
+
+double weight_G(int N, double L, int collision, double b0, long long a2, long long b2) {
+  (void)N;
+  const double pi = kPi;
+  double R2 = 2.0 * (2.0 * L / (3.0 * std::sqrt(2.0) + 1.0));
+  double c = pi / (2.0 * L);
+  double Kc = 16.0 * pi * pi * b0;
+  double a = std::sqrt((double)a2), b = std::sqrt((double)b2);
+  bool hs = collision == SGS_HARD_SPHERE;
+  if (a2 == 0 && b2 == 0) return hs ? Kc * std::pow(R2, 4) / 4.0 : Kc * R2 * R2 * R2 / 3.0;
+  if (a2 == 0 || b2 == 0) {
+    double A = c * (a2 == 0 ? b : a);
+    return hs ? Kc * radial_sin3(A, R2) : Kc * radial_sin2(A, R2);
+  }
+  double A = c * a, B = c * b;
+  // sinc(A x) sinc(B x) = [cos((A-B)x) - cos((A+B)x)] / (2 A B x^2)
+  if (hs) return Kc / (2.0 * A * B) * (radial_I1(A - B, R2) - radial_I1(A + B, R2));
+  return Kc / (2.0 * A * B) * (radial_I0(A - B, R2) - radial_I0(A + B, R2));
+}
+
+bool valid_nv(int N) { return N >= 8 && N <= 32 && N % 4 == 0; }
+
+struct Unit {
+  int k1, k2, m1lo, m1hi;
+  long long step0;
+  int steps;
+  int row;
+};
+
+}  // namespace
+
+struct sgs_handle {
+  int n_inst = 0, N = 0, n = 0, H = 0, precision = SGS_FP64;
+  int C = 0, G = 0;
+  double L = 0.0, dv = 0.0;
+  long long field = 0;
+  bool spectral = true;  // false when every instance uses BGK
+  std::vector<sgs_problem> prob;
+  std::vector<InstDev> inst;
+  std::vector<long long> cell_off;
+  std::vector<int> cell_inst;
+  // spectral-sum plan
+  std::vector<Unit> units;  // launch order
+  std::vector<int2> row_k;
+  std::vector<int> row_start, row_units;
+  long long steps = 0;
+  int NW = 1, PW64 = 0, PW32 = 0;
+  // tables
+  std::vector<double> tw_cos, tw_sin, Gtab, Lo;
+  long long na = 0, nb = 0;
+  // workspace
+  size_t ws_bytes = 0;
+  char* ws = nullptr;
+  struct {
+    size_t inst, cell_off, cell_inst, cnt, theta, nu, scratch, tw_cos, tw_sin, G, Lo, units, step0, row_k, row_start,
+        row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, end;
+  } off;
+  int sweep_cluster = 1, sweep_tpb = 256;
+  long long spin_max = 1LL << 26;
+
+  template <typename T>
+  T* at(size_t o) const {
+    return reinterpret_cast<T*>(ws + o);
+  }
+};
+
+namespace {
+
+int plan(sgs_handle* h) {
+  int N = h->N, n = N - 1, H = N / 2 - 1;
+  h->n = n;
+  h->H = H;
+  h->G = (h->C + kLanes - 1) / kLanes;
+  h->NW = h->G >= 2 ? 2 : 1;
+  h->PW64 = sum_pad(H, 8);
+  h->PW32 = sum_pad(H, 4);
+  // twiddles: angle 2 pi ((k j) mod N) / N, k in [-H, H], j = i - N/2 + 1
+  h->tw_cos.assign((size_t)n * N, 0.0);
+  h->tw_sin.assign((size_t)n * N, 0.0);
+  for (int k = -H; k <= H; k++)
+    for (int i = 0; i < N; i++) {
+      long long kj = ((long long)k * (i - N / 2 + 1)) % N;
+      if (kj < 0) kj += N;
+      double ang = 2.0 * kPi * (double)kj / N;
+      h->tw_cos[(size_t)(k + H) * N + i] = std::cos(ang);
+      h->tw_sin[(size_t)(k + H) * N + i] = std::sin(ang);
+    }
+  if (!h->spectral) return SGS_OK;
+  const sgs_problem& p0 = h->prob[0];
+  h->na = 3LL * H * H + 1;
+  h->nb = 12LL * H * H + 1;
+  h->Gtab.resize((size_t)(h->na * h->nb));
+  h->Lo.resize((size_t)h->na);
+  for (long long a2 = 0; a2 < h->na; a2++) {
+    for (long long b2 = 0; b2 < h->nb; b2++)
+      h->Gtab[(size_t)(a2 * h->nb + b2)] = weight_G(N, p0.v_max, p0.collision, p0.b0, a2, b2);
+    h->Lo[(size_t)a2] = weight_G(N, p0.v_max, p0.collision, p0.b0, 4 * a2, 0);
+  }
+  // rows of the Hermitian half: k1 > 0, or k1 == 0 and k2 >= 0
+  std::vector<Unit> u;
+  long long total = 0;
+  int row = 0;
+  for (int k1 = 0; k1 <= H; k1++)
+    for (int k2 = -H; k2 <= H; k2++) {
+      if (k1 == 0 && k2 < 0) continue;
+      int m1lo = std::max(-H, k1 - H), m1hi = std::min(H, k1 + H);
+      int nm2 = n - std::abs(k2);
+      total += (long long)(m1hi - m1lo + 1) * nm2;
+      h->row_k.push_back(make_int2(k1, k2));
+      row++;
+    }
+  int n_rows = row;
+  int blocks_y = (h->G + h->NW - 1) / h->NW;
+  long long target_units = std::max(1LL, 3000LL / blocks_y);
+  long long cap = std::max<long long>(n, total / target_units);
+  long long step = 0;
+  for (int r = 0; r < n_rows; r++) {
+    int k1 = h->row_k[r].x, k2 = h->row_k[r].y;
+    int m1lo = std::max(-H, k1 - H), m1hi = std::min(H, k1 + H);
+    int nm2 = n - std::abs(k2);
+    int per = (int)std::max(1LL, cap / nm2);
+    for (int m = m1lo; m <= m1hi; m += per) {
+      Unit x;
+      x.k1 = k1;
+      x.k2 = k2;
+      x.m1lo = m;
+      x.m1hi = std::min(m1hi, m + per - 1);
+      x.steps = (x.m1hi - x.m1lo + 1) * nm2;
+      x.step0 = step;
+      x.row = r;
+      step += x.steps;
+      u.push_back(x);
+    }
+  }
+  h->steps = step;
+  // longest units first
+  std::stable_sort(u.begin(), u.end(), [](const Unit& a, const Unit& b) { return a.steps > b.steps; });
+  h->units = u;
+  h->row_start.assign(n_rows + 1, 0);
+  for (auto& x : u) h->row_start[x.row + 1]++;
+  for (int r = 0; r < n_rows; r++) h->row_start[r + 1] += h->row_start[r];
+  h->row_units.assign(u.size(), 0);
+  std::vector<int> fill(h->row_start.begin(), h->row_start.end() - 1);
+  // within a row, partials are summed in m1 order
+  std::vector<int> order(u.size());
+  for (size_t i = 0; i < u.size(); i++) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return u[a].row != u[b].row ? u[a].row < u[b].row : u[a].m1lo < u[b].m1lo;
+  });
+  for (int i : order) h->row_units[fill[u[i].row]++] = i;
+  return SGS_OK;
+}
+
+void layout(sgs_handle* h) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  int N = h->N, n = h->n, C = h->C, G = h->G;
+  auto& f = h->off;
+  f.inst = take(sizeof(InstDev) * h->n_inst);
+  f.cell_off = take(sizeof(long long) * C);
+  f.cell_inst = take(sizeof(int) * C);
+  f.cnt = take(sizeof(Counters) * h->n_inst);
+  f.theta = take(sizeof(double) * 5 * C);
+  f.nu = take(sizeof(double) * C);
+  f.scratch = take(sizeof(double) * (2 * h->n_inst + 2 * C + 64));
+  f.tw_cos = take(sizeof(double) * n * N);
+  f.tw_sin = take(sizeof(double) * n * N);
+  bool sp = h->spectral;
+  size_t U = h->units.size();
+  f.G = take(sp ? sizeof(double) * h->na * h->nb : 0);
+  f.Lo = take(sp ? sizeof(double) * h->na : 0);
+  f.units = take(sizeof(int4) * U);
+  f.step0 = take(sizeof(long long) * U);
+  f.row_k = take(sizeof(int2) * h->row_k.size());
+  f.row_start = take(sizeof(int) * h->row_start.size());
+  f.row_units = take(sizeof(int) * h->row_units.size());
+  f.W64 = take(sp ? sizeof(double) * h->steps * h->PW64 : 0);
+  f.W32 = take(sp && h->precision == SGS_FP32 ? sizeof(float) * h->steps * h->PW32 : 0);
+  size_t cpl = sizeof(double2);
+  size_t spec = sp ? (size_t)G * n * n * n * kLanes * cpl : 0;
+  f.st1a = take(sp ? (size_t)C * N * N * n * cpl : 0);
+  f.st1b = take(sp ? (size_t)C * N * N * n * cpl : 0);
+  f.st2a = take(sp ? (size_t)C * N * n * n * cpl : 0);
+  f.st2b = take(sp ? (size_t)C * N * n * n * cpl : 0);
+  f.ahat = take(spec);
+  f.bhat = take(spec);
+  f.qhat = take(spec);
+  f.partial = take(sp ? U * G * n * kLanes * cpl : 0);
+  f.end = o;
+  h->ws_bytes = o;
+}
+
+int check_problem(const sgs_problem& p) {
+  if (p.space_dim != 1) return p.space_dim == 2 ? SGS_ERR_UNSUPPORTED : SGS_ERR_ARG;
+  if (p.nx < 1 || !(p.x_hi > p.x_lo)) return SGS_ERR_ARG;
+  if (!valid_nv(p.nv) || !(p.v_max > 0.0)) return SGS_ERR_ARG;
+  if (p.collision < SGS_MAXWELL || p.collision > SGS_BGK) return SGS_ERR_ARG;
+  if (!(p.b0 > 0.0) || !(p.eps > 0.0)) return SGS_ERR_ARG;
+  if (p.precision != SGS_FP64 && p.precision != SGS_FP32) return SGS_ERR_ARG;
+  if (p.inner_method != SGS_PFP && p.inner_method != SGS_FP) return SGS_ERR_ARG;
+  if (p.inner_max < 0 || p.inner_fixed < 0 || p.newton_max < 1) return SGS_ERR_ARG;
+  for (int s = 0; s < 2; s++) {
+    if (p.bc[s].kind != SGS_DIFFUSE && p.bc[s].kind != SGS_INFLOW) return SGS_ERR_ARG;
+    if (!(p.bc[s].T > 0.0)) return SGS_ERR_ARG;
+    if (p.bc[s].kind == SGS_INFLOW && !(p.bc[s].rho > 0.0)) return SGS_ERR_ARG;
+    if (p.bc[s].kind == SGS_DIFFUSE && p.bc[s].u[0] != 0.0) return SGS_ERR_UNSUPPORTED;  // tangential walls only
+  }
+  return SGS_OK;
+}
+
+void fill_inst(const sgs_problem& p, int N, double dv, InstDev& I) {
+  memset(&I, 0, sizeof(I));
+  I.J = p.nx;
+  I.collision = p.collision;
+  I.dx = (p.x_hi - p.x_lo) / p.nx;
+  I.eps = p.eps;
+  I.b0 = p.b0;
+  I.total_mass = p.total_mass;
+  I.inner_tol = p.inner_tol;
+  I.inner_max = p.inner_max;
+  I.inner_fixed = p.inner_fixed;
+  I.inner_method = p.inner_method;
+  I.newton_max = p.newton_max;
+  I.newton_tol = p.newton_tol;
+  double w = dv * dv * dv;
+  for (int s = 0; s < 2; s++) {
+    const sgs_bc& b = p.bc[s];
+    I.bc_kind[s] = b.kind;
+    I.bc_rho[s] = b.rho;
+    double T = b.T;
+    double norm = 1.0 / (2.0 * kPi * T * std::sqrt(2.0 * kPi * T));
+    for (int d = 0; d < 3; d++)
+      for (int i = 0; i < N; i++) {
+        double v = node(i, N, dv);
+        double x = std::exp(-(v - b.u[d]) * (v - b.u[d]) / (2.0 * T));
+        if (d == 0) {
+          bool incoming = s == 0 ? v > 0.0 : v < 0.0;
+          x = incoming ? norm * x : 0.0;
+        }
+        I.wall[s][d][i] = x;
+      }
+    // sum over incoming v of w v1 Mhat
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int i = 0; i < N; i++) {
+      s1 += node(i, N, dv) * I.wall[s][0][i];
+      s2 += I.wall[s][1][i];
+      s3 += I.wall[s][2][i];
+    }
+    I.wall_denom[s] = w * s1 * s2 * s3;
+  }
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return SGS_OK;
+  fprintf(stderr, "sgs: CUDA error: %s\n", cudaGetErrorString(e));
+  return SGS_ERR_CUDA;
+}
+
+AuxArgs aux_args(const sgs_handle* h) {
+  AuxArgs a;
+  a.inst = h->at<InstDev>(h->off.inst);
+  a.n_inst = h->n_inst;
+  a.N = h->N;
+  a.C = h->C;
+  a.dv = h->dv;
+  a.cell_off = h->at<long long>(h->off.cell_off);
+  a.cell_inst = h->at<int>(h->off.cell_inst);
+  a.scratch = h->at<double>(h->off.scratch);
+  return a;
+}
+
+CellTables cell_tables(const sgs_handle* h) {
+  CellTables ct;
+  ct.inst = h->at<InstDev>(h->off.inst);
+  ct.cell_off = h->at<long long>(h->off.cell_off);
+  ct.cell_inst = h->at<int>(h->off.cell_inst);
+  return ct;
+}
+
+template <typename T>
+CollideCtx<T> collide_ctx(const sgs_handle* h) {
+  typedef typename CplxOf<T>::type CT;
+  CollideCtx<T> x;
+  x.N = h->N;
+  x.C = h->C;
+  x.H = h->H;
+  x.NW = h->NW;
+  x.n_units = (int)h->units.size();
+  x.dv = h->dv;
+  x.ct = cell_tables(h);
+  x.theta = h->at<double>(h->off.theta);
+  x.nu = h->at<double>(h->off.nu);
+  x.sb.tw_cos = h->at<double>(h->off.tw_cos);
+  x.sb.tw_sin = h->at<double>(h->off.tw_sin);
+  x.sb.st1a = h->at<CT>(h->off.st1a);
+  x.sb.st1b = h->at<CT>(h->off.st1b);
+  x.sb.st2a = h->at<CT>(h->off.st2a);
+  x.sb.st2b = h->at<CT>(h->off.st2b);
+  x.sb.ahat = h->at<CT>(h->off.ahat);
+  x.sb.bhat = h->at<CT>(h->off.bhat);
+  x.sb.qhat = h->at<CT>(h->off.qhat);
+  x.sum.units = h->at<int4>(h->off.units);
+  x.sum.unit_step0 = h->at<long long>(h->off.step0);
+  x.sum.W = sizeof(T) == 8 ? h->at<T>(h->off.W64) : h->at<T>(h->off.W32);
+  x.sum.ahat = x.sb.ahat;
+  x.sum.bhat = x.sb.bhat;
+  x.sum.partial = h->at<CT>(h->off.partial);
+  x.sum.G = h->G;
+  x.sum.cnt = h->at<Counters>(h->off.cnt);
+  x.sum.spin_max = h->spin_max;
+  x.red.row_k = h->at<int2>(h->off.row_k);
+  x.red.row_start = h->at<int>(h->off.row_start);
+  x.red.row_units = h->at<int>(h->off.row_units);
+  x.red.partial = x.sum.partial;
+  x.red.qhat = x.sb.qhat;
+  x.red.n = h->n;
+  x.red.G = h->G;
+  x.red.n_rows = (int)h->row_k.size();
+  return x;
+}
+
+int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int precision, cudaStream_t st) {
+  CellTables ct = cell_tables(h);
+  double* theta = h->at<double>(h->off.theta);
+  double* nu = h->at<double>(h->off.nu);
+  const sgs_problem& p0 = h->prob[0];
+  cudaError_t e = launch_moments(f, ct, h->C, h->N, h->dv, p0.newton_tol, p0.newton_max, theta, nu,
+                                 h->at<Counters>(h->off.cnt), st);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!h->spectral) return cuda_status(launch_collide_bgk(f, ct, h->C, h->N, h->dv, theta, nu, Q, P, st));
+  if (precision == SGS_FP32) {
+    if (h->off.W32 == h->off.st1a) return SGS_ERR_ARG;  // FP32 tables not built
+    return cuda_status(launch_collide_spectral<float>(f, Q, P, collide_ctx<float>(h), st));
+  }
+  return cuda_status(launch_collide_spectral<double>(f, Q, P, collide_ctx<double>(h), st));
+}
+
+int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int dir, cudaStream_t st) {
+  SweepArgs a;
+  a.inst = h->at<InstDev>(h->off.inst);
+  a.n_inst = h->n_inst;
+  a.f = f;
+  a.P = P;
+  a.rhs = rhs;
+  a.nu = h->at<double>(h->off.nu);
+  a.cnt = h->at<Counters>(h->off.cnt);
+  a.N = h->N;
+  a.dv = h->dv;
+  a.dir = dir;
+  return cuda_status(launch_sweep(a, h->sweep_cluster, h->sweep_tpb, st));
+}
+
+}  // namespace
+
+extern "C" {
+
+int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t* workspace_bytes) {
+  if (!problems || n_inst < 1 || !out) return SGS_ERR_ARG;
+  *out = nullptr;
+  for (int q = 0; q < n_inst; q++) {
+    int r = check_problem(problems[q]);
+    if (r != SGS_OK) return r;
+    if (problems[q].nv != problems[0].nv || problems[q].v_max != problems[0].v_max ||
+        problems[q].precision != problems[0].precision || problems[q].b0 != problems[0].b0 ||
+        (problems[q].collision == SGS_BGK) != (problems[0].collision == SGS_BGK) ||
+        (problems[q].collision != SGS_BGK && problems[q].collision != problems[0].collision))
+      return SGS_ERR_UNSUPPORTED;
+  }
+  sgs_handle* h = new (std::nothrow) sgs_handle();
+  if (!h) return SGS_ERR_NOMEM;
+  h->n_inst = n_inst;
+  h->prob.assign(problems, problems + n_inst);
+  h->N = problems[0].nv;
+  h->L = problems[0].v_max;
+  h->dv = 2.0 * h->L / h->N;
+  h->precision = problems[0].precision;
+  h->spectral = problems[0].collision != SGS_BGK;
+  long long K = (long long)h->N * h->N * h->N;
+  h->inst.resize(n_inst);
+  long long off = 0;
+  int cell = 0;
+  for (int q = 0; q < n_inst; q++) {
+    fill_inst(problems[q], h->N, h->dv, h->inst[q]);
+    h->inst[q].f_off = off;
+    h->inst[q].cell0 = cell;
+    for (int j = 0; j < problems[q].nx; j++) {
+      h->cell_off.push_back(off + j * K);
+      h->cell_inst.push_back(q);
+    }
+    off += (long long)problems[q].nx * K;
+    cell += problems[q].nx;
+  }
+  h->field = off;
+  h->C = cell;
+  int r = plan(h);
+  if (r != SGS_OK) {
+    delete h;
+    return r;
+  }
+  layout(h);
+  h->sweep_cluster = sweep_cluster_for(h->N);
+  *out = h;
+  if (workspace_bytes) *workspace_bytes = h->ws_bytes;
+  return SGS_OK;
+}
+
+int sgs_bind_workspace(sgs_handle* h, void* device_ptr, size_t bytes) {
+  if (!h || !device_ptr) return SGS_ERR_ARG;
+  if (bytes < h->ws_bytes) return SGS_ERR_WORKSPACE;
+  if (((uintptr_t)device_ptr) % kAlign) return SGS_ERR_ARG;
+  h->ws = (char*)device_ptr;
+  auto up = [&](size_t o, const void* src, size_t n) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpy(h->ws + o, src, n, cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = cudaSuccess;
+  std::vector<int4> u4;
+  std::vector<long long> s0;
+  for (auto& x : h->units) {
+    u4.push_back(make_int4(x.k1, x.k2, x.m1lo, x.m1hi));
+    s0.push_back(x.step0);
+  }
+#define SGS_UP(field, vec) \
+  if (e == cudaSuccess) e = up(h->off.field, vec.data(), sizeof(vec[0]) * vec.size())
+  SGS_UP(inst, h->inst);
+  SGS_UP(cell_off, h->cell_off);
+  SGS_UP(cell_inst, h->cell_inst);
+  SGS_UP(tw_cos, h->tw_cos);
+  SGS_UP(tw_sin, h->tw_sin);
+  SGS_UP(G, h->Gtab);
+  SGS_UP(Lo, h->Lo);
+  SGS_UP(units, u4);
+  SGS_UP(step0, s0);
+  SGS_UP(row_k, h->row_k);
+  SGS_UP(row_start, h->row_start);
+  SGS_UP(row_units, h->row_units);
+#undef SGS_UP
+  if (e == cudaSuccess) e = cudaMemset(h->ws + h->off.cnt, 0, sizeof(Counters) * h->n_inst);
+  if (e == cudaSuccess && h->spectral) {
+    // spectral lanes beyond the last cell must hold zeros
+    e = cudaMemset(h->ws + h->off.ahat, 0, h->off.qhat - h->off.ahat);
+    if (e == cudaSuccess)
+      e = launch_build_weights<double>(h->at<int4>(h->off.units), h->at<long long>(h->off.step0), (int)h->units.size(),
+                                       h->H, h->PW64, h->at<double>(h->off.G), h->nb, h->at<double>(h->off.Lo),
+                                       h->at<double>(h->off.W64), 0);
+    if (e == cudaSuccess && h->precision == SGS_FP32)
+      e = launch_build_weights<float>(h->at<int4>(h->off.units), h->at<long long>(h->off.step0), (int)h->units.size(),
+                                      h->H, h->PW32, h->at<double>(h->off.G), h->nb, h->at<double>(h->off.Lo),
+                                      h->at<float>(h->off.W32), 0);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return cuda_status(e);
+}
+
+int sgs_layout(const sgs_handle* h, int inst, size_t* f_offset, int* n_cells, int* nv) {
+  if (!h || inst < 0 || inst >= h->n_inst) return SGS_ERR_ARG;
+  if (f_offset) *f_offset = (size_t)h->inst[inst].f_off;
+  if (n_cells) *n_cells = h->inst[inst].J;
+  if (nv) *nv = h->N;
+  return SGS_OK;
+}
+
+size_t sgs_field_elems(const sgs_handle* h) { return h ? (size_t)h->field : 0; }
+
+int sgs_collide(sgs_handle* h, const double* f, double* Q, double* P, void* stream) {
+  if (!h || !f) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return collide_impl(h, f, Q, P, h->precision, as_stream(stream));
+}
+
+int sgs_collide_prec(sgs_handle* h, const double* f, double* Q, double* P, int precision, void* stream) {
+  if (!h || !f || (precision != SGS_FP64 && precision != SGS_FP32)) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  if (precision == SGS_FP32 && h->precision != SGS_FP32) return SGS_ERR_ARG;
+  return collide_impl(h, f, Q, P, precision, as_stream(stream));
+}
+
+int sgs_sweep_forward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream) {
+  if (!h || !f || !P) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return sweep_impl(h, f, P, rhs, +1, as_stream(stream));
+}
+
+int sgs_sweep_backward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream) {
+  if (!h || !f || !P) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return sweep_impl(h, f, P, rhs, -1, as_stream(stream));
+}
+
+int sgs_rescale(sgs_handle* h, double* f, void* stream) {
+  if (!h || !f) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return cuda_status(launch_rescale(aux_args(h), f, as_stream(stream)));
+}
+
+int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, void* stream) {
+  if (!h || !f || !Q || !res) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return cuda_status(launch_residual(aux_args(h), f, Q, rhs, res, as_stream(stream)));
+}
+
+int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, int flags, double* res, void* stream) {
+  if (!h || !f || !P) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  int r;
+  if (!(flags & SGS_IT_P_VALID)) {
+    r = collide_impl(h, f, nullptr, P, h->precision, st);
+    if (r) return r;
+  }
+  if ((r = sweep_impl(h, f, P, nullptr, +1, st))) return r;
+  if ((r = collide_impl(h, f, nullptr, P, h->precision, st))) return r;
+  if ((r = sweep_impl(h, f, P, nullptr, -1, st))) return r;
+  if ((r = cuda_status(launch_rescale(aux_args(h), f, st)))) return r;
+  if (flags & SGS_IT_EVAL) {
+    if (!Q) return SGS_ERR_ARG;
+    if ((r = collide_impl(h, f, Q, P, h->precision, st))) return r;
+    if (res && (r = cuda_status(launch_residual(aux_args(h), f, Q, nullptr, res, st)))) return r;
+  }
+  return SGS_OK;
+}
+
+int sgs_vcycle(sgs_handle* h, double* f, int levels, int pre, int post, int coarse_iters, void* stream) {
+  (void)f;
+  (void)levels;
+  (void)pre;
+  (void)post;
+  (void)coarse_iters;
+  (void)stream;
+  if (!h) return SGS_ERR_ARG;
+  return SGS_ERR_UNSUPPORTED;
+}
+
+int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream) {
+  if (!h || !out) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+  if (e != cudaSuccess) return cuda_status(e);
+  std::vector<Counters> c(h->n_inst);
+  e = cudaMemcpy(c.data(), h->ws + h->off.cnt, sizeof(Counters) * h->n_inst, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  memset(out, 0, sizeof(*out));
+  for (auto& x : c) {
+    out->status |= x.status;
+    out->visits += x.visits;
+    out->inner_iters += x.inner_iters;
+    out->newton_iters += x.newton_iters;
+    out->newton_solves += x.newton_solves;
+    out->fallbacks += x.fallbacks;
+  }
+  return SGS_OK;
+}
+
+int sgs_reset_stats(sgs_handle* h, void* stream) {
+  if (!h) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return cuda_status(cudaMemsetAsync(h->ws + h->off.cnt, 0, sizeof(Counters) * h->n_inst, as_stream(stream)));
+}
+
+void sgs_destroy(sgs_handle* h) { delete h; }
+
+const char* sgs_strerror(int code) {
+  switch (code) {
+    case SGS_OK: return "ok";
+    case SGS_ERR_ARG: return "invalid argument";
+    case SGS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SGS_ERR_CUDA: return "CUDA runtime error";
+    case SGS_ERR_WORKSPACE: return "workspace missing or too small";
+    case SGS_ERR_NOMEM: return "host allocation failed";
+  }
+  return "unknown error";
+}
+
+double sgs_host_weight(int nv, double v_max, int collision, double b0, long long a2, long long b2) {
+  return weight_G(nv, v_max, collision, b0, a2, b2);
+}
+
+}  // extern "C"

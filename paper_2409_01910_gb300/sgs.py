@@ -1,0 +1,253 @@
+"""Thin Python binding of the C ABI in include/sgs.h (argument marshalling only).
+
+PyTorch provides device memory and streams; every step of the solver runs in the CUDA
+library ``_build/libsgs.so``. There is no CPU fallback: if the library cannot be loaded
+the calls raise.
+
+Names follow the C entry points: ``setup``, ``collide``, ``sweep_forward``,
+``sweep_backward``, ``rescale``, ``residual``, ``iterate``, ``vcycle``, ``read_status``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE, ERR_NOMEM = 0, -1, -2, -3, -4, -5
+ST_NEWTON_FAIL, ST_INNER_CAP, ST_NONPOSITIVE, ST_NONFINITE, ST_TIMEOUT = 1, 2, 4, 8, 16
+MAXWELL, HARD_SPHERE, BGK = 0, 1, 2
+DIFFUSE, INFLOW = 0, 1
+FP64, FP32 = 0, 1
+PFP, FP = 0, 1
+IT_P_VALID, IT_EVAL = 1, 2
+
+
+class _BC(C.Structure):
+    _fields_ = [("kind", C.c_int), ("rho", C.c_double), ("u", C.c_double * 3), ("T", C.c_double)]
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("space_dim", C.c_int),
+        ("nx", C.c_int),
+        ("x_lo", C.c_double),
+        ("x_hi", C.c_double),
+        ("nv", C.c_int),
+        ("v_max", C.c_double),
+        ("collision", C.c_int),
+        ("b0", C.c_double),
+        ("eps", C.c_double),
+        ("bc", _BC * 2),
+        ("total_mass", C.c_double),
+        ("precision", C.c_int),
+        ("inner_tol", C.c_double),
+        ("inner_max", C.c_int),
+        ("inner_fixed", C.c_int),
+        ("newton_tol", C.c_double),
+        ("newton_max", C.c_int),
+        ("inner_method", C.c_int),
+    ]
+
+
+class _Stats(C.Structure):
+    _fields_ = [
+        ("status", C.c_uint),
+        ("visits", C.c_ulonglong),
+        ("inner_iters", C.c_ulonglong),
+        ("newton_iters", C.c_ulonglong),
+        ("newton_solves", C.c_ulonglong),
+        ("fallbacks", C.c_ulonglong),
+    ]
+
+
+@dataclass
+class Problem:
+    """Python mirror of sgs_problem (1-D space, 3-D velocity)."""
+
+    nx: int = 16
+    x_lo: float = 0.0
+    x_hi: float = 1.0
+    nv: int = 16
+    v_max: float = 6.0
+    collision: int = MAXWELL
+    b0: float = 1.0 / (4.0 * 3.141592653589793)
+    eps: float = 1.0
+    bc_kind: Sequence[int] = (DIFFUSE, DIFFUSE)
+    bc_rho: Sequence[float] = (1.0, 1.0)
+    bc_u: Sequence[Sequence[float]] = ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0))
+    bc_T: Sequence[float] = (1.0, 2.0)
+    total_mass: float = 1.0
+    precision: int = FP64
+    inner_tol: float = 1e-8
+    inner_max: int = 200
+    inner_fixed: int = 0
+    newton_tol: float = 1e-10
+    newton_max: int = 50
+    inner_method: int = PFP
+    space_dim: int = 1
+
+    def c(self) -> _Problem:
+        p = _Problem()
+        for name in ("space_dim", "nx", "x_lo", "x_hi", "nv", "v_max", "collision", "b0", "eps", "total_mass",
+                     "precision", "inner_tol", "inner_max", "inner_fixed", "newton_tol", "newton_max",
+                     "inner_method"):
+            setattr(p, name, getattr(self, name))
+        for s in range(2):
+            p.bc[s].kind = self.bc_kind[s]
+            p.bc[s].rho = self.bc_rho[s]
+            p.bc[s].T = self.bc_T[s]
+            for d in range(3):
+                p.bc[s].u[d] = self.bc_u[s][d]
+        return p
+
+
+_lib = None
+
+
+def lib(build: bool = True):
+    """Loads the CUDA library (building it first if asked and needed). Raises if absent."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not found at {path}; run paper_2409_01910_gb300.build.build()")
+        L = C.CDLL(path)
+        vp, d = C.c_void_p, C.POINTER(C.c_double)
+        sig = {
+            "sgs_setup": (C.c_int, [C.POINTER(_Problem), C.c_int, C.POINTER(vp), C.POINTER(C.c_size_t)]),
+            "sgs_bind_workspace": (C.c_int, [vp, vp, C.c_size_t]),
+            "sgs_layout": (C.c_int, [vp, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "sgs_field_elems": (C.c_size_t, [vp]),
+            "sgs_collide": (C.c_int, [vp, vp, vp, vp, vp]),
+            "sgs_collide_prec": (C.c_int, [vp, vp, vp, vp, C.c_int, vp]),
+            "sgs_sweep_forward": (C.c_int, [vp, vp, vp, vp, vp]),
+            "sgs_sweep_backward": (C.c_int, [vp, vp, vp, vp, vp]),
+            "sgs_rescale": (C.c_int, [vp, vp, vp]),
+            "sgs_residual": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+            "sgs_iterate": (C.c_int, [vp, vp, vp, vp, C.c_int, vp, vp]),
+            "sgs_vcycle": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]),
+            "sgs_read_status": (C.c_int, [vp, C.POINTER(_Stats), vp]),
+            "sgs_reset_stats": (C.c_int, [vp, vp]),
+            "sgs_destroy": (None, [vp]),
+            "sgs_strerror": (C.c_char_p, [C.c_int]),
+            "sgs_host_weight": (C.c_double, [C.c_int, C.c_double, C.c_int, C.c_double, C.c_longlong, C.c_longlong]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SGSError(RuntimeError):
+    pass
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise SGSError(f"{what}: {lib().sgs_strerror(code).decode()} ({code})")
+
+
+def host_weight(nv, v_max, collision, b0, a2, b2) -> float:
+    return lib().sgs_host_weight(nv, v_max, collision, b0, a2, b2)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    import torch
+
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "fields are contiguous FP64 CUDA tensors"
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Solver:
+    """Owns one library handle and its torch-allocated workspace."""
+
+    def __init__(self, problems, device="cuda"):
+        import torch
+
+        if isinstance(problems, Problem):
+            problems = [problems]
+        self.problems = list(problems)
+        arr = (_Problem * len(self.problems))(*[p.c() for p in self.problems])
+        h = C.c_void_p()
+        ws = C.c_size_t()
+        _check(lib().sgs_setup(arr, len(self.problems), C.byref(h), C.byref(ws)), "sgs_setup")
+        self.h = h
+        self.workspace = torch.empty(max(int(ws.value), 256), dtype=torch.uint8, device=device)
+        _check(lib().sgs_bind_workspace(self.h, self.workspace.data_ptr(), self.workspace.numel()),
+               "sgs_bind_workspace")
+        self.n_inst = len(self.problems)
+        self.field_elems = int(lib().sgs_field_elems(self.h))
+        self.device = device
+
+    def layout(self, inst: int):
+        off, J, nv = C.c_size_t(), C.c_int(), C.c_int()
+        _check(lib().sgs_layout(self.h, inst, C.byref(off), C.byref(J), C.byref(nv)), "sgs_layout")
+        return int(off.value), int(J.value), int(nv.value)
+
+    def field(self):
+        import torch
+
+        return torch.zeros(self.field_elems, dtype=torch.float64, device=self.device)
+
+    def view(self, fld, inst: int):
+        off, J, N = self.layout(inst)
+        return fld[off: off + J * N ** 3].view(J, N, N, N)
+
+    def collide(self, f, Q=None, P=None, precision=None, stream=None):
+        if precision is None:
+            _check(lib().sgs_collide(self.h, _ptr(f), _ptr(Q), _ptr(P), _stream(stream)), "sgs_collide")
+        else:
+            _check(lib().sgs_collide_prec(self.h, _ptr(f), _ptr(Q), _ptr(P), precision, _stream(stream)),
+                   "sgs_collide_prec")
+
+    def sweep_forward(self, f, P, rhs=None, stream=None):
+        _check(lib().sgs_sweep_forward(self.h, _ptr(f), _ptr(P), _ptr(rhs), _stream(stream)), "sgs_sweep_forward")
+
+    def sweep_backward(self, f, P, rhs=None, stream=None):
+        _check(lib().sgs_sweep_backward(self.h, _ptr(f), _ptr(P), _ptr(rhs), _stream(stream)), "sgs_sweep_backward")
+
+    def rescale(self, f, stream=None):
+        _check(lib().sgs_rescale(self.h, _ptr(f), _stream(stream)), "sgs_rescale")
+
+    def residual(self, f, Q, res, rhs=None, stream=None):
+        _check(lib().sgs_residual(self.h, _ptr(f), _ptr(Q), _ptr(rhs), _ptr(res), _stream(stream)), "sgs_residual")
+
+    def iterate(self, f, Q, P, flags=0, res=None, stream=None):
+        _check(lib().sgs_iterate(self.h, _ptr(f), _ptr(Q), _ptr(P), flags, _ptr(res), _stream(stream)),
+               "sgs_iterate")
+
+    def vcycle(self, f, levels, pre=1, post=1, coarse_iters=10, stream=None):
+        _check(lib().sgs_vcycle(self.h, _ptr(f), levels, pre, post, coarse_iters, _stream(stream)), "sgs_vcycle")
+
+    def read_status(self, stream=None) -> dict:
+        st = _Stats()
+        _check(lib().sgs_read_status(self.h, C.byref(st), _stream(stream)), "sgs_read_status")
+        return {k: int(getattr(st, k)) for k, _ in _Stats._fields_}
+
+    def reset_stats(self, stream=None):
+        _check(lib().sgs_reset_stats(self.h, _stream(stream)), "sgs_reset_stats")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sgs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
