@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the SGS-PFP solver on GB300: cell updates per second.
+
+Workload: planar heat transfer, 64 cells on [0, 1], 32^3 velocities on [-8, 8]^3, Maxwell
+molecules (B = 1/(4 pi)), eps = 0.01, diffuse walls with seeded temperatures
+T_L ~ U[0.8, 1.2], T_R ~ U[1.5, 2.5] (seed 0), synthetic initial state.
+
+A step is one SGS iteration of the mixed solver: forward scan, collision, backward scan,
+mass rescale, collision (the collision sums in FP32, moments/Newton/residual in FP64), with
+the FP64 defect-correction evaluation (FP64 collision + FP64 residual + right-hand side)
+every --dc-every steps. One cell update is one cell visit of a scan; a step makes 2 x 64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 runs independent replicas (one per GPU, launched by torchrun): the method is a
+sequential scan per problem, so work is replicated, not sharded ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s (SGS-PFP, mixed FP32 collision + FP64 defect correction)"
+UNIT = "cell-updates/s"
+L2_BYTES = 129 * 2**20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--dc-every", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- native
+def workload():
+    from paper_2409_01910_gb300 import inputs as I
+
+    return I.heat_64cells_32v(seed=0)
+
+
+def make_solver(wl, precision):
+    from paper_2409_01910_gb300 import sgs
+
+    p = sgs.Problem(nx=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, nv=wl.N, v_max=wl.L, eps=wl.eps,
+                    bc_T=(wl.T_left, wl.T_right), total_mass=wl.total_mass, precision=precision)
+    return sgs.Solver(p)
+
+
+def pairs_per_cell(N):
+    h = N // 2 - 1
+    return (3 * h * h + 3 * h + 1) ** 3
+
+
+def run_native(args, rank, world, local):
+    import torch
+
+    from paper_2409_01910_gb300 import sgs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    wl = workload()
+    f0 = torch.from_numpy(wl.initial_state().reshape(-1)).to(dev)
+    s = make_solver(wl, sgs.FP32)
+    f = f0.clone()
+    Q, P, rhs = s.field(), s.field(), s.field()
+    res_hi = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    visits_per_step = 2 * wl.J
+
+    def step(i):
+        if i % args.dc_every == 0:
+            s.dc_step(f, Q, P, rhs, 0, res=res_hi)
+        s.iterate(f, Q, P, rhs=rhs, flags=sgs.IT_P_VALID | sgs.IT_EVAL)
+
+    # warm-up (untimed): the first DC evaluation also initialises P
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    s.profile(True)
+    s.profile_read()
+    launches0 = s.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[i][0].record(stream)
+            step(args.warmup + i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = s.launch_count() - launches0
+    prof = s.profile_read()
+    s.profile(False)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    ms_total = float(sum(ms_steps))
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * visits_per_step * args.steps / (ms_total * 1e-3)
+    status = s.read_status()
+
+    # dominant kernel class and its roofline
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    dom = max(prof, key=lambda k: prof[k][0])
+    roof = roofline(dom, prof, wl, s, sm_mhz)
+
+    # end to end through the C ABI with host buffers: H2D of the state (f, P), one step,
+    # D2H of the step's residual
+    e2e = None
+    if rank == 0 or world > 1:
+        e2e = end_to_end(s, f, Q, P, rhs, wl, args, stream)
+
+    # plain FP64 GPU form for comparison (same step, FP64 collision sum and FP64 scan)
+    fp64 = fp64_form(wl, args, f0, dev, stream)
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "cells": wl.J, "nv": wl.N, "v_max": wl.L, "eps": wl.eps,
+                       "T_walls": [round(wl.T_left, 6), round(wl.T_right, 6)], "collision": "maxwell",
+                       "precision": "mixed: FP32 collision sum + FP32 scan, FP64 moments/residual/defect correction",
+                       "dc_every": args.dc_every, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+            "fp64": fp64,
+            "device_status": status["status"],
+            "inner_iters_per_visit": status["inner_iters"] / max(1, status["visits"]),
+        }
+    return out
+
+
+def roofline(dom, prof, wl, s, sm_mhz):
+    ms, n = prof[dom]
+    avg = ms / max(1, n)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    K = wl.N ** 3
+    if dom == "sum":
+        # algorithmic work: 10 flops per mode pair over the Hermitian half, 64 cells
+        flops = 10 * 0.5 * pairs_per_cell(wl.N) * wl.J
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+        ach = flops / (avg * 1e-3) / 1e12
+        return {"kernel": "k_sum<float> (direct spectral sum)", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
+    if dom == "sweep":
+        byts = 5 * K * 8 * wl.J  # read f_{j-1}, f_j, f_{j+1}, P_j; write f_j per visit
+        ach = byts / (avg * 1e-3) / 1e9
+        return {"kernel": "k_sweep<float> (persistent SGS scan)", "bound": "hbm", "achieved": ach,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    byts = 2 * K * 8 * wl.J
+    ach = byts / (avg * 1e-3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": None}
+
+
+def end_to_end(s, f, Q, P, rhs, wl, args, stream):
+    import torch
+
+    from paper_2409_01910_gb300 import sgs
+
+    hf = f.cpu().pin_memory()
+    hP = P.cpu().pin_memory()
+    hres = torch.zeros(1, dtype=torch.float64).pin_memory()
+    res = torch.zeros(1, dtype=torch.float64, device=f.device)
+    steps = max(3, args.steps // 2)
+    for _ in range(2):
+        f.copy_(hf, non_blocking=True)
+        P.copy_(hP, non_blocking=True)
+        s.iterate(f, Q, P, rhs=rhs, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
+        hres.copy_(res, non_blocking=True)
+        torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for _ in range(steps):
+        t0.record(stream)
+        f.copy_(hf, non_blocking=True)
+        P.copy_(hP, non_blocking=True)
+        s.iterate(f, Q, P, rhs=rhs, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
+        hres.copy_(res, non_blocking=True)
+        t1.record(stream)
+        t1.synchronize()
+        total += t0.elapsed_time(t1)
+    ms = total / steps
+    return {"value": 2 * wl.J / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 2 * hf.numel() * 8,
+            "d2h_bytes_per_step": 8, "ms_per_step": ms,
+            "note": "state (f, P) copied from pinned host memory and the residual read back every step"}
+
+
+def fp64_form(wl, args, f0, dev, stream):
+    import torch
+
+    from paper_2409_01910_gb300 import sgs
+
+    s = make_solver(wl, sgs.FP64)
+    f = f0.clone()
+    Q, P = s.field(), s.field()
+    res = torch.zeros(1, dtype=torch.float64, device=dev)
+    s.iterate(f, Q, P, flags=sgs.IT_EVAL, res=res)
+    torch.cuda.synchronize()
+    s.profile(True)
+    s.profile_read()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.fp64_steps):
+        s.iterate(f, Q, P, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.fp64_steps
+    prof = s.profile_read()
+    s.close()
+    return {"value": 2 * wl.J / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": args.fp64_steps,
+            "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()}}
+
+
+# ------------------------------------------------------------------------------- oracle
+def oracle_sample(wl, n_collide_cells=None, n_visits=2):
+    """Times the FP64 oracle on a bounded sample of the workload: the collision step of a
+    few cells (threads over cells) and a few cell visits. Returns seconds per cell update
+    (one cell visit plus one cell's collision evaluation)."""
+    from oracle import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    S = n_collide_cells or min(8, cores)
+    prob = O.Problem(N=wl.N, L=wl.L, J=wl.J, eps=wl.eps, bc_T=(wl.T_left, wl.T_right), total_mass=wl.total_mass)
+    f = wl.initial_state()
+    O.collide(prob, f[:1])  # builds the weight table (not timed)
+    t = time.perf_counter()
+    Qc, Pc, nu = O.collide(prob, f[:S])
+    t_coll = (time.perf_counter() - t) / S
+    dx = prob.dx
+    V = (np.arange(wl.N) - wl.N // 2 + 1) * (2 * wl.L / wl.N)
+    vp = np.maximum(V, 0)[:, None, None]
+    vm = np.minimum(V, 0)[:, None, None]
+    t = time.perf_counter()
+    for j in range(1, 1 + n_visits):
+        r = (-vp * f[j - 1] + vm * f[j + 1]) / dx - Pc[j] / wl.eps
+        O.cell_solve(prob, dx, r, nu[j], f[j])
+    t_visit = (time.perf_counter() - t) / n_visits
+    return t_coll + t_visit, cores, S, n_visits, t_coll, t_visit
+
+
+def cpu_baseline(wl):
+    sec, cores, S, nv, tc, tv = oracle_sample(wl)
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 C oracle: collision step of {S} cells (OpenMP over cells, {tc:.2f} s/cell) + "
+                       f"{nv} cell visits ({tv:.2f} s/visit) of the same workload; value = 1/(per-cell collision + "
+                       f"per-visit time)")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    wl = workload()
+    times = []
+    for i in range(args.warmup + args.steps):
+        sec, cores, S, nv, tc, tv = oracle_sample(wl, n_visits=1)
+        if i >= args.warmup:
+            times.append(sec)
+    sec = sum(times) / len(times)
+    value = 1.0 / sec
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "cells": wl.J, "nv": wl.N, "eps": wl.eps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: collision step of min(8, cores) cells + 1 cell visit, FP64 C oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    import torch
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = run_native(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(workload())
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -143,12 +143,39 @@ int sgs_collide_prec(sgs_handle* h, const double* f, double* Q, double* P, int p
  * With both flags set, consecutive calls cost two collision evaluations per iteration. */
 #define SGS_IT_P_VALID 1
 #define SGS_IT_EVAL 2
-int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, int flags, double* res, void* stream);
+int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, const double* rhs, int flags, double* res,
+                void* stream);
+
+/* One step of FP64 defect correction for the mixed solver (handle set up with SGS_FP32):
+ *   Q = Q_FP64[f_k], res = FP64 residual of f_k (device, n_inst doubles, nullable),
+ *   rhs = R_lo(f_k) - R_hi(f_k) = (Q - Q_FP32[f_k]) / eps,
+ *   then lo_iters SGS iterations on R_lo(f) = rhs with the FP32 collision sum and the FP32
+ *   sweep, which return f_{k+1}. Q, P, rhs are caller-owned device fields (scratch). The
+ *   fixed point of the step solves the FP64 equations: R_hi(f) = 0. */
+int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, double* rhs, int lo_iters, double* res, void* stream);
 
 /* One FAS V-cycle (eq. (30)) on every instance: levels >= 2 grids with H = 2h (each level's
  * cell count must be even), pre/post SGS smoothing iterations, coarse_iters iterations on
  * the coarsest grid. Coarse fields live in the workspace. */
 int sgs_vcycle(sgs_handle* h, double* f, int levels, int pre, int post, int coarse_iters, void* stream);
+
+/* Kernel-time profiling. When enabled, every group of launches is bracketed by CUDA events
+ * recorded on the launching stream; sgs_profile_read synchronises on them and returns, per
+ * class, the summed milliseconds and the number of bracketed groups, then clears them.
+ * sgs_launch_count returns the number of kernels enqueued through the handle so far. */
+enum sgs_prof_class {
+  SGS_PROF_MOMENTS = 0,     /* moments + discrete Maxwellian of every cell */
+  SGS_PROF_DFT = 1,         /* forward DFT of f - M and f + M (3 kernels) */
+  SGS_PROF_SUM = 2,         /* direct spectral sum */
+  SGS_PROF_REDUCE_IDFT = 3, /* partial reduction + inverse DFT + P (4 kernels), or BGK */
+  SGS_PROF_SWEEP = 4,       /* persistent SGS scan */
+  SGS_PROF_RESIDUAL = 5,    /* outer residual */
+  SGS_PROF_RESCALE = 6,     /* mass rescale and the defect-correction right-hand side */
+  SGS_PROF_CLASSES = 7
+};
+int sgs_profile(sgs_handle* h, int enable);
+int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, int n_classes);
+unsigned long long sgs_launch_count(const sgs_handle* h);
 
 /* Synchronises the stream and reads the accumulated status and counters. */
 int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream);

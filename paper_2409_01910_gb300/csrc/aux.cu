@@ -138,6 +138,22 @@ cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Defect-correction right-hand side b = (Q_hi - Q_lo) / eps, in place over Q_lo.
+__global__ void __launch_bounds__(256) k_dc_rhs(AuxArgs a, const double* __restrict__ Qhi, double* Qlo_b) {
+  int c = blockIdx.x;
+  const InstDev& I = a.inst[a.cell_inst[c]];
+  double inv_eps = 1.0 / I.eps;
+  int K = a.N * a.N * a.N;
+  long long base = a.cell_off[c];
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < K; e += gridDim.y * blockDim.x)
+    Qlo_b[base + e] = (Qhi[base + e] - Qlo_b[base + e]) * inv_eps;
+}
+
+cudaError_t launch_dc_rhs(const AuxArgs& a, const double* Qhi, double* Qlo_b, cudaStream_t st) {
+  k_dc_rhs<<<dim3(a.C, 4), 256, 0, st>>>(a, Qhi, Qlo_b);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------------
 // Multigrid transfers on one instance's contiguous cells (K doubles per cell).
 // ---------------------------------------------------------------------------------------

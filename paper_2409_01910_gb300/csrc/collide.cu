@@ -59,9 +59,10 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ f, C
   }
   const InstDev& I = ct.inst[ct.cell_inst[c]];
   double th[5] = {0, 0, 0, 0, 0};
-  MaxwEval ev;
+  MaxwEval<double> ev;
   int it = -1;
-  if (continuum_guess(m, th)) it = maxwellian_newton(N, dv, w, false, 0.0, m, th, newton_tol, newton_max, ev);
+  if (continuum_guess<double>(m, th))
+    it = maxwellian_newton<double>(N, dv, w, false, 0.0, m, th, newton_tol, newton_max, ev);
   double rho = m[0];
   double T = (m[4] / rho - (m[1] * m[1] + m[2] * m[2] + m[3] * m[3]) / (rho * rho)) / 3.0;
   double nuv = 4.0 * kPi * I.b0 * rho;
@@ -616,7 +617,7 @@ cudaError_t launch_sum(const SumArgs<T>& a, int H, int NW, int n_units, cudaStre
 }
 
 template <typename T>
-cudaError_t launch_collide_spectral(const double* f, double* Q, double* P, const CollideCtx<T>& x, cudaStream_t st) {
+cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, cudaStream_t st) {
   int N = x.N, n = N - 1, C = x.C;
   cudaError_t e;
   size_t sm1 = dft_smem<T>(N, 0, 2 * N * N);
@@ -631,8 +632,18 @@ cudaError_t launch_collide_spectral(const double* f, double* Q, double* P, const
   if (e != cudaSuccess) return e;
   // groups beyond the last cell keep the zeros written at bind time
   k_dft_i1<T><<<dim3(C, n), 256, sm2, st>>>(x.sb, N);
-  e = launch_sum<T>(x.sum, x.H, x.NW, x.n_units, st);
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spectral_sum(const CollideCtx<T>& x, cudaStream_t st) {
+  return launch_sum<T>(x.sum, x.H, x.NW, x.n_units, st);
+}
+
+template <typename T>
+cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const CollideCtx<T>& x, cudaStream_t st) {
+  int N = x.N, n = N - 1, C = x.C;
+  cudaError_t e;
   k_sum_reduce<T><<<dim3(x.red.n_rows, x.red.G), 256, 0, st>>>(x.red);
   size_t sm3 = dft_smem<T>(N, n * n, 0);
   e = cudaFuncSetAttribute(k_idft_k1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
@@ -667,10 +678,14 @@ cudaError_t launch_build_weights(const int4* units, const long long* unit_step0,
   return cudaGetLastError();
 }
 
-template cudaError_t launch_collide_spectral<double>(const double*, double*, double*, const CollideCtx<double>&,
-                                                     cudaStream_t);
-template cudaError_t launch_collide_spectral<float>(const double*, double*, double*, const CollideCtx<float>&,
-                                                    cudaStream_t);
+template cudaError_t launch_dft<double>(const double*, const CollideCtx<double>&, cudaStream_t);
+template cudaError_t launch_dft<float>(const double*, const CollideCtx<float>&, cudaStream_t);
+template cudaError_t launch_spectral_sum<double>(const CollideCtx<double>&, cudaStream_t);
+template cudaError_t launch_spectral_sum<float>(const CollideCtx<float>&, cudaStream_t);
+template cudaError_t launch_reduce_idft<double>(const double*, double*, double*, const CollideCtx<double>&,
+                                                cudaStream_t);
+template cudaError_t launch_reduce_idft<float>(const double*, double*, double*, const CollideCtx<float>&,
+                                               cudaStream_t);
 template cudaError_t launch_build_weights<double>(const int4*, const long long*, int, int, int, const double*,
                                                   long long, const double*, double*, cudaStream_t);
 template cudaError_t launch_build_weights<float>(const int4*, const long long*, int, int, int, const double*,

@@ -49,14 +49,80 @@ struct Counters {
 __host__ __device__ inline double node(int i, int N, double dv) { return (double)(i - N / 2 + 1) * dv; }
 
 // ---------------------------------------------------------------------------------------
+// Double-float ("df64") arithmetic: a value is hi + lo with two FP32 numbers, |lo| <= ulp(hi)/2,
+// carried through error-free transformations (Knuth's two-sum, Dekker's fast two-sum, and the
+// FMA form of the exact product). Addition and multiplication keep about 48 significant bits
+// relative to the operands, enough for the cancellations of the cell equation, and run on the
+// FP32 pipes, which on this GPU have ~40x the FP64 throughput.
+// ---------------------------------------------------------------------------------------
+struct dfloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+  float s = a.hi + b.hi;
+  float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  return df_fast_two_sum(s, e);
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
+__device__ __forceinline__ dfloat& operator-=(dfloat& a, dfloat b) { return a = a - b; }
+
+// Conversions used by code templated on the arithmetic type E.
+template <typename E>
+__device__ __forceinline__ E cvt(double x);
+template <>
+__device__ __forceinline__ double cvt<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float cvt<float>(double x) { return (float)x; }
+template <>
+__device__ __forceinline__ dfloat cvt<dfloat>(double x) {
+  float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double tod(double x) { return x; }
+__device__ __forceinline__ double tod(float x) { return (double)x; }
+__device__ __forceinline__ double tod(dfloat x) { return (double)x.hi + (double)x.lo; }
+
+// exp evaluated in FP64 for double and df64, in FP32 for float
+template <typename E>
+__device__ __forceinline__ E exp_e(double x) {
+  return cvt<E>(exp(x));
+}
+template <>
+__device__ __forceinline__ float exp_e<float>(double x) {
+  return expf((float)x);
+}
+
+__device__ __forceinline__ double shfl_x(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_x(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ dfloat shfl_x(dfloat v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+// ---------------------------------------------------------------------------------------
 // Warp reductions (butterfly: every lane receives the total, in a fixed order).
 // ---------------------------------------------------------------------------------------
-template <int NV>
-__device__ inline void warp_allsum(double (&x)[NV]) {
+template <int NV, typename T>
+__device__ inline void warp_allsum(T (&x)[NV]) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int q = 0; q < NV; q++) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
+    for (int q = 0; q < NV; q++) x[q] += shfl_x(x[q], o);
   }
 }
 
@@ -75,73 +141,79 @@ __device__ inline void warp_allsum(double (&x)[NV]) {
 //
 // Called by one full warp; lane i < N handles node i. All lanes return the same result.
 // ---------------------------------------------------------------------------------------
-struct NewtonOut {
-  double th[5];
-  int iters;   // > 0 on success, -1 on failure
-};
-
+template <typename E>
 struct MaxwEval {
-  double F[5];
-  double A[15];  // upper triangle of sum wk M phi phi^T, row-major (i <= j)
+  E F[5];        // weighted moments of M minus the target
+  float A[15];   // upper triangle of sum wk M phi phi^T (row-major, i <= j): Newton direction only
   double fn;     // max |F_i| / |target_0|
-  double e[3];   // this lane's E_1 (with exp(alpha)), E_2, E_3
+  E e[3];        // this lane's E_1 (with exp(alpha)), E_2, E_3
 };
 
-__device__ inline void maxw_eval(int N, double dv, double w, bool wv1, double inv_dx, const double* target,
-                                 const double* th, MaxwEval& out) {
+template <typename E>
+__device__ inline void maxw_eval(int N, double dv, double w, bool wv1, double inv_dx, const E* target,
+                                 const double* th, MaxwEval<E>& out) {
   int lane = threadIdx.x & 31;
-  double s[15];
-  double vi = node(lane < N ? lane : 0, N, dv);
-  double v2 = vi * vi;
+  E s[15];
+  double vd = node(lane < N ? lane : 0, N, dv);
+  E vi = cvt<E>(vd), v2 = cvt<E>(vd * vd);
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    double e = lane < N ? exp(th[1 + d] * vi - th[4] * v2) : 0.0;
+    E e = lane < N ? exp_e<E>(th[1 + d] * vd - th[4] * vd * vd) : cvt<E>(0.0);
     out.e[d] = e;
-    double om = (d == 0 && wv1) ? fabs(vi) * inv_dx : 1.0;
-    double x = om * e;
+    E x = (d == 0 && wv1) ? cvt<E>(fabs(vd) * inv_dx) * e : e;
     s[5 * d + 0] = x;
     s[5 * d + 1] = x * vi;
-    s[5 * d + 2] = x * v2;
-    s[5 * d + 3] = x * v2 * vi;
-    s[5 * d + 4] = x * v2 * v2;
+    s[5 * d + 2] = s[5 * d + 1] * vi;
+    s[5 * d + 3] = s[5 * d + 2] * vi;
+    s[5 * d + 4] = s[5 * d + 2] * v2;
   }
-  warp_allsum<15>(s);
-  double ea = exp(th[0]);
-  out.e[0] *= ea;
-  const double* S1 = s;
-  const double* S2 = s + 5;
-  const double* S3 = s + 10;
-  double c = w * ea;
-  // sums of phi_i phi_j M over the grid, from the 1-D sums
-  double m00 = S1[0] * S2[0] * S3[0];
-  double m1 = S1[1] * S2[0] * S3[0], m2 = S1[0] * S2[1] * S3[0], m3 = S1[0] * S2[0] * S3[1];
-  double q11 = S1[2] * S2[0] * S3[0], q22 = S1[0] * S2[2] * S3[0], q33 = S1[0] * S2[0] * S3[2];
-  double q12 = S1[1] * S2[1] * S3[0], q13 = S1[1] * S2[0] * S3[1], q23 = S1[0] * S2[1] * S3[1];
-  double e2 = q11 + q22 + q33;  // sum |v|^2 M
-  // sum v_d |v|^2 M
-  double c1 = S1[3] * S2[0] * S3[0] + S1[1] * S2[2] * S3[0] + S1[1] * S2[0] * S3[2];
-  double c2 = S1[2] * S2[1] * S3[0] + S1[0] * S2[3] * S3[0] + S1[0] * S2[1] * S3[2];
-  double c3 = S1[2] * S2[0] * S3[1] + S1[0] * S2[2] * S3[1] + S1[0] * S2[0] * S3[3];
-  // sum |v|^4 M
-  double e4 = S1[4] * S2[0] * S3[0] + S1[0] * S2[4] * S3[0] + S1[0] * S2[0] * S3[4] +
-              2.0 * (S1[2] * S2[2] * S3[0] + S1[2] * S2[0] * S3[2] + S1[0] * S2[2] * S3[2]);
-  double mom[5] = {m00, m1, m2, m3, e2};
+  warp_allsum<15, E>(s);
+  E ea = exp_e<E>(th[0]);
+  out.e[0] = out.e[0] * ea;
+  const E* S1 = s;
+  const E* S2 = s + 5;
+  const E* S3 = s + 10;
+  E c = cvt<E>(w) * ea;
+  // sums of phi_i M over the grid, from the 1-D sums
+  E s23 = S2[0] * S3[0];
+  E m00 = S1[0] * s23;
+  E m1 = S1[1] * s23, m2 = S1[0] * (S2[1] * S3[0]), m3 = S1[0] * (S2[0] * S3[1]);
+  E e2 = S1[2] * s23 + S1[0] * (S2[2] * S3[0] + S2[0] * S3[2]);
+  E mom[5] = {m00, m1, m2, m3, e2};
   double amax = 0.0;
 #pragma unroll
   for (int i = 0; i < 5; i++) {
     out.F[i] = c * mom[i] - target[i];
-    amax = fmax(amax, fabs(out.F[i]));
+    amax = fmax(amax, fabs(tod(out.F[i])));
   }
-  out.fn = amax / fabs(target[0]);
-  double A[15] = {m00, m1, m2, m3, e2, q11, q12, q13, c1, q22, q23, c2, q33, c3, e4};
+  out.fn = amax / fabs(tod(target[0]));
+  // Jacobian entries in FP32: they only set the Newton direction
+  float f1[5], f2[5], f3[5];
 #pragma unroll
-  for (int i = 0; i < 15; i++) out.A[i] = c * A[i];
+  for (int p = 0; p < 5; p++) {
+    f1[p] = (float)tod(S1[p]);
+    f2[p] = (float)tod(S2[p]);
+    f3[p] = (float)tod(S3[p]);
+  }
+  float q11 = f1[2] * f2[0] * f3[0], q22 = f1[0] * f2[2] * f3[0], q33 = f1[0] * f2[0] * f3[2];
+  float q12 = f1[1] * f2[1] * f3[0], q13 = f1[1] * f2[0] * f3[1], q23 = f1[0] * f2[1] * f3[1];
+  float c1 = f1[3] * f2[0] * f3[0] + f1[1] * f2[2] * f3[0] + f1[1] * f2[0] * f3[2];
+  float c2 = f1[2] * f2[1] * f3[0] + f1[0] * f2[3] * f3[0] + f1[0] * f2[1] * f3[2];
+  float c3 = f1[2] * f2[0] * f3[1] + f1[0] * f2[2] * f3[1] + f1[0] * f2[0] * f3[3];
+  float e4 = f1[4] * f2[0] * f3[0] + f1[0] * f2[4] * f3[0] + f1[0] * f2[0] * f3[4] +
+             2.0f * (f1[2] * f2[2] * f3[0] + f1[2] * f2[0] * f3[2] + f1[0] * f2[2] * f3[2]);
+  float cf = (float)tod(c);
+  float A[15] = {f1[0] * f2[0] * f3[0], f1[1] * f2[0] * f3[0], f1[0] * f2[1] * f3[0], f1[0] * f2[0] * f3[1],
+                 q11 + q22 + q33, q11, q12, q13, c1, q22, q23, c2, q33, c3, e4};
+#pragma unroll
+  for (int i = 0; i < 15; i++) out.A[i] = cf * A[i];
 }
 
-// Solves A y = b for the symmetric positive definite 5x5 matrix given by its upper
-// triangle (row-major). Returns false if A is not numerically positive definite.
-__device__ inline bool chol5_solve(const double* Au, const double* b, double* y) {
-  double a[5][5];
+// Solves A y = b (FP32) for the symmetric positive definite 5x5 matrix given by its upper
+// triangle (row-major). Returns false if A is not numerically positive definite. The
+// solution only serves as a Newton direction; the residual F stays in the caller's precision.
+__device__ inline bool chol5_solve(const float* Au, const float* b, float* y) {
+  float a[5][5];
   int t = 0;
 #pragma unroll
   for (int i = 0; i < 5; i++)
@@ -151,53 +223,63 @@ __device__ inline bool chol5_solve(const double* Au, const double* b, double* y)
       a[j][i] = Au[t];
       t++;
     }
-  double l[5][5];
+  // symmetric diagonal scaling keeps the FP32 factorisation well conditioned
+  float sc[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    if (!(a[i][i] > 0.0f)) return false;
+    sc[i] = rsqrtf(a[i][i]);
+  }
+  float l[5][5];
 #pragma unroll
   for (int i = 0; i < 5; i++)
 #pragma unroll
-    for (int j = 0; j < 5; j++) l[i][j] = 0.0;
+    for (int j = 0; j < 5; j++) l[i][j] = 0.0f;
 #pragma unroll
   for (int j = 0; j < 5; j++) {
-    double d = a[j][j];
+    float d = a[j][j] * sc[j] * sc[j];
 #pragma unroll
     for (int k = 0; k < j; k++) d -= l[j][k] * l[j][k];
-    if (!(d > 0.0)) return false;
-    double ljj = sqrt(d);
+    if (!(d > 0.0f)) return false;
+    float ljj = sqrtf(d);
     l[j][j] = ljj;
-    double inv = 1.0 / ljj;
+    float inv = 1.0f / ljj;
 #pragma unroll
     for (int i = j + 1; i < 5; i++) {
-      double s = a[i][j];
+      float s = a[i][j] * sc[i] * sc[j];
 #pragma unroll
       for (int k = 0; k < j; k++) s -= l[i][k] * l[j][k];
       l[i][j] = s * inv;
     }
   }
-  double z[5];
+  float z[5];
 #pragma unroll
   for (int i = 0; i < 5; i++) {
-    double s = b[i];
+    float s = b[i] * sc[i];
 #pragma unroll
     for (int k = 0; k < i; k++) s -= l[i][k] * z[k];
     z[i] = s / l[i][i];
   }
 #pragma unroll
   for (int i = 4; i >= 0; i--) {
-    double s = z[i];
+    float s = z[i];
 #pragma unroll
     for (int k = i + 1; k < 5; k++) s -= l[k][i] * y[k];
     y[i] = s / l[i][i];
   }
+#pragma unroll
+  for (int i = 0; i < 5; i++) y[i] *= sc[i];
   return true;
 }
 
 // Continuum Maxwellian with the given moments (rho, rho U, sum |v|^2 f): initial guess.
-__device__ inline bool continuum_guess(const double* m, double* th) {
-  double rho = m[0];
+template <typename E>
+__device__ inline bool continuum_guess(const E* m, double* th) {
+  double rho = tod(m[0]);
   if (!(rho > 0.0)) return false;
-  double U0 = m[1] / rho, U1 = m[2] / rho, U2 = m[3] / rho;
+  double U0 = tod(m[1]) / rho, U1 = tod(m[2]) / rho, U2 = tod(m[3]) / rho;
   double uu = U0 * U0 + U1 * U1 + U2 * U2;
-  double T = (m[4] / rho - uu) / 3.0;
+  double T = (tod(m[4]) / rho - uu) / 3.0;
   if (!(T > 0.0)) return false;
   th[4] = 0.5 / T;
   th[1] = U0 / T;
@@ -207,26 +289,29 @@ __device__ inline bool continuum_guess(const double* m, double* th) {
   return true;
 }
 
-// Newton for the weighted discrete Maxwellian. th holds the initial guess on entry.
-// On return ev holds the evaluation at the returned theta (lane-local E factors included).
-__device__ inline int maxwellian_newton(int N, double dv, double w, bool wv1, double inv_dx, const double* target,
-                                        double* th, double tol, int maxit, MaxwEval& ev) {
+// Newton for the weighted discrete Maxwellian from the guess in th. The residual F is
+// evaluated in E (FP64 or FP32) and the direction from the FP32 factorisation (inexact
+// Newton: the root is the one of F in E). The step is halved while the scaled residual
+// grows; the iteration stops right after a step whose exponent change
+// |da| + L sum|db| + L^2 |dg| is below tol. On return ev holds the evaluation at th.
+template <typename E>
+__device__ inline int maxwellian_newton(int N, double dv, double w, bool wv1, double inv_dx, const E* target,
+                                        double* th, double tol, int maxit, MaxwEval<E>& ev) {
   double L = node(N - 1, N, dv);
-  maxw_eval(N, dv, w, wv1, inv_dx, target, th, ev);
-  bool done = false;
-  int it;
-  for (it = 0; it < maxit; it++) {
-    double y[5];
-    if (!chol5_solve(ev.A, ev.F, y)) return -1;
-    double d[5] = {-y[0], -y[1], -y[2], -y[3], y[4]};  // delta = -D A^{-1} F, D = diag(1,1,1,1,-1)
+  maxw_eval<E>(N, dv, w, wv1, inv_dx, target, th, ev);
+  for (int it = 0; it < maxit; it++) {
+    float y[5], Ff[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) Ff[i] = (float)tod(ev.F[i]);
+    if (!chol5_solve(ev.A, Ff, y)) return -1;
+    double d[5] = {-(double)y[0], -(double)y[1], -(double)y[2], -(double)y[3], (double)y[4]};  // -D A^{-1} F
     double lam = 1.0;
     double fn = ev.fn;
     double tt[5];
-    int hv;
-    for (hv = 0; hv < 40; hv++) {
+    for (int hv = 0; hv < 40; hv++) {
 #pragma unroll
       for (int i = 0; i < 5; i++) tt[i] = th[i] + lam * d[i];
-      maxw_eval(N, dv, w, wv1, inv_dx, target, tt, ev);
+      maxw_eval<E>(N, dv, w, wv1, inv_dx, target, tt, ev);
       if (ev.fn == ev.fn && (ev.fn <= fn || ev.fn <= 1e-10)) break;
       lam *= 0.5;
     }
@@ -234,8 +319,7 @@ __device__ inline int maxwellian_newton(int N, double dv, double w, bool wv1, do
     for (int i = 0; i < 5; i++) th[i] = tt[i];
     double step = lam * (fabs(d[0]) + L * (fabs(d[1]) + fabs(d[2]) + fabs(d[3])) + L * L * fabs(d[4]));
     if (!(step == step)) return -1;
-    if (done) return it + 1;
-    if (step <= tol) done = true;
+    if (step <= tol) return it + 1;
   }
   return -1;
 }

@@ -117,15 +117,30 @@ cudaError_t launch_moments(const double* f, const CellTables& ct, int C, int N, 
 cudaError_t launch_collide_bgk(const double* f, const CellTables& ct, int C, int N, double dv, const double* theta,
                                const double* nu, double* Q, double* P, cudaStream_t st);
 template <typename T>
-cudaError_t launch_collide_spectral(const double* f, double* Q, double* P, const CollideCtx<T>& x, cudaStream_t st);
+cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, cudaStream_t st);
+template <typename T>
+cudaError_t launch_spectral_sum(const CollideCtx<T>& x, cudaStream_t st);
+template <typename T>
+cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const CollideCtx<T>& x, cudaStream_t st);
 template <typename T>
 cudaError_t launch_build_weights(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
                                  const double* G, long long nb, const double* Lo, T* W, cudaStream_t st);
 
-cudaError_t launch_sweep(const SweepArgs& a, int cluster, int tpb, cudaStream_t st);
-int sweep_cluster_for(int N);
+struct SweepShape {
+  int ept;      // velocity nodes per thread (divides N)
+  int cluster;  // CTAs per instance
+  int tpb;      // threads per CTA
+};
+// arithmetic of the sweep's elementwise work and reductions
+constexpr int kSweepF64 = 0;   // native FP64
+constexpr int kSweepDF64 = 1;  // double-float on the FP32 pipes (FP64-class accuracy)
+constexpr int kSweepF32 = 2;   // plain FP32 (converges only to FP32 resolution)
+SweepShape sweep_shape(int N, int arith);
+bool sweep_shape_valid(int N, const SweepShape& sh);
+cudaError_t launch_sweep(const SweepArgs& a, const SweepShape& sh, int arith, cudaStream_t st);
 
 cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st);
+cudaError_t launch_dc_rhs(const AuxArgs& a, const double* Qhi, double* Qlo_b, cudaStream_t st);
 cudaError_t launch_residual(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
                             cudaStream_t st);
 cudaError_t launch_restrict(const double* fine, double* coarse, long long K, int Jc, cudaStream_t st);

@@ -97,7 +97,17 @@ struct sgs_handle {
     size_t inst, cell_off, cell_inst, cnt, theta, nu, scratch, tw_cos, tw_sin, G, Lo, units, step0, row_k, row_start,
         row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, end;
   } off;
-  int sweep_cluster = 1, sweep_tpb = 256;
+  SweepShape sweep{8, 1, 256};
+  int sweep_arith = kSweepF64;
+  // profiling: per-class CUDA-event pairs recorded on the launching stream
+  bool prof = false;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  unsigned long long launches = 0;
   long long spin_max = 1LL << 26;
 
   template <typename T>
@@ -304,6 +314,40 @@ int cuda_status(cudaError_t e) {
   return SGS_ERR_CUDA;
 }
 
+cudaEvent_t take_event(sgs_handle* h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Counts the kernels a host call enqueues and, when profiling is on, brackets them with
+// CUDA events on the same stream.
+struct Scope {
+  sgs_handle* h;
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Scope(sgs_handle* h_, int cls_, cudaStream_t st_, int n_launch) : h(h_), cls(cls_), st(st_) {
+    h->launches += n_launch;
+    if (h->prof) {
+      a = take_event(h);
+      b = take_event(h);
+      if (a && b) cudaEventRecord(a, st);
+    }
+  }
+  ~Scope() {
+    if (h->prof && a && b) {
+      cudaEventRecord(b, st);
+      h->recs.push_back({cls, a, b});
+    }
+  }
+};
+
 AuxArgs aux_args(const sgs_handle* h) {
   AuxArgs a;
   a.inst = h->at<InstDev>(h->off.inst);
@@ -372,15 +416,37 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
   double* theta = h->at<double>(h->off.theta);
   double* nu = h->at<double>(h->off.nu);
   const sgs_problem& p0 = h->prob[0];
-  cudaError_t e = launch_moments(f, ct, h->C, h->N, h->dv, p0.newton_tol, p0.newton_max, theta, nu,
-                                 h->at<Counters>(h->off.cnt), st);
-  if (e != cudaSuccess) return cuda_status(e);
-  if (!h->spectral) return cuda_status(launch_collide_bgk(f, ct, h->C, h->N, h->dv, theta, nu, Q, P, st));
-  if (precision == SGS_FP32) {
-    if (h->off.W32 == h->off.st1a) return SGS_ERR_ARG;  // FP32 tables not built
-    return cuda_status(launch_collide_spectral<float>(f, Q, P, collide_ctx<float>(h), st));
+  cudaError_t e;
+  {
+    Scope sc(h, SGS_PROF_MOMENTS, st, 1);
+    e = launch_moments(f, ct, h->C, h->N, h->dv, p0.newton_tol, p0.newton_max, theta, nu,
+                       h->at<Counters>(h->off.cnt), st);
   }
-  return cuda_status(launch_collide_spectral<double>(f, Q, P, collide_ctx<double>(h), st));
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!h->spectral) {
+    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 1);
+    return cuda_status(launch_collide_bgk(f, ct, h->C, h->N, h->dv, theta, nu, Q, P, st));
+  }
+  auto run = [&](auto x) -> int {
+    cudaError_t er;
+    {
+      Scope sc(h, SGS_PROF_DFT, st, 3);
+      er = launch_dft(f, x, st);
+    }
+    if (er != cudaSuccess) return cuda_status(er);
+    {
+      Scope sc(h, SGS_PROF_SUM, st, 1);
+      er = launch_spectral_sum(x, st);
+    }
+    if (er != cudaSuccess) return cuda_status(er);
+    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 4);
+    return cuda_status(launch_reduce_idft(f, Q, P, x, st));
+  };
+  if (precision == SGS_FP32) {
+    if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
+    return run(collide_ctx<float>(h));
+  }
+  return run(collide_ctx<double>(h));
 }
 
 int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int dir, cudaStream_t st) {
@@ -395,7 +461,37 @@ int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int
   a.N = h->N;
   a.dv = h->dv;
   a.dir = dir;
-  return cuda_status(launch_sweep(a, h->sweep_cluster, h->sweep_tpb, st));
+  Scope sc(h, SGS_PROF_SWEEP, st, 1);
+  return cuda_status(launch_sweep(a, h->sweep, h->sweep_arith, st));
+}
+
+int rescale_impl(sgs_handle* h, double* f, cudaStream_t st) {
+  Scope sc(h, SGS_PROF_RESCALE, st, 2);
+  return cuda_status(launch_rescale(aux_args(h), f, st));
+}
+
+int residual_impl(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, cudaStream_t st) {
+  Scope sc(h, SGS_PROF_RESIDUAL, st, res ? 3 : 2);
+  return cuda_status(launch_residual(aux_args(h), f, Q, rhs, res, st));
+}
+
+int iterate_impl(sgs_handle* h, double* f, double* Q, double* P, const double* rhs, int flags, double* res,
+                 cudaStream_t st) {
+  int r;
+  if (!(flags & SGS_IT_P_VALID)) {
+    r = collide_impl(h, f, nullptr, P, h->precision, st);
+    if (r) return r;
+  }
+  if ((r = sweep_impl(h, f, P, rhs, +1, st))) return r;
+  if ((r = collide_impl(h, f, nullptr, P, h->precision, st))) return r;
+  if ((r = sweep_impl(h, f, P, rhs, -1, st))) return r;
+  if ((r = rescale_impl(h, f, st))) return r;
+  if (flags & SGS_IT_EVAL) {
+    if (!Q) return SGS_ERR_ARG;
+    if ((r = collide_impl(h, f, Q, P, h->precision, st))) return r;
+    if (res && (r = residual_impl(h, f, Q, rhs, res, st))) return r;
+  }
+  return SGS_OK;
 }
 
 }  // namespace
@@ -446,7 +542,8 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
     return r;
   }
   layout(h);
-  h->sweep_cluster = sweep_cluster_for(h->N);
+  h->sweep_arith = h->precision == SGS_FP32 ? kSweepDF64 : kSweepF64;
+  h->sweep = sweep_shape(h->N, h->sweep_arith);
   *out = h;
   if (workspace_bytes) *workspace_bytes = h->ws_bytes;
   return SGS_OK;
@@ -538,33 +635,39 @@ int sgs_sweep_backward(sgs_handle* h, double* f, const double* P, const double* 
 int sgs_rescale(sgs_handle* h, double* f, void* stream) {
   if (!h || !f) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;
-  return cuda_status(launch_rescale(aux_args(h), f, as_stream(stream)));
+  return rescale_impl(h, f, as_stream(stream));
 }
 
 int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, void* stream) {
   if (!h || !f || !Q || !res) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;
-  return cuda_status(launch_residual(aux_args(h), f, Q, rhs, res, as_stream(stream)));
+  return residual_impl(h, f, Q, rhs, res, as_stream(stream));
 }
 
-int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, int flags, double* res, void* stream) {
+int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, const double* rhs, int flags, double* res,
+                void* stream) {
   if (!h || !f || !P) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;
+  return iterate_impl(h, f, Q, P, rhs, flags, res, as_stream(stream));
+}
+
+int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, double* rhs, int lo_iters, double* res, void* stream) {
+  if (!h || !f || !Q || !P || !rhs || lo_iters < 0) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  if (h->precision != SGS_FP32) return SGS_ERR_ARG;
   cudaStream_t st = as_stream(stream);
   int r;
-  if (!(flags & SGS_IT_P_VALID)) {
-    r = collide_impl(h, f, nullptr, P, h->precision, st);
-    if (r) return r;
+  // FP64 collision and residual of the current iterate: the convergence test
+  if ((r = collide_impl(h, f, Q, nullptr, SGS_FP64, st))) return r;
+  if (res && (r = residual_impl(h, f, Q, nullptr, res, st))) return r;
+  // b = R_lo(f_k) - R_hi(f_k) = (Q_hi - Q_lo) / eps; the lo collision also leaves P_lo(f_k)
+  if ((r = collide_impl(h, f, rhs, P, SGS_FP32, st))) return r;
+  {
+    Scope sc(h, SGS_PROF_RESCALE, st, 1);
+    if ((r = cuda_status(launch_dc_rhs(aux_args(h), Q, rhs, st)))) return r;
   }
-  if ((r = sweep_impl(h, f, P, nullptr, +1, st))) return r;
-  if ((r = collide_impl(h, f, nullptr, P, h->precision, st))) return r;
-  if ((r = sweep_impl(h, f, P, nullptr, -1, st))) return r;
-  if ((r = cuda_status(launch_rescale(aux_args(h), f, st)))) return r;
-  if (flags & SGS_IT_EVAL) {
-    if (!Q) return SGS_ERR_ARG;
-    if ((r = collide_impl(h, f, Q, P, h->precision, st))) return r;
-    if (res && (r = cuda_status(launch_residual(aux_args(h), f, Q, nullptr, res, st)))) return r;
-  }
+  for (int it = 0; it < lo_iters; it++)
+    if ((r = iterate_impl(h, f, Q, P, rhs, it == 0 ? SGS_IT_P_VALID : 0, nullptr, st))) return r;
   return SGS_OK;
 }
 
@@ -605,7 +708,45 @@ int sgs_reset_stats(sgs_handle* h, void* stream) {
   return cuda_status(cudaMemsetAsync(h->ws + h->off.cnt, 0, sizeof(Counters) * h->n_inst, as_stream(stream)));
 }
 
-void sgs_destroy(sgs_handle* h) { delete h; }
+int sgs_profile(sgs_handle* h, int enable) {
+  if (!h) return SGS_ERR_ARG;
+  h->prof = enable != 0;
+  return SGS_OK;
+}
+
+int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, int n_classes) {
+  if (!h || n_classes < 0) return SGS_ERR_ARG;
+  for (int c = 0; c < n_classes; c++) {
+    if (ms) ms[c] = 0.0;
+    if (launches) launches[c] = 0;
+  }
+  for (auto& rec : h->recs) {
+    cudaError_t e = cudaEventSynchronize(rec.b);
+    if (e != cudaSuccess) return cuda_status(e);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, rec.a, rec.b);
+    if (rec.cls < n_classes) {
+      if (ms) ms[rec.cls] += t;
+      if (launches) launches[rec.cls] += 1;
+    }
+    h->pool.push_back(rec.a);
+    h->pool.push_back(rec.b);
+  }
+  h->recs.clear();
+  return SGS_OK;
+}
+
+unsigned long long sgs_launch_count(const sgs_handle* h) { return h ? h->launches : 0; }
+
+void sgs_destroy(sgs_handle* h) {
+  if (!h) return;
+  for (auto& rec : h->recs) {
+    h->pool.push_back(rec.a);
+    h->pool.push_back(rec.b);
+  }
+  for (auto e : h->pool) cudaEventDestroy(e);
+  delete h;
+}
 
 const char* sgs_strerror(int code) {
   switch (code) {

@@ -23,6 +23,8 @@ DIFFUSE, INFLOW = 0, 1
 FP64, FP32 = 0, 1
 PFP, FP = 0, 1
 IT_P_VALID, IT_EVAL = 1, 2
+PROF_NAMES = ("moments", "dft", "sum", "reduce_idft", "sweep", "residual", "rescale")
+PROF_CLASSES = len(PROF_NAMES)
 
 
 class _BC(C.Structure):
@@ -127,7 +129,11 @@ def lib(build: bool = True):
             "sgs_sweep_backward": (C.c_int, [vp, vp, vp, vp, vp]),
             "sgs_rescale": (C.c_int, [vp, vp, vp]),
             "sgs_residual": (C.c_int, [vp, vp, vp, vp, vp, vp]),
-            "sgs_iterate": (C.c_int, [vp, vp, vp, vp, C.c_int, vp, vp]),
+            "sgs_iterate": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, vp, vp]),
+            "sgs_dc_step": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, vp, vp]),
+            "sgs_profile": (C.c_int, [vp, C.c_int]),
+            "sgs_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_ulonglong), C.c_int]),
+            "sgs_launch_count": (C.c_ulonglong, [vp]),
             "sgs_vcycle": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]),
             "sgs_read_status": (C.c_int, [vp, C.POINTER(_Stats), vp]),
             "sgs_reset_stats": (C.c_int, [vp, vp]),
@@ -226,9 +232,25 @@ class Solver:
     def residual(self, f, Q, res, rhs=None, stream=None):
         _check(lib().sgs_residual(self.h, _ptr(f), _ptr(Q), _ptr(rhs), _ptr(res), _stream(stream)), "sgs_residual")
 
-    def iterate(self, f, Q, P, flags=0, res=None, stream=None):
-        _check(lib().sgs_iterate(self.h, _ptr(f), _ptr(Q), _ptr(P), flags, _ptr(res), _stream(stream)),
+    def iterate(self, f, Q, P, flags=0, res=None, rhs=None, stream=None):
+        _check(lib().sgs_iterate(self.h, _ptr(f), _ptr(Q), _ptr(P), _ptr(rhs), flags, _ptr(res), _stream(stream)),
                "sgs_iterate")
+
+    def dc_step(self, f, Q, P, rhs, lo_iters, res=None, stream=None):
+        _check(lib().sgs_dc_step(self.h, _ptr(f), _ptr(Q), _ptr(P), _ptr(rhs), lo_iters, _ptr(res),
+                                 _stream(stream)), "sgs_dc_step")
+
+    def profile(self, enable=True):
+        _check(lib().sgs_profile(self.h, 1 if enable else 0), "sgs_profile")
+
+    def profile_read(self):
+        ms = (C.c_double * PROF_CLASSES)()
+        n = (C.c_ulonglong * PROF_CLASSES)()
+        _check(lib().sgs_profile_read(self.h, ms, n, PROF_CLASSES), "sgs_profile_read")
+        return {PROF_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(PROF_CLASSES)}
+
+    def launch_count(self) -> int:
+        return int(lib().sgs_launch_count(self.h))
 
     def vcycle(self, f, levels, pre=1, post=1, coarse_iters=10, stream=None):
         _check(lib().sgs_vcycle(self.h, _ptr(f), levels, pre, post, coarse_iters, _stream(stream)), "sgs_vcycle")

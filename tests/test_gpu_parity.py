@@ -219,3 +219,44 @@ def test_nonfinite_input_sets_status_and_returns():
     s.sweep_forward(fd, P)
     st = s.read_status()
     assert st["status"] & (sgs.ST_NONFINITE | sgs.ST_NEWTON_FAIL | sgs.ST_NONPOSITIVE)
+
+
+@pytest.mark.parametrize("N,J,eps,direction", [(8, 6, 0.01, 1), (16, 4, 0.1, -1)])
+def test_sweep_df64_parity(oracle, N, J, eps, direction):
+    """Mixed-precision handles scan in double-float on the FP32 pipes: FP64-class accuracy."""
+    L = 6.0
+    d = spec(nx=J, nv=N, v_max=L, eps=eps, inner_fixed=6, precision=sgs.FP32)
+    f0 = I.initial_state(J, N, L, T=1.5, seed=7)
+    po = oracle_problem(oracle, d)
+    Qo, Po, nuo = oracle.collide(po, f0)
+    fo = f0.copy()
+    oracle.sweep(po, fo, Po, nuo, direction)
+    s = sgs.Solver(gpu_problem(d))
+    fd = to_dev(f0)
+    Q, P = s.field(), s.field()
+    s.collide(fd, Q, P)
+    Pd = to_dev(Po)
+    if direction > 0:
+        s.sweep_forward(fd, Pd)
+    else:
+        s.sweep_backward(fd, Pd)
+    assert s.read_status()["status"] == 0
+    assert rel(fd.cpu().numpy().reshape(f0.shape), fo) <= 1e-11
+
+
+def test_defect_correction_reaches_fp64_fixed_point(oracle):
+    """FP32 collision sums + df64 scans + FP64 defect correction converge to the FP64
+    solution: the FP64 residual falls well below the FP32 collision error."""
+    wl = I.heat_16cells_16v()
+    d = spec(nx=wl.J, nv=wl.N, v_max=wl.L, eps=0.1, T=(wl.T_left, wl.T_right), total_mass=wl.total_mass,
+             precision=sgs.FP32, inner_tol=1e-11)
+    s = sgs.Solver(gpu_problem(d))
+    f = to_dev(wl.initial_state())
+    Q, P, rhs = s.field(), s.field(), s.field()
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    hist = []
+    for k in range(12):
+        s.dc_step(f, Q, P, rhs, 8, res=res)
+        hist.append(res.item())
+    assert hist[-1] < 1e-9, hist
+    assert s.read_status()["status"] == 0
