@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--dc-every", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["sweep", "sum", "sum64"], default=None,
+                    help="run a small case of one kernel class (for profiler captures) and exit")
     return ap.parse_args()
 
 
@@ -140,15 +142,15 @@ def run_native(args, rank, world, local):
     f0 = torch.from_numpy(wl.initial_state().reshape(-1)).to(dev)
     s = make_solver(wl, sgs.FP32)
     f = f0.clone()
-    Q, P, rhs = s.field(), s.field(), s.field()
+    Q, P = s.field(), s.field()
     res_hi = torch.zeros(1, dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     visits_per_step = 2 * wl.J
 
     def step(i):
         if i % args.dc_every == 0:
-            s.dc_step(f, Q, P, rhs, 0, res=res_hi)
-        s.iterate(f, Q, P, rhs=rhs, flags=sgs.IT_P_VALID | sgs.IT_EVAL)
+            s.dc_step(f, Q, P, 0, res=res_hi)
+        s.iterate(f, Q, P, flags=sgs.IT_P_VALID | sgs.IT_EVAL)
 
     # warm-up (untimed): the first DC evaluation also initialises P
     for i in range(args.warmup):
@@ -190,7 +192,7 @@ def run_native(args, rank, world, local):
     # D2H of the step's residual
     e2e = None
     if rank == 0 or world > 1:
-        e2e = end_to_end(s, f, Q, P, rhs, wl, args, stream)
+        e2e = end_to_end(s, f, Q, P, wl, args, stream)
 
     # plain FP64 GPU form for comparison (same step, FP64 collision sum and FP64 scan)
     fp64 = fp64_form(wl, args, f0, dev, stream)
@@ -253,7 +255,7 @@ def roofline(dom, prof, wl, s, sm_mhz):
             "frac": ach / peaks["hbm_gbs"], "traffic": None}
 
 
-def end_to_end(s, f, Q, P, rhs, wl, args, stream):
+def end_to_end(s, f, Q, P, wl, args, stream):
     import torch
 
     from paper_2409_01910_gb300 import sgs
@@ -266,7 +268,7 @@ def end_to_end(s, f, Q, P, rhs, wl, args, stream):
     for _ in range(2):
         f.copy_(hf, non_blocking=True)
         P.copy_(hP, non_blocking=True)
-        s.iterate(f, Q, P, rhs=rhs, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
+        s.iterate(f, Q, P, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
         hres.copy_(res, non_blocking=True)
         torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -276,7 +278,7 @@ def end_to_end(s, f, Q, P, rhs, wl, args, stream):
         t0.record(stream)
         f.copy_(hf, non_blocking=True)
         P.copy_(hP, non_blocking=True)
-        s.iterate(f, Q, P, rhs=rhs, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
+        s.iterate(f, Q, P, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
         hres.copy_(res, non_blocking=True)
         t1.record(stream)
         t1.synchronize()
@@ -370,8 +372,36 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_case(which):
+    """Small instance of one kernel class for ncu: the persistent scan on 4 cells, or the
+    spectral sum on 32 cells (one lane group), both on the 32^3 grid of the workload."""
+    import torch
+
+    from paper_2409_01910_gb300 import inputs as I
+    from paper_2409_01910_gb300 import sgs
+
+    J = 4 if which == "sweep" else 32
+    p = sgs.Problem(nx=J, nv=32, v_max=8.0, eps=0.01, bc_T=(1.0, 1.8), total_mass=1.0,
+                    precision=sgs.FP64 if which == "sum64" else sgs.FP32)
+    s = sgs.Solver(p)
+    f = torch.from_numpy(I.initial_state(J, 32, 8.0, T=1.4).reshape(-1)).cuda()
+    Q, P = s.field(), s.field()
+    s.collide(f, Q, P)
+    for _ in range(2):
+        if which == "sweep":
+            g = f.clone()
+            s.sweep_forward(g, P)
+        else:
+            s.collide(f, Q, P)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": which, "status": s.read_status()}))
+
+
 def main():
     args = parse()
+    if args.case:
+        profile_case(args.case)
+        return
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)

@@ -147,12 +147,16 @@ int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, const double* rh
                 void* stream);
 
 /* One step of FP64 defect correction for the mixed solver (handle set up with SGS_FP32):
- *   Q = Q_FP64[f_k], res = FP64 residual of f_k (device, n_inst doubles, nullable),
- *   rhs = R_lo(f_k) - R_hi(f_k) = (Q - Q_FP32[f_k]) / eps,
- *   then lo_iters SGS iterations on R_lo(f) = rhs with the FP32 collision sum and the FP32
- *   sweep, which return f_{k+1}. Q, P, rhs are caller-owned device fields (scratch). The
- *   fixed point of the step solves the FP64 equations: R_hi(f) = 0. */
-int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, double* rhs, int lo_iters, double* res, void* stream);
+ *   Q, P = FP64 collision of the current iterate f_k; res = its FP64 residual (device,
+ *   n_inst doubles, nullable); f_k becomes the reference state; then lo_iters SGS
+ *   iterations in which every FP32 collision is evaluated in increment form
+ *     Q(f) = Q_FP64(f_k) + [Q_s(a - a_k, b) + Q_s(a_k, b - b_k)]_FP32,  a = f - M, b = f + M,
+ *   an exact identity of the symmetric bilinear form whose FP32 rounding error scales with
+ *   f - f_k. Each step therefore moves f towards the FP64 solution R_FP64(f) = 0 without an
+ *   FP32 noise floor. The reference stays in force for later FP32 collisions on this handle
+ *   until sgs_dc_clear() or the next sgs_dc_step(). Q and P are caller-owned device fields. */
+int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, int lo_iters, double* res, void* stream);
+int sgs_dc_clear(sgs_handle* h);
 
 /* One FAS V-cycle (eq. (30)) on every instance: levels >= 2 grids with H = 2h (each level's
  * cell count must be even), pre/post SGS smoothing iterations, coarse_iters iterations on

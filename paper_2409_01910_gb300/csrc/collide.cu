@@ -96,7 +96,7 @@ __device__ inline void maxwell_factors(const double* theta, int c, int N, double
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_dft_i3(const double* __restrict__ f, CellTables ct, const double* theta,
-                                                 SpecBufs<T> sb, int N, double dv) {
+                                                 SpecBufs<T> sb, int N, double dv, DftMode md) {
   extern __shared__ __align__(16) unsigned char smraw[];
   int n = N - 1;
   T* cs = (T*)smraw;             // [n][N] cos
@@ -104,20 +104,35 @@ __global__ void __launch_bounds__(256) k_dft_i3(const double* __restrict__ f, Ce
   T* sa = sn + n * N;            // [N][N] a slab (i2, i3)
   T* sbb = sa + N * N;           // [N][N] b slab
   __shared__ double E[3 * kMaxN];
+  __shared__ double Er[3 * kMaxN];
   int c = blockIdx.x, i1 = blockIdx.y;
   maxwell_factors(theta, c, N, dv, E);
+  if (md.mode != 0) maxwell_factors(md.theta_ref, c, N, dv, Er);
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
     cs[t] = (T)sb.tw_cos[t];
     sn[t] = (T)sb.tw_sin[t];
   }
   __syncthreads();
-  const double* fc = f + ct.cell_off[c] + (long long)i1 * N * N;
+  const long long off = ct.cell_off[c] + (long long)i1 * N * N;
+  const double* fc = f + off;
   for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
     int i2 = t / N, i3 = t % N;
     double M = E[i1] * E[kMaxN + i2] * E[2 * kMaxN + i3];
     double x = fc[t];
-    sa[t] = (T)(x - M);
-    sbb[t] = (T)(x + M);
+    if (md.mode == 0) {  // a = f - M, b = f + M
+      sa[t] = (T)(x - M);
+      sbb[t] = (T)(x + M);
+    } else {  // increments against the reference state f_ref, M_ref (exact in FP64, then rounded)
+      double Mr = Er[i1] * Er[kMaxN + i2] * Er[2 * kMaxN + i3];
+      double xr = md.f_ref[off + t];
+      if (md.mode == 1) {  // a = (f - M) - (f_ref - M_ref), b = f + M
+        sa[t] = (T)((x - xr) - (M - Mr));
+        sbb[t] = (T)(x + M);
+      } else {  // a unused, b = (f + M) - (f_ref + M_ref)
+        sa[t] = (T)0;
+        sbb[t] = (T)((x - xr) + (M - Mr));
+      }
+    }
   }
   __syncthreads();
   typedef typename CplxOf<T>::type CT;
@@ -391,6 +406,13 @@ __global__ void k_sum_reduce(RedArgs<T> a) {
       sr += (double)v.x;
       si += (double)v.y;
     }
+    if (a.partial2)
+      for (int q = u0; q < u1; q++) {
+        int u = a.row_units[q];
+        CT v = a.partial2[((long long)u * a.G + g) * n * kLanes + t];
+        sr += (double)v.x;
+        si += (double)v.y;
+      }
     int k3i = t / kLanes, lane = t % kLanes;
     long long o = ((((long long)g * n + (k1 + H)) * n + (k2 + H)) * n + k3i) * kLanes + lane;
     a.qhat[o] = make_cplx((T)sr, (T)si);
@@ -471,7 +493,7 @@ __global__ void __launch_bounds__(256) k_idft_k2(SpecBufs<T> sb, int N) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* __restrict__ f, CellTables ct,
                                                   const double* theta, const double* nu, double* Q, double* P,
-                                                  int N, double dv) {
+                                                  int N, double dv, const double* __restrict__ Qadd) {
   typedef typename CplxOf<T>::type CT;
   extern __shared__ __align__(16) unsigned char smraw[];
   int n = N - 1;
@@ -498,6 +520,7 @@ __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* _
       re += q.x * cs[k3 * N + i3] - q.y * sn[k3 * N + i3];
     }
     double q = (double)re;
+    if (Qadd) q += Qadd[base + t];
     if (Q) Q[base + t] = q;
     if (P) {
       double M = E[i1] * E[kMaxN + i2] * E[2 * kMaxN + i3];
@@ -617,13 +640,13 @@ cudaError_t launch_sum(const SumArgs<T>& a, int H, int NW, int n_units, cudaStre
 }
 
 template <typename T>
-cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, cudaStream_t st) {
+cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, const DftMode& md, cudaStream_t st) {
   int N = x.N, n = N - 1, C = x.C;
   cudaError_t e;
   size_t sm1 = dft_smem<T>(N, 0, 2 * N * N);
   e = cudaFuncSetAttribute(k_dft_i3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
   if (e != cudaSuccess) return e;
-  k_dft_i3<T><<<dim3(C, N), 256, sm1, st>>>(f, x.ct, x.theta, x.sb, N, x.dv);
+  k_dft_i3<T><<<dim3(C, N), 256, sm1, st>>>(f, x.ct, x.theta, x.sb, N, x.dv, md);
   size_t sm2 = dft_smem<T>(N, 2 * N * n, 0);
   e = cudaFuncSetAttribute(k_dft_i2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   if (e != cudaSuccess) return e;
@@ -636,15 +659,20 @@ cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, cudaStream_t st)
 }
 
 template <typename T>
-cudaError_t launch_spectral_sum(const CollideCtx<T>& x, cudaStream_t st) {
-  return launch_sum<T>(x.sum, x.H, x.NW, x.n_units, st);
+cudaError_t launch_spectral_sum(const CollideCtx<T>& x, typename CplxOf<T>::type* partial, cudaStream_t st) {
+  SumArgs<T> a = x.sum;
+  if (partial) a.partial = partial;
+  return launch_sum<T>(a, x.H, x.NW, x.n_units, st);
 }
 
 template <typename T>
-cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const CollideCtx<T>& x, cudaStream_t st) {
+cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const CollideCtx<T>& x,
+                               const typename CplxOf<T>::type* partial2, const double* Qadd, cudaStream_t st) {
   int N = x.N, n = N - 1, C = x.C;
   cudaError_t e;
-  k_sum_reduce<T><<<dim3(x.red.n_rows, x.red.G), 256, 0, st>>>(x.red);
+  RedArgs<T> ra = x.red;
+  ra.partial2 = partial2;
+  k_sum_reduce<T><<<dim3(x.red.n_rows, x.red.G), 256, 0, st>>>(ra);
   size_t sm3 = dft_smem<T>(N, n * n, 0);
   e = cudaFuncSetAttribute(k_idft_k1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
   if (e != cudaSuccess) return e;
@@ -655,7 +683,7 @@ cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const Coll
   size_t sm4 = dft_smem<T>(N, N * n, 0);
   e = cudaFuncSetAttribute(k_idft_k3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
   if (e != cudaSuccess) return e;
-  k_idft_k3<T><<<dim3(C, N), 256, sm4, st>>>(x.sb, f, x.ct, x.theta, x.nu, Q, P, N, x.dv);
+  k_idft_k3<T><<<dim3(C, N), 256, sm4, st>>>(x.sb, f, x.ct, x.theta, x.nu, Q, P, N, x.dv, Qadd);
   return cudaGetLastError();
 }
 
@@ -678,14 +706,14 @@ cudaError_t launch_build_weights(const int4* units, const long long* unit_step0,
   return cudaGetLastError();
 }
 
-template cudaError_t launch_dft<double>(const double*, const CollideCtx<double>&, cudaStream_t);
-template cudaError_t launch_dft<float>(const double*, const CollideCtx<float>&, cudaStream_t);
-template cudaError_t launch_spectral_sum<double>(const CollideCtx<double>&, cudaStream_t);
-template cudaError_t launch_spectral_sum<float>(const CollideCtx<float>&, cudaStream_t);
+template cudaError_t launch_dft<double>(const double*, const CollideCtx<double>&, const DftMode&, cudaStream_t);
+template cudaError_t launch_dft<float>(const double*, const CollideCtx<float>&, const DftMode&, cudaStream_t);
+template cudaError_t launch_spectral_sum<double>(const CollideCtx<double>&, double2*, cudaStream_t);
+template cudaError_t launch_spectral_sum<float>(const CollideCtx<float>&, float2*, cudaStream_t);
 template cudaError_t launch_reduce_idft<double>(const double*, double*, double*, const CollideCtx<double>&,
-                                                cudaStream_t);
+                                                const double2*, const double*, cudaStream_t);
 template cudaError_t launch_reduce_idft<float>(const double*, double*, double*, const CollideCtx<float>&,
-                                               cudaStream_t);
+                                               const float2*, const double*, cudaStream_t);
 template cudaError_t launch_build_weights<double>(const int4*, const long long*, int, int, int, const double*,
                                                   long long, const double*, double*, cudaStream_t);
 template cudaError_t launch_build_weights<float>(const int4*, const long long*, int, int, int, const double*,

@@ -67,6 +67,15 @@ struct SumArgs {
   long long spin_max;
 };
 
+// Inputs of the first DFT pass: mode 0 transforms (f - M, f + M); modes 1 and 2 transform
+// increments against a reference state (f_ref, M[f_ref]): mode 1 gives (Da, f + M), mode 2 gives
+// (unused, Db), where Da = (f - M) - (f_ref - M_ref) and Db = (f + M) - (f_ref + M_ref).
+struct DftMode {
+  int mode;
+  const double* f_ref;
+  const double* theta_ref;
+};
+
 template <typename T>
 struct RedArgs {
   typedef typename CplxOf<T>::type CT;
@@ -74,6 +83,7 @@ struct RedArgs {
   const int* row_start;   // CSR over row_units
   const int* row_units;
   const CT* partial;
+  const CT* partial2;     // optional second set of partials, summed after the first
   CT* qhat;
   int n, G, n_rows;
 };
@@ -117,11 +127,12 @@ cudaError_t launch_moments(const double* f, const CellTables& ct, int C, int N, 
 cudaError_t launch_collide_bgk(const double* f, const CellTables& ct, int C, int N, double dv, const double* theta,
                                const double* nu, double* Q, double* P, cudaStream_t st);
 template <typename T>
-cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, cudaStream_t st);
+cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, const DftMode& md, cudaStream_t st);
 template <typename T>
-cudaError_t launch_spectral_sum(const CollideCtx<T>& x, cudaStream_t st);
+cudaError_t launch_spectral_sum(const CollideCtx<T>& x, typename CplxOf<T>::type* partial, cudaStream_t st);
 template <typename T>
-cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const CollideCtx<T>& x, cudaStream_t st);
+cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const CollideCtx<T>& x,
+                               const typename CplxOf<T>::type* partial2, const double* Qadd, cudaStream_t st);
 template <typename T>
 cudaError_t launch_build_weights(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
                                  const double* G, long long nb, const double* Lo, T* W, cudaStream_t st);

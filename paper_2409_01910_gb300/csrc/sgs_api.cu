@@ -95,8 +95,10 @@ struct sgs_handle {
   char* ws = nullptr;
   struct {
     size_t inst, cell_off, cell_inst, cnt, theta, nu, scratch, tw_cos, tw_sin, G, Lo, units, step0, row_k, row_start,
-        row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, end;
+        row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, partial2, f_ref, Q_ref, theta_ref,
+        ahat_ref, end;
   } off;
+  bool dc_ref = false;  // FP32 collisions use the increment form against the stored reference
   SweepShape sweep{8, 1, 256};
   int sweep_arith = kSweepF64;
   // profiling: per-class CUDA-event pairs recorded on the launching stream
@@ -242,6 +244,13 @@ void layout(sgs_handle* h) {
   f.bhat = take(spec);
   f.qhat = take(spec);
   f.partial = take(sp ? U * G * n * kLanes * cpl : 0);
+  // defect-correction reference state (mixed precision only)
+  bool dc = sp && h->precision == SGS_FP32;
+  f.partial2 = take(dc ? U * G * n * kLanes * sizeof(float2) : 0);
+  f.f_ref = take(dc ? sizeof(double) * h->field : 0);
+  f.Q_ref = take(dc ? sizeof(double) * h->field : 0);
+  f.theta_ref = take(dc ? sizeof(double) * 5 * C : 0);
+  f.ahat_ref = take(dc ? (size_t)G * n * n * n * kLanes * sizeof(float2) : 0);
   f.end = o;
   h->ws_bytes = o;
 }
@@ -431,19 +440,55 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     cudaError_t er;
     {
       Scope sc(h, SGS_PROF_DFT, st, 3);
-      er = launch_dft(f, x, st);
+      er = launch_dft(f, x, DftMode{0, nullptr, nullptr}, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
     {
       Scope sc(h, SGS_PROF_SUM, st, 1);
-      er = launch_spectral_sum(x, st);
+      er = launch_spectral_sum(x, nullptr, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
     Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 4);
-    return cuda_status(launch_reduce_idft(f, Q, P, x, st));
+    return cuda_status(launch_reduce_idft(f, Q, P, x, nullptr, nullptr, st));
+  };
+  // Increment form against the reference f_ref (defect correction): with a = f - M, b = f + M,
+  //   Q(f) = Q_ref + Q_s(a - a_ref, b) + Q_s(a_ref, b - b_ref)   (exact: Q_s is bilinear),
+  // both sums in FP32 on small increments, so the rounding error vanishes as f -> f_ref.
+  auto run_inc = [&](CollideCtx<float> x) -> int {
+    typedef float2 CT;
+    DftMode m1{1, h->at<double>(h->off.f_ref), h->at<double>(h->off.theta_ref)};
+    DftMode m2{2, m1.f_ref, m1.theta_ref};
+    CT* part2 = h->at<CT>(h->off.partial2);
+    cudaError_t er;
+    {
+      Scope sc(h, SGS_PROF_DFT, st, 3);
+      er = launch_dft(f, x, m1, st);
+    }
+    if (er != cudaSuccess) return cuda_status(er);
+    {
+      Scope sc(h, SGS_PROF_SUM, st, 1);
+      er = launch_spectral_sum(x, nullptr, st);
+    }
+    if (er != cudaSuccess) return cuda_status(er);
+    {
+      Scope sc(h, SGS_PROF_DFT, st, 3);
+      er = launch_dft(f, x, m2, st);
+      if (er == cudaSuccess)
+        er = cudaMemcpyAsync(x.sb.ahat, h->at<CT>(h->off.ahat_ref),
+                             (size_t)h->G * h->n * h->n * h->n * kLanes * sizeof(CT), cudaMemcpyDeviceToDevice, st);
+    }
+    if (er != cudaSuccess) return cuda_status(er);
+    {
+      Scope sc(h, SGS_PROF_SUM, st, 1);
+      er = launch_spectral_sum(x, part2, st);
+    }
+    if (er != cudaSuccess) return cuda_status(er);
+    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 4);
+    return cuda_status(launch_reduce_idft(f, Q, P, x, part2, h->at<double>(h->off.Q_ref), st));
   };
   if (precision == SGS_FP32) {
     if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
+    if (h->dc_ref) return run_inc(collide_ctx<float>(h));
     return run(collide_ctx<float>(h));
   }
   return run(collide_ctx<double>(h));
@@ -651,23 +696,43 @@ int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, const double* rh
   return iterate_impl(h, f, Q, P, rhs, flags, res, as_stream(stream));
 }
 
-int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, double* rhs, int lo_iters, double* res, void* stream) {
-  if (!h || !f || !Q || !P || !rhs || lo_iters < 0) return SGS_ERR_ARG;
+int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, int lo_iters, double* res, void* stream) {
+  if (!h || !f || !Q || !P || lo_iters < 0) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;
-  if (h->precision != SGS_FP32) return SGS_ERR_ARG;
+  if (h->precision != SGS_FP32 || !h->spectral) return SGS_ERR_ARG;
   cudaStream_t st = as_stream(stream);
   int r;
-  // FP64 collision and residual of the current iterate: the convergence test
-  if ((r = collide_impl(h, f, Q, nullptr, SGS_FP64, st))) return r;
+  // FP64 collision and residual of the current iterate f_k: the convergence test
+  h->dc_ref = false;
+  if ((r = collide_impl(h, f, Q, P, SGS_FP64, st))) return r;
   if (res && (r = residual_impl(h, f, Q, nullptr, res, st))) return r;
-  // b = R_lo(f_k) - R_hi(f_k) = (Q_hi - Q_lo) / eps; the lo collision also leaves P_lo(f_k)
-  if ((r = collide_impl(h, f, rhs, P, SGS_FP32, st))) return r;
+  // new reference: f_ref = f_k, theta_ref = theta(f_k), Q_ref = Q_FP64(f_k), ahat_ref = FP32 DFT of f_k - M_k
+  cudaError_t e = cudaMemcpyAsync(h->ws + h->off.f_ref, f, sizeof(double) * h->field, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + h->off.Q_ref, Q, sizeof(double) * h->field, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + h->off.theta_ref, h->ws + h->off.theta, sizeof(double) * 5 * h->C,
+                        cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e);
   {
-    Scope sc(h, SGS_PROF_RESCALE, st, 1);
-    if ((r = cuda_status(launch_dc_rhs(aux_args(h), Q, rhs, st)))) return r;
+    CollideCtx<float> x = collide_ctx<float>(h);
+    Scope sc(h, SGS_PROF_DFT, st, 3);
+    e = launch_dft(f, x, DftMode{0, nullptr, nullptr}, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->ws + h->off.ahat_ref, x.sb.ahat,
+                          (size_t)h->G * h->n * h->n * h->n * kLanes * sizeof(float2), cudaMemcpyDeviceToDevice, st);
   }
+  if (e != cudaSuccess) return cuda_status(e);
+  h->dc_ref = true;
+  // P from the FP64 collision is P of f_k in the increment form as well (zero increments)
   for (int it = 0; it < lo_iters; it++)
-    if ((r = iterate_impl(h, f, Q, P, rhs, it == 0 ? SGS_IT_P_VALID : 0, nullptr, st))) return r;
+    if ((r = iterate_impl(h, f, Q, P, nullptr, it == 0 ? SGS_IT_P_VALID : 0, nullptr, st))) return r;
+  return SGS_OK;
+}
+
+int sgs_dc_clear(sgs_handle* h) {
+  if (!h) return SGS_ERR_ARG;
+  h->dc_ref = false;
   return SGS_OK;
 }
 

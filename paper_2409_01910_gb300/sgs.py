@@ -130,7 +130,8 @@ def lib(build: bool = True):
             "sgs_rescale": (C.c_int, [vp, vp, vp]),
             "sgs_residual": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "sgs_iterate": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, vp, vp]),
-            "sgs_dc_step": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, vp, vp]),
+            "sgs_dc_step": (C.c_int, [vp, vp, vp, vp, C.c_int, vp, vp]),
+            "sgs_dc_clear": (C.c_int, [vp]),
             "sgs_profile": (C.c_int, [vp, C.c_int]),
             "sgs_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_ulonglong), C.c_int]),
             "sgs_launch_count": (C.c_ulonglong, [vp]),
@@ -236,9 +237,12 @@ class Solver:
         _check(lib().sgs_iterate(self.h, _ptr(f), _ptr(Q), _ptr(P), _ptr(rhs), flags, _ptr(res), _stream(stream)),
                "sgs_iterate")
 
-    def dc_step(self, f, Q, P, rhs, lo_iters, res=None, stream=None):
-        _check(lib().sgs_dc_step(self.h, _ptr(f), _ptr(Q), _ptr(P), _ptr(rhs), lo_iters, _ptr(res),
-                                 _stream(stream)), "sgs_dc_step")
+    def dc_step(self, f, Q, P, lo_iters, res=None, stream=None):
+        _check(lib().sgs_dc_step(self.h, _ptr(f), _ptr(Q), _ptr(P), lo_iters, _ptr(res), _stream(stream)),
+               "sgs_dc_step")
+
+    def dc_clear(self):
+        _check(lib().sgs_dc_clear(self.h), "sgs_dc_clear")
 
     def profile(self, enable=True):
         _check(lib().sgs_profile(self.h, 1 if enable else 0), "sgs_profile")
