@@ -131,6 +131,22 @@ int sgs_rescale(sgs_handle* h, double* f, void* stream);
  * n_inst doubles) = sqrt(dx sum_j sum_k w R^2) per instance. Q from sgs_collide(f). */
 int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, void* stream);
 
+/* Outer residual of ONE instance that allocates nothing (no counterpart in the paper: it
+ * is a service for callers). Callers that cannot allocate device memory - code inside a
+ * host framework that owns every allocation, code under a hard memory budget, paths where
+ * an allocation could synchronise the device - need neither a handle nor a workspace here:
+ * p describes the instance (fields as for sgs_setup), f and Q (device, p->nx * nv^3
+ * doubles, cells contiguous) and rhs (device, nullable) are the inputs, res (device, one
+ * double) the output, as in sgs_residual. The per-cell partial sums live in a static
+ * device array of the library (32 KiB + 64 B, kept by every GPU that loads the library
+ * until the process exits), so at most 4096 cells are accepted; larger nx returns
+ * SGS_ERR_ARG with a message naming the limit. The first call on a device looks up the
+ * array's device address with that device current; make that first call before any
+ * stream capture. All calls share the array: calls that overlap on the GPU race, so order
+ * them on one stream. Every slot a call reads is written earlier in the same call. */
+int sgs_residual_noalloc(const sgs_problem* p, const double* f, const double* Q, const double* rhs, double* res,
+                         void* stream);
+
 /* Collision step in a chosen arithmetic (SGS_FP32 needs a handle set up with precision
  * SGS_FP32, whose workspace then carries both weight tables). Same fields as sgs_collide. */
 int sgs_collide_prec(sgs_handle* h, const double* f, double* Q, double* P, int precision, void* stream);
