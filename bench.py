@@ -195,7 +195,7 @@ def run_native(args, rank, world, local):
         e2e = end_to_end(s, f, Q, P, wl, args, stream)
 
     # plain FP64 GPU form for comparison (same step, FP64 collision sum and FP64 scan)
-    fp64 = fp64_form(wl, args, f0, dev, stream)
+    fp64 = fp64_form(wl, args, f0, dev, stream) if args.fp64_steps > 0 else None
 
     out = None
     if rank == 0:

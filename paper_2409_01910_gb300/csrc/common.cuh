@@ -82,6 +82,52 @@ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
 __device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
 __device__ __forceinline__ dfloat& operator-=(dfloat& a, dfloat b) { return a = a - b; }
 
+// Exact split of a double into a double-float by bit manipulation (no FP64 instruction):
+// hi keeps the leading 24 significand bits (truncated), lo the next bits rounded to 24.
+// Magnitudes below 2^-100 (irrelevant next to the O(1) values they are summed with) map to 0.
+__device__ __forceinline__ dfloat df_split(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  unsigned int sign = (unsigned int)(u >> 63) << 31;
+  int e = (int)((u >> 52) & 0x7ff) - 1023;
+  if (e < -100) return {0.0f, 0.0f};
+  unsigned long long m = (u & 0xfffffffffffffULL) | 0x10000000000000ULL;  // 53-bit significand
+  unsigned int mh = (unsigned int)(m >> 29);                               // top 24 bits
+  float hi = __int_as_float((int)(sign | ((unsigned int)(e + 127) << 23) | (mh & 0x7fffff)));
+  unsigned int ml = (unsigned int)(m & 0x1fffffffULL);                     // low 29 bits
+  float lo = ldexpf((float)ml, e - 52);
+  return {hi, sign ? -lo : lo};
+}
+
+// exp in double-float arithmetic (no FP64 instruction): Cody and Waite's additive argument
+// reduction x = k ln2 + r with ln2 split into three floats (the first with trailing zero bits,
+// so k * c1 is exact for |k| < 512), then exp(r), |r| <= ln2/2, from its Taylor series to
+// degree 13 by Horner's rule, and exp(x) = 2^k exp(r).
+__device__ inline dfloat df_exp(dfloat x) {
+  const float c1 = 0.693145751953125f, c2 = 1.428606765330187e-06f, c3 = 5.497923148104107e-14f;
+  const float inv_ln2 = 1.4426950408889634f;
+  if (x.hi < -87.0f) return {0.0f, 0.0f};
+  float kf = rintf(x.hi * inv_ln2);
+  // x.hi - kf c1 is exact (kf c1 is exact and, by Sterbenz's lemma, so is the difference)
+  dfloat r = dfloat{x.hi - kf * c1, 0.0f} + dfloat{x.lo, 0.0f};
+  float p = kf * c2;
+  dfloat kc2 = {p, fmaf(kf, c2, -p)};
+  r = r - kc2;
+  r = r - dfloat{kf * c3, 0.0f};
+  const float ch[14] = {1.0f, 1.0f, 0.5f, 0.1666666716337204f, 0.0416666679084301f, 0.008333333767950535f,
+                        0.0013888889225199819f, 0.00019841270113829523f, 2.4801587642286904e-05f,
+                        2.7557318844628753e-06f, 2.755731998149713e-07f, 2.5052107943679403e-08f,
+                        2.0876755879584152e-09f, 1.6059044372074283e-10f};
+  const float cl[14] = {0.0f, 0.0f, 0.0f, -4.967053879312289e-09f, -1.2417634698280722e-09f,
+                        -4.34617203337595e-10f, -3.3631094437103215e-11f, -2.725596874933456e-12f,
+                        -3.40699609366682e-13f, 3.793571224297229e-14f, -7.575112209051195e-15f,
+                        4.4176230446483665e-16f, 1.1082839147459852e-16f, -5.352526511562726e-18f};
+  dfloat acc = {ch[13], cl[13]};
+#pragma unroll
+  for (int n = 12; n >= 0; n--) acc = acc * r + dfloat{ch[n], cl[n]};
+  int k = (int)kf;
+  return {ldexpf(acc.hi, k), ldexpf(acc.lo, k)};
+}
+
 // Conversions used by code templated on the arithmetic type E.
 template <typename E>
 __device__ __forceinline__ E cvt(double x);
@@ -91,12 +137,19 @@ template <>
 __device__ __forceinline__ float cvt<float>(double x) { return (float)x; }
 template <>
 __device__ __forceinline__ dfloat cvt<dfloat>(double x) {
-  float h = (float)x;
-  return {h, (float)(x - (double)h)};
+  return df_split(x);
 }
 __device__ __forceinline__ double tod(double x) { return x; }
 __device__ __forceinline__ double tod(float x) { return (double)x; }
 __device__ __forceinline__ double tod(dfloat x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ float tof(double x) { return (float)x; }
+__device__ __forceinline__ float tof(float x) { return x; }
+__device__ __forceinline__ float tof(dfloat x) { return x.hi; }
+
+// exp in the precision of E without leaving it
+__device__ __forceinline__ double exp_in(double x) { return exp(x); }
+__device__ __forceinline__ float exp_in(float x) { return expf(x); }
+__device__ __forceinline__ dfloat exp_in(dfloat x) { return df_exp(x); }
 
 // exp evaluated in FP64 for double and df64, in FP32 for float
 template <typename E>

@@ -5,16 +5,19 @@
 // single launch. Each thread owns EPT consecutive velocity nodes of one pencil (fixed i1, i2)
 // in every cell, so a thread only ever reads and writes its own nodes: the upwind neighbour's
 // new value is its own earlier write, and no two threads touch the same global element.
-// Every velocity sum (moments, cell-equation residual, step-1 target) is a cluster-wide
-// reduction: per-thread partials -> warp butterfly -> block -> each CTA reads every CTA's
-// partial through distributed shared memory in rank order, so all CTAs hold bit-identical
-// totals and take identical branches. The discrete-Maxwellian Newton solves need only O(N)
-// work on the tensor grid (separable Maxwellian) and run redundantly in warp 0 of every CTA,
-// warm-started from the previous solution of the visit.
 //
-// E is the arithmetic of the elementwise work, the reductions and the Newton residuals:
-// double for the FP64 solver, float for the low-precision smoother of the mixed solver (whose
-// FP64 accuracy comes from the FP64 collision and residual of the defect-correction loop).
+// The visit of a cell is a chain of short dependent steps (velocity sums, Newton solves of
+// the discrete Maxwellian); the kernel is built to shorten that chain:
+//   - a velocity sum: per-thread partials -> warp butterfly -> block -> one thread per
+//     (value, CTA rank) reads the partial through distributed shared memory and a shuffle
+//     tree forms the total, identical in every CTA of the cluster (identical branches);
+//   - a Newton iteration: the Maxwellian is separable, so warps 0, 1, 2 evaluate the
+//     factors and 1-D sums of the three velocity dimensions concurrently, and warp 0
+//     combines them, factorises the Jacobian (FP32: inexact Newton) and updates theta.
+//
+// E is the arithmetic of the elementwise work, the sums and the Newton residuals: double for
+// the FP64 solver, double-float (two FP32 numbers, FP64-class accuracy, no FP64 instruction
+// on the critical path) for the mixed solver, float for experiments at FP32 resolution.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -22,19 +25,34 @@ namespace sgs {
 
 template <typename E>
 struct SweepSmem {
-  E vv[kMaxN];   // nodes v_i
-  E vq[kMaxN];   // v_i^2
-  E E1[kMaxN];   // factors of the Maxwellian in use (E1 carries exp(alpha))
-  E E2[kMaxN];
-  E E3[kMaxN];
-  E W3[2][kMaxN];  // third factor of each wall's unit Maxwellian
+  E vv[kMaxN];         // nodes v_i
+  E vq[kMaxN];         // v_i^2
+  E c1e[kMaxN];        // |v_i| / dx (step-1 weights)
+  E den[kMaxN];        // 1 / (|v_i|/dx + nu/eps) of the current cell
+  E c1A[kMaxN];        // |v_i|/dx + nu/eps of the current cell
+  E ef[3][kMaxN];      // factors of the last Newton evaluation (ef[0] carries exp(alpha))
+  E Eg[3][kMaxN];      // factors of M[g]
+  E Ep[3][kMaxN];      // factors of the step-1 Maxwellian
+  E S[3][5];           // 1-D sums of the last evaluation (unweighted)
+  E S1w[5];            // dimension-1 sums with the step-1 weights |v1|/dx, same evaluation
+  E svE[5];            // step-1 target s
+  E W3[2][kMaxN];      // third factor of each wall's unit Maxwellian
   E red_warp[32][8];
+  E red_tote[8];
+  E thE[5];            // trial theta in E
+  E scal[4];           // per-visit scalars: rho_l, rho_r, nu/eps
   double red_part[2][8];
   double red_tot[8];
-  double thg[5];  // theta of M[g]
-  double thp[5];  // theta of the step-1 Maxwellian
+  double thg[5], thp[5], th_try[5], dir[5];
+  float fn;
+  int flag;
+  int ctl;             // broadcast decisions of thread 0
 };
 
+// ---------------------------------------------------------------------------------------
+// Cluster-wide sum of NV values per thread; tot (double) and sm.red_tote (E) receive the
+// totals, identical in every CTA.
+// ---------------------------------------------------------------------------------------
 template <int NV, typename E>
 __device__ inline void cluster_reduce(E (&v)[NV], double (&tot)[NV], SweepSmem<E>& sm, int& buf,
                                       cg::cluster_group& cl, int CS) {
@@ -51,58 +69,251 @@ __device__ inline void cluster_reduce(E (&v)[NV], double (&tot)[NV], SweepSmem<E
     sm.red_part[buf][threadIdx.x] = tod(t);
   }
   cl.sync();
-  if (threadIdx.x < NV) {
-    double t = 0.0;
-    for (int r = 0; r < CS; r++) {
-      const double* p = cl.map_shared_rank(&sm.red_part[buf][0], r);
-      t += p[threadIdx.x];
+  // one thread per (value q, rank r): lanes of a warp hold segments of CS consecutive ranks
+  if (CS == 1) {
+    if (threadIdx.x < NV) sm.red_tot[threadIdx.x] = sm.red_part[buf][threadIdx.x];
+  } else {
+    const int per_warp = 32 / CS;  // values per warp
+    const int nwarps = (NV + per_warp - 1) / per_warp;
+    if (wid < nwarps) {
+      int q = wid * per_warp + lane / CS, r = lane % CS;
+      double x = 0.0;
+      if (q < NV) x = cl.map_shared_rank(&sm.red_part[buf][0], r)[q];
+      for (int o = CS >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (q < NV && r == 0) sm.red_tot[q] = x;
     }
-    sm.red_tot[threadIdx.x] = t;
   }
   __syncthreads();
+  if (threadIdx.x < NV) sm.red_tote[threadIdx.x] = cvt<E>(sm.red_tot[threadIdx.x]);
 #pragma unroll
   for (int q = 0; q < NV; q++) tot[q] = sm.red_tot[q];
   buf ^= 1;
+  __syncthreads();
 }
 
-// Newton for the (weighted) discrete Maxwellian run by warp 0: warm start from th0 when
-// given, else (or on failure) from the continuum guess. Stores the factors and theta.
+// ---------------------------------------------------------------------------------------
+// Newton for the discrete Maxwellian, executed by the whole CTA with uniform control flow.
+// ---------------------------------------------------------------------------------------
+// Warps 0-2: factors and 1-D sums S_d^p of dimension d at the trial theta in sm.thE.
 template <typename E>
-__device__ inline int newton_store(SweepSmem<E>& sm, int N, double dv, double w, bool wv1, double inv_dx,
-                                   const E* target,
-                                   const double* th0, double* th_out, double tol, int maxit, unsigned& status,
-                                   bool store_on_fail) {
-  const int lane = threadIdx.x & 31;
-  double th[5];
-  MaxwEval<E> ev;
-  int it = -1;
+__device__ __noinline__ void eval_cta(SweepSmem<E>& sm, int N) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (wid < 3) {
+    const int d = wid;
+    E e = cvt<E>(0.0);
+    if (lane < N) {
+      E x = sm.thE[1 + d] * sm.vv[lane] - sm.thE[4] * sm.vq[lane];
+      if (d == 0) x += sm.thE[0];
+      e = exp_in(x);
+    }
+    sm.ef[d][lane] = e;
+    E s[5];
+    s[0] = e;
+    s[1] = e * sm.vv[lane];
+    s[2] = e * sm.vq[lane];
+    s[3] = s[2] * sm.vv[lane];
+    s[4] = s[2] * sm.vq[lane];
+    if (d == 0) {  // the same sums weighted by |v1|/dx as well (step 1, eq. (24))
+      E c = sm.c1e[lane];
+      E s10[10];
+#pragma unroll
+      for (int q = 0; q < 5; q++) {
+        s10[q] = s[q];
+        s10[5 + q] = s[q] * c;
+      }
+      warp_allsum<10, E>(s10);
+      if (lane < 5) {
+        E t = s10[0], tw = s10[5];
+#pragma unroll
+        for (int q = 1; q < 5; q++)
+          if (lane == q) {
+            t = s10[q];
+            tw = s10[5 + q];
+          }
+        sm.S[0][lane] = t;
+        sm.S1w[lane] = tw;
+      }
+    } else {
+      warp_allsum<5, E>(s);
+      if (lane < 5) {
+        E t = s[0];
+#pragma unroll
+        for (int q = 1; q < 5; q++)
+          if (lane == q) t = s[q];
+        sm.S[d][lane] = t;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Warp 0: residual F (E), Jacobian (FP32) and the scaled residual norm from the 1-D sums.
+template <typename E>
+__device__ inline void combine(const SweepSmem<E>& sm, E w, bool wv1, const E* target, E (&F)[5], float (&A)[15],
+                               float& fn) {
+  const E* S1 = wv1 ? sm.S1w : sm.S[0];
+  const E* S2 = sm.S[1];
+  const E* S3 = sm.S[2];
+  E s23 = S2[0] * S3[0];
+  E mom[5] = {S1[0] * s23, S1[1] * s23, S1[0] * (S2[1] * S3[0]), S1[0] * (S2[0] * S3[1]),
+              S1[2] * s23 + S1[0] * (S2[2] * S3[0] + S2[0] * S3[2])};
+  float amax = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    F[i] = w * mom[i] - target[i];
+    amax = fmaxf(amax, fabsf(tof(F[i])));
+  }
+  fn = amax / fabsf(tof(target[0]));
+  float f1[5], f2[5], f3[5];
+#pragma unroll
+  for (int p = 0; p < 5; p++) {
+    f1[p] = tof(S1[p]);
+    f2[p] = tof(S2[p]);
+    f3[p] = tof(S3[p]);
+  }
+  float q11 = f1[2] * f2[0] * f3[0], q22 = f1[0] * f2[2] * f3[0], q33 = f1[0] * f2[0] * f3[2];
+  float q12 = f1[1] * f2[1] * f3[0], q13 = f1[1] * f2[0] * f3[1], q23 = f1[0] * f2[1] * f3[1];
+  float c1 = f1[3] * f2[0] * f3[0] + f1[1] * f2[2] * f3[0] + f1[1] * f2[0] * f3[2];
+  float c2 = f1[2] * f2[1] * f3[0] + f1[0] * f2[3] * f3[0] + f1[0] * f2[1] * f3[2];
+  float c3 = f1[2] * f2[0] * f3[1] + f1[0] * f2[2] * f3[1] + f1[0] * f2[0] * f3[3];
+  float e4 = f1[4] * f2[0] * f3[0] + f1[0] * f2[4] * f3[0] + f1[0] * f2[0] * f3[4] +
+             2.0f * (f1[2] * f2[2] * f3[0] + f1[2] * f2[0] * f3[2] + f1[0] * f2[2] * f3[2]);
+  float cf = tof(w);
+  float Aa[15] = {f1[0] * f2[0] * f3[0], f1[1] * f2[0] * f3[0], f1[0] * f2[1] * f3[0], f1[0] * f2[0] * f3[1],
+                  q11 + q22 + q33, q11, q12, q13, c1, q22, q23, c2, q33, c3, e4};
+#pragma unroll
+  for (int i = 0; i < 15; i++) A[i] = cf * Aa[i];
+}
+
+// Newton from the theta in th (shared memory). With have_eval the last evaluation (sm.S,
+// sm.S1w, sm.ef) is already at th and is reused. On success th holds the root, the last
+// evaluation is at th, and the return value is the iteration count; -1 on failure. Scalar
+// FP64 decisions are taken by thread 0 and broadcast (FP64 is scarce on this GPU).
+template <typename E>
+__device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, bool wv1, const E* target, double* th,
+                                       double L, double tol, int maxit, bool have_eval) {
+  const int wid = threadIdx.x >> 5, tid = threadIdx.x;
+  if (!have_eval) {
+    if (tid < 5) sm.thE[tid] = cvt<E>(th[tid]);
+    __syncthreads();
+    eval_cta<E>(sm, N);
+  }
+  E F[5];
+  float A[15], fnv = 0.0f;
+  if (wid == 0) {
+    combine<E>(sm, w, wv1, target, F, A, fnv);
+    if (tid == 0) sm.fn = fnv;
+  }
+  __syncthreads();
+  float fn_cur = sm.fn;
+  for (int it = 0; it < maxit; it++) {
+    if (wid == 0) {
+      float y[5], Ff[5];
+#pragma unroll
+      for (int i = 0; i < 5; i++) Ff[i] = tof(F[i]);
+      bool ok = chol5_solve(A, Ff, y);
+      if (tid == 0) {
+        sm.flag = ok;
+        sm.dir[0] = -(double)y[0];
+        sm.dir[1] = -(double)y[1];
+        sm.dir[2] = -(double)y[2];
+        sm.dir[3] = -(double)y[3];
+        sm.dir[4] = (double)y[4];  // -D A^{-1} F, D = diag(1,1,1,1,-1)
+      }
+    }
+    __syncthreads();
+    if (!sm.flag) return -1;
+    float lam = 1.0f;
+    for (int hv = 0; hv < 40; hv++) {
+      if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+          double t = th[k] + (double)lam * sm.dir[k];
+          sm.th_try[k] = t;
+          sm.thE[k] = cvt<E>(t);
+        }
+      }
+      __syncthreads();
+      eval_cta<E>(sm, N);
+      if (wid == 0) {
+        combine<E>(sm, w, wv1, target, F, A, fnv);
+        if (tid == 0) sm.fn = fnv;
+      }
+      __syncthreads();
+      float fnt = sm.fn;
+      if (fnt == fnt && (fnt <= fn_cur || fnt <= 1e-10f)) {
+        fn_cur = fnt;
+        break;
+      }
+      lam *= 0.5f;
+    }
+    if (tid == 0) {
+      double step = (double)lam * (fabs(sm.dir[0]) + L * (fabs(sm.dir[1]) + fabs(sm.dir[2]) + fabs(sm.dir[3])) +
+                                   L * L * fabs(sm.dir[4]));
+#pragma unroll
+      for (int k = 0; k < 5; k++) th[k] = sm.th_try[k];
+      sm.ctl = !(step == step) ? -1 : (step <= tol ? 1 : 0);
+    }
+    __syncthreads();
+    int c = sm.ctl;
+    if (c < 0) return -1;
+    if (c > 0) return it + 1;
+  }
+  return -1;
+}
+
+template <typename E>
+__device__ inline void copy_factors(SweepSmem<E>& sm, E (*dst)[kMaxN]) {
+  if (threadIdx.x < 3 * kMaxN) {
+    int d = threadIdx.x / kMaxN, i = threadIdx.x % kMaxN;
+    dst[d][i] = sm.ef[d][i];
+  }
+  __syncthreads();
+}
+
+// M[g] of the moments in mom: warm start from th0 (if any; have_eval: the last evaluation is
+// at th0), then from the continuum Maxwellian; on failure keeps th0 (status reported).
+// Result in sm.thg and sm.Eg; the last evaluation is at sm.thg afterwards.
+template <typename E>
+__device__ __noinline__ int solve_mg(SweepSmem<E>& sm, int N, E w, const E* mom, const double* th0, bool have_eval,
+                                     double L, double tol, int maxit, unsigned& status) {
+  const int tid = threadIdx.x;
+  double keep[5];
   if (th0) {
 #pragma unroll
-    for (int k = 0; k < 5; k++) th[k] = th0[k];
-    it = maxwellian_newton<E>(N, dv, w, wv1, inv_dx, target, th, tol, maxit, ev);
+    for (int k = 0; k < 5; k++) keep[k] = th0[k];
   }
-  if (it < 0 && !wv1) {
-    if (continuum_guess<E>(target, th)) it = maxwellian_newton<E>(N, dv, w, wv1, inv_dx, target, th, tol, maxit, ev);
-    else status |= SGS_ST_NONPOSITIVE;
+  __syncthreads();
+  int it = -1;
+  if (th0) {
+    if (tid < 5) sm.thg[tid] = keep[tid];
+    __syncthreads();
+    it = newton_cta<E>(sm, N, w, false, mom, sm.thg, L, tol, maxit, have_eval);
   }
-  if (it < 0 && !wv1) status |= SGS_ST_NEWTON_FAIL;
-  if (it > 0 || store_on_fail) {
-    if (it < 0) {
-      // keep the last usable theta (warm start) so the sweep can continue and report
-      if (th0) {
-#pragma unroll
-        for (int k = 0; k < 5; k++) th[k] = th0[k];
-      }
-      maxw_eval<E>(N, dv, w, wv1, inv_dx, target, th, ev);
+  if (it < 0) {
+    if (tid == 0) {
+      double tg[5];
+      bool ok = continuum_guess<E>(mom, tg);
+      sm.ctl = ok;
+      if (ok)
+        for (int k = 0; k < 5; k++) sm.thg[k] = tg[k];
     }
-    __syncwarp();
-    if (lane < N) {
-      sm.E1[lane] = ev.e[0];
-      sm.E2[lane] = ev.e[1];
-      sm.E3[lane] = ev.e[2];
+    __syncthreads();
+    if (sm.ctl) {
+      it = newton_cta<E>(sm, N, w, false, mom, sm.thg, L, tol, maxit, false);
+    } else {
+      status |= SGS_ST_NONPOSITIVE;
     }
-    if (lane < 5) th_out[lane] = th[lane];
   }
+  if (it < 0) {
+    status |= SGS_ST_NEWTON_FAIL;
+    if (th0 && tid < 5) sm.thg[tid] = keep[tid];
+    __syncthreads();
+    if (tid < 5) sm.thE[tid] = cvt<E>(sm.thg[tid]);
+    __syncthreads();
+    eval_cta<E>(sm, N);
+  }
+  copy_factors<E>(sm, sm.Eg);
   return it;
 }
 
@@ -115,21 +326,24 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   const InstDev& I = a.inst[q];
   __shared__ SweepSmem<E> sm;
   const int N = a.N, K = N * N * N;
-  const double dv = a.dv, w = a.dv * a.dv * a.dv;
+  const double dv = a.dv, wd = a.dv * a.dv * a.dv;
+  const E w = cvt<E>(wd);
   const int J = I.J;
   const double inv_dx = 1.0 / I.dx;
-  const E inv_eps = cvt<E>(1.0 / I.eps);
-  const int tid = threadIdx.x, wid = tid >> 5;
+  const double L = node(N - 1, N, dv);
+  const int tid = threadIdx.x;
   const bool pfp = I.inner_method == SGS_PFP;
-  const bool lowp = sizeof(E) == 4;  // plain FP32 (not df64): tolerances at FP32 resolution
+  const bool lowp = sizeof(E) == 4;  // plain FP32: tolerances at FP32 resolution
   const double ntol = lowp ? fmax(I.newton_tol, 1e-5) : I.newton_tol;
+  const E inv_eps = cvt<E>(1.0 / I.eps);
   const E zero = cvt<E>(0.0);
-  if (tid < N) {
-    double v = node(tid, N, dv);
+  if (tid < kMaxN) {
+    double v = tid < N ? node(tid, N, dv) : 0.0;
     sm.vv[tid] = cvt<E>(v);
     sm.vq[tid] = cvt<E>(v * v);
-    sm.W3[0][tid] = cvt<E>(I.wall[0][2][tid]);
-    sm.W3[1][tid] = cvt<E>(I.wall[1][2][tid]);
+    sm.c1e[tid] = cvt<E>(fabs(v) * inv_dx);
+    sm.W3[0][tid] = cvt<E>(tid < N ? I.wall[0][2][tid] : 0.0);
+    sm.W3[1][tid] = cvt<E>(tid < N ? I.wall[1][2][tid] : 0.0);
   }
   __syncthreads();
 
@@ -139,11 +353,11 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   const bool own = e0 < K;
   const int pen = own ? e0 / N : 0, i30 = own ? e0 % N : 0;
   const int i1 = pen / N, i2 = pen % N;
-  const double v1d = node(i1, N, dv), v2d = node(i2, N, dv);
-  const E v1 = cvt<E>(v1d), v2 = cvt<E>(v2d);
-  const E c1 = cvt<E>(fabs(v1d) * inv_dx);
+  const double v1d = node(i1, N, dv);
+  const E v1 = sm.vv[i1], v2 = sm.vv[i2];
+  const E c1 = sm.c1e[i1];
   const E vpd = cvt<E>(fmax(v1d, 0.0) * inv_dx), vmd = cvt<E>(fmin(v1d, 0.0) * inv_dx);
-  const E vq12 = cvt<E>(v1d * v1d + v2d * v2d);
+  const E vq12 = sm.vq[i1] + sm.vq[i2];
   const E wl12 = cvt<E>(I.wall[0][0][i1] * I.wall[0][1][i2]);
   const E wr12 = cvt<E>(I.wall[1][0][i1] * I.wall[1][1][i2]);
 
@@ -177,16 +391,23 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     cluster_reduce<7, E>(m7, t7, sm, buf, cl, CS);
     E mom[5];
 #pragma unroll
-    for (int k = 0; k < 5; k++) mom[k] = cvt<E>(w * t7[k]);
-    const E rho_l = cvt<E>(I.bc_kind[0] == SGS_INFLOW ? I.bc_rho[0] : -(w * t7[5]) / I.wall_denom[0]);
-    const E rho_r = cvt<E>(I.bc_kind[1] == SGS_INFLOW ? I.bc_rho[1] : -(w * t7[6]) / I.wall_denom[1]);
+    for (int k = 0; k < 5; k++) mom[k] = w * sm.red_tote[k];
+    if (tid < N) {
+      const double Ad = a.nu[I.cell0 + j] / I.eps;
+      double c = fabs(node(tid, N, dv)) * inv_dx + Ad;
+      sm.c1A[tid] = cvt<E>(c);
+      sm.den[tid] = cvt<E>(1.0 / c);
+      if (tid == 0) {
+        sm.scal[0] = cvt<E>(I.bc_kind[0] == SGS_INFLOW ? I.bc_rho[0] : -(wd * t7[5]) / I.wall_denom[0]);
+        sm.scal[1] = cvt<E>(I.bc_kind[1] == SGS_INFLOW ? I.bc_rho[1] : -(wd * t7[6]) / I.wall_denom[1]);
+        sm.scal[2] = cvt<E>(Ad);
+      }
+    }
+    __syncthreads();
+    const E rho_l = sm.scal[0], rho_r = sm.scal[1], Acoef = sm.scal[2];
+    const E c1A = sm.c1A[i1], den = sm.den[i1];
 
     // ---- r = (-v1^+ f_{j-1} + v1^- f_{j+1}) / dx - P_j / eps - b_j (neighbours: latest values)
-    const double nuj = a.nu[I.cell0 + j];
-    const double Ad = nuj / I.eps;
-    const E Acoef = cvt<E>(Ad);
-    const E den = cvt<E>(1.0 / (fabs(v1d) * inv_dx + Ad));
-    const E c1A = cvt<E>(fabs(v1d) * inv_dx + Ad);
     if (own) {
       const double* Pj = a.P + cbase;
       const double* bj = a.rhs ? a.rhs + cbase : nullptr;
@@ -194,37 +415,36 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       for (int t = 0; t < EPT; t++) {
         E left = lw ? rho_l * wl12 * sm.W3[0][i30 + t] : cvt<E>(fj[t - K]);
         E right = rw ? rho_r * wr12 * sm.W3[1][i30 + t] : cvt<E>(fj[t + K]);
-        double pb = Pj[t] / I.eps + (bj ? bj[t] : 0.0);
-        r[t] = vmd * right - vpd * left - cvt<E>(pb);
+        E rv = vmd * right - vpd * left - cvt<E>(Pj[t]) * inv_eps;
+        if (bj) rv -= cvt<E>(bj[t]);
+        r[t] = rv;
       }
     }
 
-    // ---- M[g] of the stored value (warm start from the previous cell's M[g])
-    if (wid == 0) {
-      int n0 = newton_store<E>(sm, N, dv, w, false, 0.0, mom, have_th ? sm.thg : nullptr, sm.thg, ntol,
-                               I.newton_max, status, true);
+    // ---- M[g] of the stored value (warm start from the previous cell's M[g], whose
+    //      evaluation is still the last one)
+    {
+      int n0 = solve_mg<E>(sm, N, w, mom, have_th ? sm.thg : nullptr, have_th, L, ntol, I.newton_max, status);
       if (n0 > 0) c_newton += n0;
       c_solves++;
     }
     have_th = true;
-    __syncthreads();
 
     int it = 0;
     for (;;) {
       // ---- pass B: cell-equation residual, its scale, and the step-1 target s (eq. (26))
-      E e12 = sm.E1[i1] * sm.E2[i2];
+      E e12 = sm.Eg[0][i1] * sm.Eg[1][i2];
       E rs = zero, sc = zero, b0 = zero, b3 = zero, b4 = zero;
       if (own) {
 #pragma unroll
         for (int t = 0; t < EPT; t++) {
-          E M = e12 * sm.E3[i30 + t];
-          E d = M - g[t];
+          E M = e12 * sm.Eg[2][i30 + t];
           // (|v1|/dx) g + r - (nu/eps)(M - g) = (|v1|/dx + nu/eps) g + r - (nu/eps) M
           E res = c1A * g[t] + r[t] - Acoef * M;
           rs += res * res;
           E mag = c1A * g[t];
           sc += mag * mag;
-          E tt = c1 * d - r[t];
+          E tt = c1 * (M - g[t]) - r[t];
           b0 += tt;
           b3 += tt * sm.vv[i30 + t];
           b4 += tt * sm.vq[i30 + t];
@@ -233,50 +453,60 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       E v7[7] = {rs, b0, v1 * b0, v2 * b0, b3, vq12 * b0 + b4, sc};
       double t6[7];
       cluster_reduce<7, E>(v7, t6, sm, buf, cl, CS);
-      const double res = sqrt(w * t6[0]);
-      double tol = I.inner_tol;
-      if (lowp) tol = fmax(tol, 2e-6 * sqrt(w * t6[6]));
-      bool stop;
-      if (I.inner_fixed > 0) {
-        stop = it >= I.inner_fixed;
-      } else {
-        stop = res < tol || it >= I.inner_max;
-        if (stop && !(res < tol)) status |= SGS_ST_INNER_CAP;
-      }
-      if (!(res == res)) {
-        status |= SGS_ST_NONFINITE;
-        stop = true;
-      }
-      if (stop) break;
-
-      // ---- step 1 (eq. (24)) from M[g]; else the plain fixed-point step (eq. (22))
-      bool used = false;  // meaningful in warp 0 only
-      if (wid == 0) {
-        double sd[5] = {w * t6[1], w * t6[2], w * t6[3], w * t6[4], w * t6[5]};
-        if (pfp) {
-          bool exists = sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
-          if (exists) {
-            E sv[5] = {cvt<E>(sd[0]), cvt<E>(sd[1]), cvt<E>(sd[2]), cvt<E>(sd[3]), cvt<E>(sd[4])};
-            int n1 = newton_store<E>(sm, N, dv, w, true, inv_dx, sv, sm.thg, sm.thp, ntol, I.newton_max, status,
-                                     false);
-            c_solves++;
-            if (n1 > 0) {
-              c_newton += n1;
-              used = true;
-            }
-          }
-          if (!used) c_fallback++;
+      // thread 0 decides: stop, and whether step 1 is attempted (existence test, eq. (26))
+      if (tid == 0) {
+        const double res = sqrt(wd * t6[0]);
+        double tol = I.inner_tol;
+        if (lowp) tol = fmax(tol, 2e-6 * sqrt(wd * t6[6]));
+        bool stop;
+        if (I.inner_fixed > 0) {
+          stop = it >= I.inner_fixed;
+        } else {
+          stop = res < tol || it >= I.inner_max;
+          if (stop && !(res < tol)) status |= SGS_ST_INNER_CAP;
         }
+        if (!(res == res)) {
+          status |= SGS_ST_NONFINITE;
+          stop = true;
+        }
+        double sd[5] = {wd * t6[1], wd * t6[2], wd * t6[3], wd * t6[4], wd * t6[5]};
+        bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+        sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
       }
       __syncthreads();
+      const int ctl = sm.ctl;
+      if (ctl & 1) break;
+
+      // ---- step 1 (eq. (24)) from M[g]; else the plain fixed-point step (eq. (22))
+      bool used = false;
+      if (pfp) {
+        if (ctl & 2) {
+          E sv[5];
+#pragma unroll
+          for (int k = 0; k < 5; k++) sv[k] = w * sm.red_tote[1 + k];
+          if (tid < 5) sm.thp[tid] = sm.thg[tid];
+          __syncthreads();
+          // the last evaluation is M[g]'s: reused as the first one of step 1
+          int n1 = newton_cta<E>(sm, N, w, true, sv, sm.thp, L, ntol, I.newton_max, true);
+          c_solves++;
+          if (n1 > 0) {
+            c_newton += n1;
+            used = true;
+            copy_factors<E>(sm, sm.Ep);
+          }
+        }
+        if (!used) c_fallback++;
+      }
+      const bool eval_at_start = used || !(ctl & 2);  // last evaluation at the warm start below
+      E (*Eu)[kMaxN] = used ? sm.Ep : sm.Eg;
 
       // ---- step 2 (eq. (25)) and the moments of the new iterate
-      E ep = sm.E1[i1] * sm.E2[i2];
+      E ep = Eu[0][i1] * Eu[1][i2];
       E c0 = zero, c3 = zero, c4 = zero;
       if (own) {
 #pragma unroll
         for (int t = 0; t < EPT; t++) {
-          E x = (Acoef * (ep * sm.E3[i30 + t]) - r[t]) * den;
+          E x = (Acoef * (ep * Eu[2][i30 + t]) - r[t]) * den;
           g[t] = x;
           c0 += x;
           c3 += x * sm.vv[i30 + t];
@@ -287,15 +517,13 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       double t5[5];
       cluster_reduce<5, E>(m5, t5, sm, buf, cl, CS);
       it++;
-      if (wid == 0) {
-        E mm[5] = {cvt<E>(w * t5[0]), cvt<E>(w * t5[1]), cvt<E>(w * t5[2]), cvt<E>(w * t5[3]), cvt<E>(w * t5[4])};
-        // warm start: the step-1 Maxwellian approximates M of the updated iterate
-        int n2 = newton_store<E>(sm, N, dv, w, false, 0.0, mm, used ? sm.thp : sm.thg, sm.thg, ntol,
-                                 I.newton_max, status, true);
-        if (n2 > 0) c_newton += n2;
-        c_solves++;
-      }
-      __syncthreads();
+      E mm[5];
+#pragma unroll
+      for (int k = 0; k < 5; k++) mm[k] = w * sm.red_tote[k];
+      // warm start: the step-1 Maxwellian approximates M of the updated iterate
+      int n2 = solve_mg<E>(sm, N, w, mm, used ? sm.thp : sm.thg, eval_at_start, L, ntol, I.newton_max, status);
+      if (n2 > 0) c_newton += n2;
+      c_solves++;
     }
 
     if (own) {
@@ -320,7 +548,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
 }
 
 // Default launch shape: nodes per thread (a divisor of N), cluster size (a power of two, at
-// most 16) and threads per CTA (a multiple of 32, at most 256).
+// most 16) and threads per CTA (a multiple of 32 in [96, 256]; warps 0-2 serve the Newton
+// evaluations).
 SweepShape sweep_shape(int N, int arith) {
   SweepShape s;
   int K = N * N * N;
@@ -329,6 +558,7 @@ SweepShape sweep_shape(int N, int arith) {
   s.cluster = 1;
   while (s.cluster < 16 && s.cluster * 256 < threads) s.cluster *= 2;
   s.tpb = ((threads + s.cluster - 1) / s.cluster + 31) / 32 * 32;
+  if (s.tpb < 96) s.tpb = 96;
   return s;
 }
 
@@ -370,7 +600,9 @@ static cudaError_t launch_sweep_e(const SweepArgs& a, const SweepShape& sh, cuda
 bool sweep_shape_valid(int N, const SweepShape& sh) {
   int K = N * N * N;
   if (sh.ept <= 0 || N % sh.ept != 0) return false;
-  if (sh.cluster < 1 || sh.cluster > 16 || sh.tpb < 32 || sh.tpb > 256 || sh.tpb % 32) return false;
+  if (sh.cluster < 1 || sh.cluster > 16 || (sh.cluster & (sh.cluster - 1))) return false;
+  if (sh.tpb < 96 || sh.tpb > 256 || sh.tpb % 32) return false;
+  if (sh.tpb < 32 * ((8 * sh.cluster + 31) / 32)) return false;  // warps for the cluster gather
   if ((long long)sh.cluster * sh.tpb * sh.ept < K) return false;
   int e[] = {2, 4, 8, 12, 16, 20, 24, 28, 32};
   for (int x : e)
