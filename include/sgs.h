@@ -174,10 +174,16 @@ int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, const double* rh
 int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, int lo_iters, double* res, void* stream);
 int sgs_dc_clear(sgs_handle* h);
 
-/* One FAS V-cycle (eq. (30)) on every instance: levels >= 2 grids with H = 2h (each level's
- * cell count must be even), pre/post SGS smoothing iterations, coarse_iters iterations on
- * the coarsest grid. Coarse fields live in the workspace. */
+/* One FAS V-cycle (eq. (30)) on every instance, on 2 <= levels <= sgs_max_levels(h) grids
+ * with H = 2h: pre SGS-PFP iterations, restriction of f and of the residual field (mean of
+ * the two children), coarse right-hand side b_H = R_H(I f) + I(b_h - R_h(f)), recursion
+ * (coarse_iters SGS iterations on the coarsest grid), correction f += P(f_H - I f) by
+ * piecewise-constant prolongation, post SGS iterations. The mass rescale acts on the finest
+ * grid only. Coarse tables and fields live in the workspace. With an active defect-
+ * correction reference (sgs_dc_step) the finest-grid FP32 collisions use the increment form. */
 int sgs_vcycle(sgs_handle* h, double* f, int levels, int pre, int post, int coarse_iters, void* stream);
+/* Number of grids available to sgs_vcycle: 1 + how often every instance's cell count halves. */
+int sgs_max_levels(const sgs_handle* h);
 
 /* Kernel-time profiling. When enabled, every group of launches is bracketed by CUDA events
  * recorded on the launching stream; sgs_profile_read synchronises on them and returns, per

@@ -99,6 +99,16 @@ struct sgs_handle {
         ahat_ref, end;
   } off;
   bool dc_ref = false;  // FP32 collisions use the increment form against the stored reference
+  // multigrid levels: lev[0] is the bound grid (tables at off.inst, off.cell_off, off.cell_inst);
+  // level l has every instance's cell count halved l times and its own tables and fields
+  struct Level {
+    int C = 0, G = 0;
+    size_t inst = 0, cell_off = 0, cell_inst = 0, f = 0, f0 = 0, b = 0, Q = 0, P = 0, R = 0;
+    std::vector<InstDev> hinst;
+    std::vector<long long> hcell_off;
+    std::vector<int> hcell_inst;
+  };
+  std::vector<Level> lev;
   SweepShape sweep{8, 1, 256};
   int sweep_arith = kSweepF64;
   // profiling: per-class CUDA-event pairs recorded on the launching stream
@@ -251,6 +261,26 @@ void layout(sgs_handle* h) {
   f.Q_ref = take(dc ? sizeof(double) * h->field : 0);
   f.theta_ref = take(dc ? sizeof(double) * 5 * C : 0);
   f.ahat_ref = take(dc ? (size_t)G * n * n * n * kLanes * sizeof(float2) : 0);
+  size_t K = (size_t)N * N * N;
+  int nl = (int)h->lev.size();
+  for (int l = 0; l < nl; l++) {
+    auto& L = h->lev[l];
+    if (l == 0) {
+      L.inst = f.inst;
+      L.cell_off = f.cell_off;
+      L.cell_inst = f.cell_inst;
+    } else {
+      L.inst = take(sizeof(InstDev) * h->n_inst);
+      L.cell_off = take(sizeof(long long) * L.C);
+      L.cell_inst = take(sizeof(int) * L.C);
+      L.f = take(sizeof(double) * K * L.C);
+      L.f0 = take(sizeof(double) * K * L.C);
+      L.b = take(sizeof(double) * K * L.C);
+      L.Q = take(sizeof(double) * K * L.C);
+      L.P = take(sizeof(double) * K * L.C);
+    }
+    if (l + 1 < nl) L.R = take(sizeof(double) * K * L.C);
+  }
   f.end = o;
   h->ws_bytes = o;
 }
@@ -357,38 +387,40 @@ struct Scope {
   }
 };
 
-AuxArgs aux_args(const sgs_handle* h) {
+AuxArgs aux_args(const sgs_handle* h, int l = 0) {
+  const auto& L = h->lev[l];
   AuxArgs a;
-  a.inst = h->at<InstDev>(h->off.inst);
+  a.inst = h->at<InstDev>(L.inst);
   a.n_inst = h->n_inst;
   a.N = h->N;
-  a.C = h->C;
+  a.C = L.C;
   a.dv = h->dv;
-  a.cell_off = h->at<long long>(h->off.cell_off);
-  a.cell_inst = h->at<int>(h->off.cell_inst);
+  a.cell_off = h->at<long long>(L.cell_off);
+  a.cell_inst = h->at<int>(L.cell_inst);
   a.scratch = h->at<double>(h->off.scratch);
   return a;
 }
 
-CellTables cell_tables(const sgs_handle* h) {
+CellTables cell_tables(const sgs_handle* h, int l = 0) {
+  const auto& L = h->lev[l];
   CellTables ct;
-  ct.inst = h->at<InstDev>(h->off.inst);
-  ct.cell_off = h->at<long long>(h->off.cell_off);
-  ct.cell_inst = h->at<int>(h->off.cell_inst);
+  ct.inst = h->at<InstDev>(L.inst);
+  ct.cell_off = h->at<long long>(L.cell_off);
+  ct.cell_inst = h->at<int>(L.cell_inst);
   return ct;
 }
 
 template <typename T>
-CollideCtx<T> collide_ctx(const sgs_handle* h) {
+CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0) {
   typedef typename CplxOf<T>::type CT;
   CollideCtx<T> x;
   x.N = h->N;
-  x.C = h->C;
+  x.C = h->lev[l].C;
   x.H = h->H;
   x.NW = h->NW;
   x.n_units = (int)h->units.size();
   x.dv = h->dv;
-  x.ct = cell_tables(h);
+  x.ct = cell_tables(h, l);
   x.theta = h->at<double>(h->off.theta);
   x.nu = h->at<double>(h->off.nu);
   x.sb.tw_cos = h->at<double>(h->off.tw_cos);
@@ -406,7 +438,7 @@ CollideCtx<T> collide_ctx(const sgs_handle* h) {
   x.sum.ahat = x.sb.ahat;
   x.sum.bhat = x.sb.bhat;
   x.sum.partial = h->at<CT>(h->off.partial);
-  x.sum.G = h->G;
+  x.sum.G = h->lev[l].G;
   x.sum.cnt = h->at<Counters>(h->off.cnt);
   x.sum.spin_max = h->spin_max;
   x.red.row_k = h->at<int2>(h->off.row_k);
@@ -415,26 +447,27 @@ CollideCtx<T> collide_ctx(const sgs_handle* h) {
   x.red.partial = x.sum.partial;
   x.red.qhat = x.sb.qhat;
   x.red.n = h->n;
-  x.red.G = h->G;
+  x.red.G = h->lev[l].G;
   x.red.n_rows = (int)h->row_k.size();
   return x;
 }
 
-int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int precision, cudaStream_t st) {
-  CellTables ct = cell_tables(h);
+int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int precision, cudaStream_t st, int l = 0) {
+  CellTables ct = cell_tables(h, l);
+  const int C = h->lev[l].C;
   double* theta = h->at<double>(h->off.theta);
   double* nu = h->at<double>(h->off.nu);
   const sgs_problem& p0 = h->prob[0];
   cudaError_t e;
   {
     Scope sc(h, SGS_PROF_MOMENTS, st, 1);
-    e = launch_moments(f, ct, h->C, h->N, h->dv, p0.newton_tol, p0.newton_max, theta, nu,
+    e = launch_moments(f, ct, C, h->N, h->dv, p0.newton_tol, p0.newton_max, theta, nu,
                        h->at<Counters>(h->off.cnt), st);
   }
   if (e != cudaSuccess) return cuda_status(e);
   if (!h->spectral) {
     Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 1);
-    return cuda_status(launch_collide_bgk(f, ct, h->C, h->N, h->dv, theta, nu, Q, P, st));
+    return cuda_status(launch_collide_bgk(f, ct, C, h->N, h->dv, theta, nu, Q, P, st));
   }
   auto run = [&](auto x) -> int {
     cudaError_t er;
@@ -488,15 +521,15 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
   };
   if (precision == SGS_FP32) {
     if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
-    if (h->dc_ref) return run_inc(collide_ctx<float>(h));
-    return run(collide_ctx<float>(h));
+    if (h->dc_ref && l == 0) return run_inc(collide_ctx<float>(h, l));
+    return run(collide_ctx<float>(h, l));
   }
-  return run(collide_ctx<double>(h));
+  return run(collide_ctx<double>(h, l));
 }
 
-int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int dir, cudaStream_t st) {
+int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int dir, cudaStream_t st, int l = 0) {
   SweepArgs a;
-  a.inst = h->at<InstDev>(h->off.inst);
+  a.inst = h->at<InstDev>(h->lev[l].inst);
   a.n_inst = h->n_inst;
   a.f = f;
   a.P = P;
@@ -515,27 +548,88 @@ int rescale_impl(sgs_handle* h, double* f, cudaStream_t st) {
   return cuda_status(launch_rescale(aux_args(h), f, st));
 }
 
-int residual_impl(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, cudaStream_t st) {
+int residual_impl(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, cudaStream_t st,
+                  int l = 0) {
   Scope sc(h, SGS_PROF_RESIDUAL, st, res ? 3 : 2);
-  return cuda_status(launch_residual(aux_args(h), f, Q, rhs, res, st));
+  return cuda_status(launch_residual(aux_args(h, l), f, Q, rhs, res, st));
+}
+
+int residual_field_impl(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* R,
+                        cudaStream_t st, int l) {
+  Scope sc(h, SGS_PROF_RESIDUAL, st, 2);
+  return cuda_status(launch_residual_field(aux_args(h, l), f, Q, rhs, R, st));
 }
 
 int iterate_impl(sgs_handle* h, double* f, double* Q, double* P, const double* rhs, int flags, double* res,
-                 cudaStream_t st) {
+                 cudaStream_t st, int l = 0) {
   int r;
   if (!(flags & SGS_IT_P_VALID)) {
-    r = collide_impl(h, f, nullptr, P, h->precision, st);
+    r = collide_impl(h, f, nullptr, P, h->precision, st, l);
     if (r) return r;
   }
-  if ((r = sweep_impl(h, f, P, rhs, +1, st))) return r;
-  if ((r = collide_impl(h, f, nullptr, P, h->precision, st))) return r;
-  if ((r = sweep_impl(h, f, P, rhs, -1, st))) return r;
-  if ((r = rescale_impl(h, f, st))) return r;
+  if ((r = sweep_impl(h, f, P, rhs, +1, st, l))) return r;
+  if ((r = collide_impl(h, f, nullptr, P, h->precision, st, l))) return r;
+  if ((r = sweep_impl(h, f, P, rhs, -1, st, l))) return r;
+  if (l == 0 && (r = rescale_impl(h, f, st))) return r;
   if (flags & SGS_IT_EVAL) {
     if (!Q) return SGS_ERR_ARG;
-    if ((r = collide_impl(h, f, Q, P, h->precision, st))) return r;
-    if (res && (r = residual_impl(h, f, Q, rhs, res, st))) return r;
+    if ((r = collide_impl(h, f, Q, P, h->precision, st, l))) return r;
+    if (res && (r = residual_impl(h, f, Q, rhs, res, st, l))) return r;
   }
+  return SGS_OK;
+}
+
+// FAS V-cycle (eq. (30)) from level l down to level levels-1; f and b are level-l fields
+// (b may be null on the finest level).
+int vcycle_impl(sgs_handle* h, int l, int levels, double* f, const double* b, int pre, int post, int coarse_iters,
+                cudaStream_t st) {
+  auto& L = h->lev[l];
+  const long long K = (long long)h->N * h->N * h->N;
+  double* Qs = l == 0 ? h->at<double>(h->lev[0].R) : h->at<double>(L.Q);  // scratch for P/Q of this level
+  double* Ps = l == 0 ? nullptr : h->at<double>(L.P);
+  int r;
+  if (l == levels - 1) {
+    for (int it = 0; it < coarse_iters; it++)
+      if ((r = iterate_impl(h, f, nullptr, Ps ? Ps : Qs, b, 0, nullptr, st, l))) return r;
+    return SGS_OK;
+  }
+  double* Pl = Ps ? Ps : h->at<double>(h->lev[0].R);
+  for (int it = 0; it < pre; it++)
+    if ((r = iterate_impl(h, f, nullptr, Pl, b, 0, nullptr, st, l))) return r;
+  auto& H = h->lev[l + 1];
+  double* R = h->at<double>(L.R);
+  double* fH = h->at<double>(H.f);
+  double* fH0 = h->at<double>(H.f0);
+  double* bH = h->at<double>(H.b);
+  double* QH = h->at<double>(H.Q);
+  double* PH = h->at<double>(H.P);
+  // residual field of the smoothed fine iterate: R_h = T(f) - Q(f)/eps - b_h
+  double* Ql = l == 0 ? R : h->at<double>(L.Q);
+  if ((r = collide_impl(h, f, Ql, nullptr, h->precision, st, l))) return r;
+  if ((r = residual_field_impl(h, f, Ql, b, R, st, l))) return r;
+  {
+    Scope sc(h, SGS_PROF_RESCALE, st, 2);
+    cudaError_t e = launch_restrict(f, fH0, K, H.C, st);
+    if (e == cudaSuccess) e = launch_restrict(R, bH, K, H.C, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  // b_H = R_H(I f) - I(R_h), with R_H(I f) the coarse residual field of the restricted iterate
+  if ((r = collide_impl(h, fH0, QH, nullptr, h->precision, st, l + 1))) return r;
+  if ((r = residual_field_impl(h, fH0, QH, nullptr, PH, st, l + 1))) return r;
+  {
+    Scope sc(h, SGS_PROF_RESCALE, st, 1);
+    cudaError_t e = launch_axpby(bH, PH, -1.0, 1.0, K * H.C, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fH, fH0, sizeof(double) * K * H.C, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if ((r = vcycle_impl(h, l + 1, levels, fH, bH, pre, post, coarse_iters, st))) return r;
+  {
+    Scope sc(h, SGS_PROF_RESCALE, st, 1);
+    cudaError_t e = launch_prolong_add(f, fH, fH0, K, H.C, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  for (int it = 0; it < post; it++)
+    if ((r = iterate_impl(h, f, nullptr, Pl, b, 0, nullptr, st, l))) return r;
   return SGS_OK;
 }
 
@@ -581,6 +675,40 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
   }
   h->field = off;
   h->C = cell;
+  {
+    sgs_handle::Level L0;
+    L0.C = cell;
+    L0.G = (cell + kLanes - 1) / kLanes;
+    h->lev.push_back(L0);
+    for (int l = 1;; l++) {
+      bool ok = true;
+      for (int q = 0; q < n_inst; q++)
+        if (problems[q].nx % (1 << l) != 0) ok = false;
+      if (!ok || l > 12) break;
+      sgs_handle::Level L;
+      long long loff = 0;
+      int lcell = 0;
+      for (int q = 0; q < n_inst; q++) {
+        sgs_problem pc = problems[q];
+        pc.nx = problems[q].nx >> l;
+        pc.total_mass = 0.0;  // no rescale on coarse levels
+        InstDev I;
+        fill_inst(pc, h->N, h->dv, I);
+        I.f_off = loff;
+        I.cell0 = lcell;
+        L.hinst.push_back(I);
+        for (int j = 0; j < pc.nx; j++) {
+          L.hcell_off.push_back(loff + j * K);
+          L.hcell_inst.push_back(q);
+        }
+        loff += (long long)pc.nx * K;
+        lcell += pc.nx;
+      }
+      L.C = lcell;
+      L.G = (lcell + kLanes - 1) / kLanes;
+      h->lev.push_back(L);
+    }
+  }
   int r = plan(h);
   if (r != SGS_OK) {
     delete h;
@@ -625,6 +753,12 @@ int sgs_bind_workspace(sgs_handle* h, void* device_ptr, size_t bytes) {
   SGS_UP(row_start, h->row_start);
   SGS_UP(row_units, h->row_units);
 #undef SGS_UP
+  for (size_t l = 1; l < h->lev.size() && e == cudaSuccess; l++) {
+    auto& L = h->lev[l];
+    e = up(L.inst, L.hinst.data(), sizeof(InstDev) * L.hinst.size());
+    if (e == cudaSuccess) e = up(L.cell_off, L.hcell_off.data(), sizeof(long long) * L.hcell_off.size());
+    if (e == cudaSuccess) e = up(L.cell_inst, L.hcell_inst.data(), sizeof(int) * L.hcell_inst.size());
+  }
   if (e == cudaSuccess) e = cudaMemset(h->ws + h->off.cnt, 0, sizeof(Counters) * h->n_inst);
   if (e == cudaSuccess && h->spectral) {
     // spectral lanes beyond the last cell must hold zeros
@@ -737,15 +871,13 @@ int sgs_dc_clear(sgs_handle* h) {
 }
 
 int sgs_vcycle(sgs_handle* h, double* f, int levels, int pre, int post, int coarse_iters, void* stream) {
-  (void)f;
-  (void)levels;
-  (void)pre;
-  (void)post;
-  (void)coarse_iters;
-  (void)stream;
-  if (!h) return SGS_ERR_ARG;
-  return SGS_ERR_UNSUPPORTED;
+  if (!h || !f || levels < 2 || pre < 0 || post < 0 || coarse_iters < 0) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  if (levels > (int)h->lev.size()) return SGS_ERR_ARG;
+  return vcycle_impl(h, 0, levels, f, nullptr, pre, post, coarse_iters, as_stream(stream));
 }
+
+int sgs_max_levels(const sgs_handle* h) { return h ? (int)h->lev.size() : 0; }
 
 int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream) {
   if (!h || !out) return SGS_ERR_ARG;

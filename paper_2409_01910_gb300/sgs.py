@@ -136,6 +136,8 @@ def lib(build: bool = True):
             "sgs_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_ulonglong), C.c_int]),
             "sgs_launch_count": (C.c_ulonglong, [vp]),
             "sgs_vcycle": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]),
+            "sgs_max_levels": (C.c_int, [vp]),
+            "sgs_residual_noalloc": (C.c_int, [C.POINTER(_Problem), vp, vp, vp, vp, vp]),
             "sgs_read_status": (C.c_int, [vp, C.POINTER(_Stats), vp]),
             "sgs_reset_stats": (C.c_int, [vp, vp]),
             "sgs_destroy": (None, [vp]),
@@ -258,6 +260,9 @@ class Solver:
 
     def vcycle(self, f, levels, pre=1, post=1, coarse_iters=10, stream=None):
         _check(lib().sgs_vcycle(self.h, _ptr(f), levels, pre, post, coarse_iters, _stream(stream)), "sgs_vcycle")
+
+    def max_levels(self) -> int:
+        return int(lib().sgs_max_levels(self.h))
 
     def read_status(self, stream=None) -> dict:
         st = _Stats()

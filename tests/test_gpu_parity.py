@@ -269,3 +269,20 @@ def test_defect_correction_tracks_fp64_iteration():
     # FP32 rounding of the increments between refreshes leaves ~1e-8; FP32 resolution is 6e-8
     assert rel(fdc.cpu().numpy(), f64.cpu().numpy()) <= 2e-8
     assert abs(res.item() - res64.item()) <= 0.05 * res64.item() + 1e-11, (res.item(), res64.item())
+
+
+@pytest.mark.parametrize("levels,pre,post,coarse", [(3, 1, 1, 2), (2, 2, 1, 3)])
+def test_vcycle_parity(oracle, levels, pre, post, coarse):
+    """FAS V-cycle (eq. (30)) on the GPU against the oracle's, fixed inner counts."""
+    N, J, L = 8, 8, 6.0
+    d = spec(nx=J, nv=N, v_max=L, eps=0.05, inner_fixed=5)
+    f0 = I.initial_state(J, N, L, T=1.5, seed=9)
+    po = oracle_problem(oracle, d)
+    fo = f0.copy()
+    oracle.vcycle(po, fo, levels, pre, post, coarse)
+    s = sgs.Solver(gpu_problem(d))
+    assert s.max_levels() == 4
+    fd = to_dev(f0)
+    s.vcycle(fd, levels, pre, post, coarse)
+    assert s.read_status()["status"] == 0
+    assert rel(fd.cpu().numpy().reshape(f0.shape), fo) <= 1e-12
