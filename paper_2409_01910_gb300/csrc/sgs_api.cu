@@ -104,6 +104,10 @@ struct sgs_handle {
   struct Level {
     int C = 0, G = 0;
     size_t inst = 0, cell_off = 0, cell_inst = 0, f = 0, f0 = 0, b = 0, Q = 0, P = 0, R = 0;
+    // increment-form reference of this level (f_ref, Q_ref, theta_ref, ahat_ref); on coarse
+    // levels the restricted iterate I f and its FP32 collision operator
+    size_t rf = 0, rQ = 0, rth = 0, rah = 0;
+    bool ref = false;
     std::vector<InstDev> hinst;
     std::vector<long long> hcell_off;
     std::vector<int> hcell_inst;
@@ -278,6 +282,17 @@ void layout(sgs_handle* h) {
       L.b = take(sizeof(double) * K * L.C);
       L.Q = take(sizeof(double) * K * L.C);
       L.P = take(sizeof(double) * K * L.C);
+    }
+    if (l == 0) {
+      L.rf = f.f_ref;
+      L.rQ = f.Q_ref;
+      L.rth = f.theta_ref;
+      L.rah = f.ahat_ref;
+    } else {
+      L.rf = L.f0;
+      L.rQ = take(dc ? sizeof(double) * K * L.C : 0);
+      L.rth = take(dc ? sizeof(double) * 5 * L.C : 0);
+      L.rah = take(dc ? (size_t)L.G * n * n * n * kLanes * sizeof(float2) : 0);
     }
     if (l + 1 < nl) L.R = take(sizeof(double) * K * L.C);
   }
@@ -489,7 +504,8 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
   // both sums in FP32 on small increments, so the rounding error vanishes as f -> f_ref.
   auto run_inc = [&](CollideCtx<float> x) -> int {
     typedef float2 CT;
-    DftMode m1{1, h->at<double>(h->off.f_ref), h->at<double>(h->off.theta_ref)};
+    const auto& Lv = h->lev[l];
+    DftMode m1{1, h->at<double>(Lv.rf), h->at<double>(Lv.rth)};
     DftMode m2{2, m1.f_ref, m1.theta_ref};
     CT* part2 = h->at<CT>(h->off.partial2);
     cudaError_t er;
@@ -507,8 +523,8 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
       Scope sc(h, SGS_PROF_DFT, st, 3);
       er = launch_dft(f, x, m2, st);
       if (er == cudaSuccess)
-        er = cudaMemcpyAsync(x.sb.ahat, h->at<CT>(h->off.ahat_ref),
-                             (size_t)h->G * h->n * h->n * h->n * kLanes * sizeof(CT), cudaMemcpyDeviceToDevice, st);
+        er = cudaMemcpyAsync(x.sb.ahat, h->at<CT>(Lv.rah),
+                             (size_t)Lv.G * h->n * h->n * h->n * kLanes * sizeof(CT), cudaMemcpyDeviceToDevice, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
     {
@@ -517,11 +533,11 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 4);
-    return cuda_status(launch_reduce_idft(f, Q, P, x, part2, h->at<double>(h->off.Q_ref), st));
+    return cuda_status(launch_reduce_idft(f, Q, P, x, part2, h->at<double>(Lv.rQ), st));
   };
   if (precision == SGS_FP32) {
     if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
-    if (h->dc_ref && l == 0) return run_inc(collide_ctx<float>(h, l));
+    if (l == 0 ? h->dc_ref : h->lev[l].ref) return run_inc(collide_ctx<float>(h, l));
     return run(collide_ctx<float>(h, l));
   }
   return run(collide_ctx<double>(h, l));
@@ -614,7 +630,23 @@ int vcycle_impl(sgs_handle* h, int l, int levels, double* f, const double* b, in
     if (e != cudaSuccess) return cuda_status(e);
   }
   // b_H = R_H(I f) - I(R_h), with R_H(I f) the coarse residual field of the restricted iterate
+  H.ref = false;
   if ((r = collide_impl(h, fH0, QH, nullptr, h->precision, st, l + 1))) return r;
+  if (h->precision == SGS_FP32 && h->spectral) {
+    // Coarse FP32 collisions in increment form against I f: the coarse operator then
+    // reproduces R_H(I f) exactly at f_H = I f, so FP32 rounding of Q_H(I f) cancels in the
+    // coarse correction f_H - I f instead of entering it as noise.
+    CollideCtx<float> x = collide_ctx<float>(h, l + 1);
+    cudaError_t e = cudaMemcpyAsync(h->ws + H.rQ, QH, sizeof(double) * K * H.C, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->ws + H.rth, h->ws + h->off.theta, sizeof(double) * 5 * H.C, cudaMemcpyDeviceToDevice,
+                          st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->ws + H.rah, x.sb.ahat, (size_t)H.G * h->n * h->n * h->n * kLanes * sizeof(float2),
+                          cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    H.ref = true;
+  }
   if ((r = residual_field_impl(h, fH0, QH, nullptr, PH, st, l + 1))) return r;
   {
     Scope sc(h, SGS_PROF_RESCALE, st, 1);

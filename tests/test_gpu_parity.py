@@ -286,3 +286,42 @@ def test_vcycle_parity(oracle, levels, pre, post, coarse):
     s.vcycle(fd, levels, pre, post, coarse)
     assert s.read_status()["status"] == 0
     assert rel(fd.cpu().numpy().reshape(f0.shape), fo) <= 1e-12
+
+
+def test_vcycle_fp32_parity(oracle):
+    """Mixed-precision V-cycle (FP32 collision sums, coarse levels in increment form against
+    the restricted iterate) against the oracle's FP64 V-cycle: the increment form is exact in
+    exact arithmetic (Q_s is bilinear), so only FP32 rounding of the sums separates them."""
+    N, J, L = 8, 8, 6.0
+    d = spec(nx=J, nv=N, v_max=L, eps=0.05, inner_fixed=5)
+    f0 = I.initial_state(J, N, L, T=1.5, seed=9)
+    fo = f0.copy()
+    oracle.vcycle(oracle_problem(oracle, d), fo, 3, 1, 1, 2)
+    s = sgs.Solver(gpu_problem(dict(d, precision=sgs.FP32)))
+    fd = to_dev(f0)
+    s.vcycle(fd, 3, 1, 1, 2)
+    assert s.read_status()["status"] == 0
+    assert rel(fd.cpu().numpy().reshape(f0.shape), fo) <= 1e-5
+
+
+def test_dc_vcycle_tracks_fp64_vcycle():
+    """Defect correction + V-cycles with FP32 sums against FP64 V-cycles from the same state:
+    with every level in increment form the iterates stay far below FP32 resolution apart."""
+    wl = I.heat_16cells_16v()
+    d = spec(nx=wl.J, nv=wl.N, v_max=wl.L, eps=0.1, T=(wl.T_left, wl.T_right), total_mass=wl.total_mass,
+             inner_tol=1e-11)
+    f0 = wl.initial_state()
+    s64 = sgs.Solver(gpu_problem(dict(d, precision=sgs.FP64)))
+    f64 = to_dev(f0)
+    s32 = sgs.Solver(gpu_problem(dict(d, precision=sgs.FP32)))
+    fdc = to_dev(f0)
+    Q, P = s32.field(), s32.field()
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for k in range(6):
+        s64.vcycle(f64, 3, 1, 1, 4)
+        s32.dc_step(fdc, Q, P, 0, res=res)
+        s32.vcycle(fdc, 3, 1, 1, 4)
+    assert s64.read_status()["status"] == 0 and s32.read_status()["status"] == 0
+    err = rel(fdc.cpu().numpy(), f64.cpu().numpy())
+    print("dc+vcycle vs fp64 vcycle rel", err)
+    assert err <= 5e-8
