@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--dc-every", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-t2tol", action="store_true", help="skip the time-to-residual runs")
+    ap.add_argument("--t2tol-all", action="store_true", help="also time the plain FP64 SGS form to 1e-8")
+    ap.add_argument("--t2tol-cap", type=float, default=150.0, help="seconds allowed per time-to-residual run")
     ap.add_argument("--case", choices=["sweep", "sum", "sum64"], default=None,
                     help="run a small case of one kernel class (for profiler captures) and exit")
     return ap.parse_args()
@@ -186,7 +189,8 @@ def run_native(args, rank, world, local):
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     dom = max(prof, key=lambda k: prof[k][0])
-    roof = roofline(dom, prof, wl, s, sm_mhz)
+    roofs = {k: roofline(k, prof, wl, sm_mhz) for k in ("sweep", "sum", "sum_fp64") if prof[k][1] > 0}
+    roof = roofs.get(dom) or roofline(dom, prof, wl, sm_mhz)
 
     # end to end through the C ABI with host buffers: H2D of the state (f, P), one step,
     # D2H of the step's residual
@@ -196,6 +200,12 @@ def run_native(args, rank, world, local):
 
     # plain FP64 GPU form for comparison (same step, FP64 collision sum and FP64 scan)
     fp64 = fp64_form(wl, args, f0, dev, stream) if args.fp64_steps > 0 else None
+
+    # time to FP64 residual 1e-8 from the initial state, mixed against FP64 (one GPU only)
+    t2tol = None
+    if world == 1 and not args.no_t2tol:
+        kinds = ["mixed_mg", "mixed_sgs", "fp64_mg"] + (["fp64_sgs"] if args.t2tol_all else [])
+        t2tol = {k: time_to_tol(wl, f0, dev, k, args.t2tol_cap) for k in kinds}
 
     out = None
     if rank == 0:
@@ -214,45 +224,127 @@ def run_native(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": wl.name, "cells": wl.J, "nv": wl.N, "v_max": wl.L, "eps": wl.eps,
                        "T_walls": [round(wl.T_left, 6), round(wl.T_right, 6)], "collision": "maxwell",
-                       "precision": "mixed: FP32 collision sum + FP32 scan, FP64 moments/residual/defect correction",
+                       "precision": ("mixed: FP32 direct spectral sums in increment form against the last FP64 "
+                                     "evaluation, double-float (FP32 pair) scans with FP64 scalar decisions, FP64 "
+                                     "moments/residual/defect correction"),
                        "dc_every": args.dc_every, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
+            "roofline_kernels": roofs,
             "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": int(launches),
             "fp64": fp64,
+            "time_to_residual_1e-8": t2tol,
             "device_status": status["status"],
             "inner_iters_per_visit": status["inner_iters"] / max(1, status["visits"]),
         }
     return out
 
 
-def roofline(dom, prof, wl, s, sm_mhz):
-    ms, n = prof[dom]
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "of measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+def kernel_traffic(name, units):
+    """DRAM bytes per launch from the committed ncu summary, scaled by the units (cell visits)
+    of one launch; None when the kernel's sources changed since the capture."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(name)
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for src in rec["sources"]:
+        h.update(open(os.path.join(ROOT, src), "rb").read())
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None
+    return rec["dram_bytes_per_unit"] * units
+
+
+def roofline(cls, prof, wl, sm_mhz):
+    """Roofline of one kernel class over the timed region: algorithmic work per launch over
+    the average launch time (CUDA events on the launching stream)."""
+    ms, n = prof[cls]
     avg = ms / max(1, n)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    peaks, src = measured_peaks()
     K = wl.N ** 3
-    if dom == "sum":
-        # algorithmic work: 10 flops per mode pair over the Hermitian half, 64 cells
+    if cls in ("sum", "sum_fp64"):
+        # algorithmic work: 10 flops per mode pair over the Hermitian half, every cell of the
+        # workload per launch
         flops = 10 * 0.5 * pairs_per_cell(wl.N) * wl.J
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
         ach = flops / (avg * 1e-3) / 1e12
-        return {"kernel": "k_sum<float> (direct spectral sum)", "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
-    if dom == "sweep":
+        if cls == "sum":
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+            return {"kernel": "k_sum<float> (direct spectral sum, FP32)", "bound": "alu", "achieved": ach,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
+        peak = 1.25
+        return {"kernel": "k_sum<double> (direct spectral sum, FP64)", "bound": "alu", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (of nominal)"}
+    if cls == "sweep":
         byts = 5 * K * 8 * wl.J  # read f_{j-1}, f_j, f_{j+1}, P_j; write f_j per visit
         ach = byts / (avg * 1e-3) / 1e9
-        return {"kernel": "k_sweep<float> (persistent SGS scan)", "bound": "hbm", "achieved": ach,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        return {"kernel": "k_sweep<dfloat,8> (persistent SGS scan, one cluster of 16 CTAs)", "bound": "hbm",
+                "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                "traffic": kernel_traffic("k_sweep<dfloat,8>", wl.J), "peak_source": f"hbm_gbs ({src})",
+                "note": "latency-bound: one visit is a chain of cluster reductions and Newton solves"}
     byts = 2 * K * 8 * wl.J
     ach = byts / (avg * 1e-3) / 1e9
-    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / peaks["hbm_gbs"], "traffic": None}
+    return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+
+
+def time_to_tol(wl, f0, dev, kind, cap_s, tol=1e-8):
+    """Seconds from the initial state until the FP64 residual falls below tol.
+
+    kinds: mixed_sgs (defect correction every 10 SGS iterations), mixed_mg (defect
+    correction before every 2 two-level V-cycles), fp64_sgs (SGS iterations, FP64 sums and
+    scans), fp64_mg (two-level V-cycles in FP64)."""
+    import torch
+
+    from paper_2409_01910_gb300 import sgs
+
+    s = make_solver(wl, sgs.FP32 if kind.startswith("mixed") else sgs.FP64)
+    f = f0.clone()
+    Q, P = s.field(), s.field()
+    res = torch.zeros(1, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r, iters, reached = float("nan"), 0, False
+    while time.perf_counter() - t0 < cap_s:
+        if kind == "mixed_sgs":
+            s.dc_step(f, Q, P, 10, res=res)
+            iters += 10
+        elif kind == "mixed_mg":
+            s.dc_step(f, Q, P, 0, res=res)
+        elif kind == "fp64_sgs":
+            s.iterate(f, Q, P, flags=sgs.IT_EVAL | (sgs.IT_P_VALID if iters else 0), res=res)
+            iters += 1
+        else:
+            s.collide(f, Q, P)
+            s.residual(f, Q, res)
+        r = float(res.item())  # synchronises
+        if r < tol or r != r:
+            reached = r < tol
+            break
+        if kind == "mixed_mg" or kind == "fp64_mg":
+            for _ in range(2 if kind == "mixed_mg" else 1):
+                s.vcycle(f, 2, 1, 1, 4)
+                iters += 1
+    sec = time.perf_counter() - t0
+    st = s.read_status()
+    s.close()
+    unit = "V-cycles" if kind.endswith("mg") else "SGS iterations"
+    return {"seconds": round(sec, 3), "reached": reached, "residual": r, unit: iters, "status": st["status"]}
 
 
 def end_to_end(s, f, Q, P, wl, args, stream):

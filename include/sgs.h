@@ -192,12 +192,13 @@ int sgs_max_levels(const sgs_handle* h);
 enum sgs_prof_class {
   SGS_PROF_MOMENTS = 0,     /* moments + discrete Maxwellian of every cell */
   SGS_PROF_DFT = 1,         /* forward DFT of f - M and f + M (3 kernels) */
-  SGS_PROF_SUM = 2,         /* direct spectral sum */
+  SGS_PROF_SUM = 2,         /* direct spectral sum, FP32 (mixed precision) */
   SGS_PROF_REDUCE_IDFT = 3, /* partial reduction + inverse DFT + P (4 kernels), or BGK */
   SGS_PROF_SWEEP = 4,       /* persistent SGS scan */
   SGS_PROF_RESIDUAL = 5,    /* outer residual */
-  SGS_PROF_RESCALE = 6,     /* mass rescale and the defect-correction right-hand side */
-  SGS_PROF_CLASSES = 7
+  SGS_PROF_RESCALE = 6,     /* mass rescale, grid transfers and other vector updates */
+  SGS_PROF_SUM_FP64 = 7,    /* direct spectral sum, FP64 */
+  SGS_PROF_CLASSES = 8
 };
 int sgs_profile(sgs_handle* h, int enable);
 int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, int n_classes);

@@ -121,9 +121,20 @@ __device__ inline dfloat df_exp(dfloat x) {
                         -4.34617203337595e-10f, -3.3631094437103215e-11f, -2.725596874933456e-12f,
                         -3.40699609366682e-13f, 3.793571224297229e-14f, -7.575112209051195e-15f,
                         4.4176230446483665e-16f, 1.1082839147459852e-16f, -5.352526511562726e-18f};
-  dfloat acc = {ch[13], cl[13]};
+  // Estrin's scheme: the same degree-13 polynomial with a dependency chain of four
+  // multiply-add levels instead of thirteen
+  dfloat c[14];
 #pragma unroll
-  for (int n = 12; n >= 0; n--) acc = acc * r + dfloat{ch[n], cl[n]};
+  for (int n = 0; n < 14; n++) c[n] = dfloat{ch[n], cl[n]};
+  dfloat r2 = r * r;
+  dfloat r4 = r2 * r2;
+  dfloat r8 = r4 * r4;
+  dfloat pr[7];
+#pragma unroll
+  for (int n = 0; n < 7; n++) pr[n] = c[2 * n] + c[2 * n + 1] * r;
+  dfloat q0 = pr[0] + pr[1] * r2, q1 = pr[2] + pr[3] * r2, q2 = pr[4] + pr[5] * r2;
+  dfloat s0 = q0 + q1 * r4, s1 = q2 + pr[6] * r4;
+  dfloat acc = s0 + s1 * r8;
   int k = (int)kf;
   return {ldexpf(acc.hi, k), ldexpf(acc.lo, k)};
 }
@@ -283,7 +294,7 @@ __device__ inline bool chol5_solve(const float* Au, const float* b, float* y) {
     if (!(a[i][i] > 0.0f)) return false;
     sc[i] = rsqrtf(a[i][i]);
   }
-  float l[5][5];
+  float l[5][5], dinv[5];
 #pragma unroll
   for (int i = 0; i < 5; i++)
 #pragma unroll
@@ -294,9 +305,10 @@ __device__ inline bool chol5_solve(const float* Au, const float* b, float* y) {
 #pragma unroll
     for (int k = 0; k < j; k++) d -= l[j][k] * l[j][k];
     if (!(d > 0.0f)) return false;
-    float ljj = sqrtf(d);
-    l[j][j] = ljj;
-    float inv = 1.0f / ljj;
+    // approximate reciprocal square root: the result is only a Newton direction
+    float inv = rsqrtf(d);
+    l[j][j] = d * inv;
+    dinv[j] = inv;
 #pragma unroll
     for (int i = j + 1; i < 5; i++) {
       float s = a[i][j] * sc[i] * sc[j];
@@ -311,14 +323,14 @@ __device__ inline bool chol5_solve(const float* Au, const float* b, float* y) {
     float s = b[i] * sc[i];
 #pragma unroll
     for (int k = 0; k < i; k++) s -= l[i][k] * z[k];
-    z[i] = s / l[i][i];
+    z[i] = s * dinv[i];
   }
 #pragma unroll
   for (int i = 4; i >= 0; i--) {
     float s = z[i];
 #pragma unroll
     for (int k = i + 1; k < 5; k++) s -= l[k][i] * y[k];
-    y[i] = s / l[i][i];
+    y[i] = s * dinv[i];
   }
 #pragma unroll
   for (int i = 0; i < 5; i++) y[i] *= sc[i];

@@ -492,7 +492,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     {
-      Scope sc(h, SGS_PROF_SUM, st, 1);
+      Scope sc(h, precision == SGS_FP64 ? SGS_PROF_SUM_FP64 : SGS_PROF_SUM, st, 1);
       er = launch_spectral_sum(x, nullptr, st);
     }
     if (er != cudaSuccess) return cuda_status(er);

@@ -45,6 +45,7 @@ struct SweepSmem {
   double red_tot[8];
   double thg[5], thp[5], th_try[5], dir[5];
   float fn;
+  float stepf;         // exponent change of the full Newton step
   int flag;
   int ctl;             // broadcast decisions of thread 0
 };
@@ -98,50 +99,33 @@ __device__ inline void cluster_reduce(E (&v)[NV], double (&tot)[NV], SweepSmem<E
 template <typename E>
 __device__ __noinline__ void eval_cta(SweepSmem<E>& sm, int N) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (wid < 3) {
-    const int d = wid;
+  if (wid < 4) {
+    // warps 0-2: dimension d; warp 3: dimension 1 again, weighted by |v1|/dx (step 1, eq. (24))
+    const int d = wid == 3 ? 0 : wid;
     E e = cvt<E>(0.0);
     if (lane < N) {
       E x = sm.thE[1 + d] * sm.vv[lane] - sm.thE[4] * sm.vq[lane];
       if (d == 0) x += sm.thE[0];
       e = exp_in(x);
     }
-    sm.ef[d][lane] = e;
+    if (wid < 3) sm.ef[d][lane] = e;
+    if (wid == 3) e = e * sm.c1e[lane];
     E s[5];
     s[0] = e;
     s[1] = e * sm.vv[lane];
     s[2] = e * sm.vq[lane];
     s[3] = s[2] * sm.vv[lane];
     s[4] = s[2] * sm.vq[lane];
-    if (d == 0) {  // the same sums weighted by |v1|/dx as well (step 1, eq. (24))
-      E c = sm.c1e[lane];
-      E s10[10];
+    warp_allsum<5, E>(s);
+    if (lane < 5) {
+      E t = s[0];
 #pragma unroll
-      for (int q = 0; q < 5; q++) {
-        s10[q] = s[q];
-        s10[5 + q] = s[q] * c;
-      }
-      warp_allsum<10, E>(s10);
-      if (lane < 5) {
-        E t = s10[0], tw = s10[5];
-#pragma unroll
-        for (int q = 1; q < 5; q++)
-          if (lane == q) {
-            t = s10[q];
-            tw = s10[5 + q];
-          }
-        sm.S[0][lane] = t;
-        sm.S1w[lane] = tw;
-      }
-    } else {
-      warp_allsum<5, E>(s);
-      if (lane < 5) {
-        E t = s[0];
-#pragma unroll
-        for (int q = 1; q < 5; q++)
-          if (lane == q) t = s[q];
+      for (int q = 1; q < 5; q++)
+        if (lane == q) t = s[q];
+      if (wid < 3)
         sm.S[d][lane] = t;
-      }
+      else
+        sm.S1w[lane] = t;
     }
   }
   __syncthreads();
@@ -214,6 +198,9 @@ __device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, bool wv1, c
       bool ok = chol5_solve(A, Ff, y);
       if (tid == 0) {
         sm.flag = ok;
+        // exponent change of a full step, |d alpha| + L sum |d beta| + L^2 |d gamma|
+        const float Lf = (float)L;
+        sm.stepf = fabsf(y[0]) + Lf * (fabsf(y[1]) + fabsf(y[2]) + fabsf(y[3])) + Lf * Lf * fabsf(y[4]);
         sm.dir[0] = -(double)y[0];
         sm.dir[1] = -(double)y[1];
         sm.dir[2] = -(double)y[2];
@@ -248,11 +235,10 @@ __device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, bool wv1, c
       lam *= 0.5f;
     }
     if (tid == 0) {
-      double step = (double)lam * (fabs(sm.dir[0]) + L * (fabs(sm.dir[1]) + fabs(sm.dir[2]) + fabs(sm.dir[3])) +
-                                   L * L * fabs(sm.dir[4]));
+      const float step = lam * sm.stepf;
 #pragma unroll
       for (int k = 0; k < 5; k++) th[k] = sm.th_try[k];
-      sm.ctl = !(step == step) ? -1 : (step <= tol ? 1 : 0);
+      sm.ctl = !(step == step) ? -1 : (step <= (float)tol ? 1 : 0);
     }
     __syncthreads();
     int c = sm.ctl;
@@ -548,7 +534,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
 }
 
 // Default launch shape: nodes per thread (a divisor of N), cluster size (a power of two, at
-// most 16) and threads per CTA (a multiple of 32 in [96, 256]; warps 0-2 serve the Newton
+// most 16) and threads per CTA (a multiple of 32 in [128, 256]; warps 0-3 serve the Newton
 // evaluations).
 SweepShape sweep_shape(int N, int arith) {
   SweepShape s;
@@ -558,7 +544,7 @@ SweepShape sweep_shape(int N, int arith) {
   s.cluster = 1;
   while (s.cluster < 16 && s.cluster * 256 < threads) s.cluster *= 2;
   s.tpb = ((threads + s.cluster - 1) / s.cluster + 31) / 32 * 32;
-  if (s.tpb < 96) s.tpb = 96;
+  if (s.tpb < 128) s.tpb = 128;
   return s;
 }
 
@@ -601,7 +587,7 @@ bool sweep_shape_valid(int N, const SweepShape& sh) {
   int K = N * N * N;
   if (sh.ept <= 0 || N % sh.ept != 0) return false;
   if (sh.cluster < 1 || sh.cluster > 16 || (sh.cluster & (sh.cluster - 1))) return false;
-  if (sh.tpb < 96 || sh.tpb > 256 || sh.tpb % 32) return false;
+  if (sh.tpb < 128 || sh.tpb > 256 || sh.tpb % 32) return false;
   if (sh.tpb < 32 * ((8 * sh.cluster + 31) / 32)) return false;  // warps for the cluster gather
   if ((long long)sh.cluster * sh.tpb * sh.ept < K) return false;
   int e[] = {2, 4, 8, 12, 16, 20, 24, 28, 32};

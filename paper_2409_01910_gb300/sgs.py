@@ -23,7 +23,7 @@ DIFFUSE, INFLOW = 0, 1
 FP64, FP32 = 0, 1
 PFP, FP = 0, 1
 IT_P_VALID, IT_EVAL = 1, 2
-PROF_NAMES = ("moments", "dft", "sum", "reduce_idft", "sweep", "residual", "rescale")
+PROF_NAMES = ("moments", "dft", "sum", "reduce_idft", "sweep", "residual", "rescale", "sum_fp64")
 PROF_CLASSES = len(PROF_NAMES)
 
 
