@@ -188,7 +188,8 @@ int sgs_max_levels(const sgs_handle* h);
 /* Kernel-time profiling. When enabled, every group of launches is bracketed by CUDA events
  * recorded on the launching stream; sgs_profile_read synchronises on them and returns, per
  * class, the summed milliseconds and the number of bracketed groups, then clears them.
- * sgs_launch_count returns the number of kernels enqueued through the handle so far. */
+ * sgs_launch_count returns the number of kernels enqueued through the handle so far.
+ * Launches enqueued while the stream is being captured into a CUDA graph are not timed. */
 enum sgs_prof_class {
   SGS_PROF_MOMENTS = 0,     /* moments + discrete Maxwellian of every cell */
   SGS_PROF_DFT = 1,         /* forward DFT of f - M and f + M (3 kernels) */
@@ -203,6 +204,39 @@ enum sgs_prof_class {
 int sgs_profile(sgs_handle* h, int enable);
 int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, int n_classes);
 unsigned long long sgs_launch_count(const sgs_handle* h);
+
+/* Batches: per-instance activity. Every instance starts active (at bind). An inactive
+ * instance is converged: the scans (and the mass rescale) skip it, so its f stays as it
+ * is, while collisions and residuals still cover every cell.
+ *   sgs_update_active: active[q] = !(res[q] < tol) for the device residuals res[n_inst]
+ *     (as written by sgs_residual / sgs_dc_step); asynchronous, graph-capturable.
+ *   sgs_activate_all: marks every instance active again; asynchronous.
+ *   sgs_read_active: synchronises the stream and copies the n_inst flags to host memory. */
+int sgs_update_active(sgs_handle* h, const double* res, double tol, void* stream);
+int sgs_activate_all(sgs_handle* h, void* stream);
+int sgs_read_active(sgs_handle* h, int* active, void* stream);
+
+/* Launch shape of the persistent scan: nodes per thread (ept, a divisor of nv with a
+ * compiled kernel: 2, 4, 8, 12, ..., 32), CTAs per cluster (a power of two <= 16; one
+ * cluster walks one instance) and threads per CTA (a multiple of 32 in [128, 256]) with
+ * ept * cluster * threads >= nv^3. sgs_set_sweep_shape returns SGS_ERR_ARG for an invalid
+ * shape and SGS_ERR_UNSUPPORTED for one that cannot be resident on the device. */
+int sgs_get_sweep_shape(const sgs_handle* h, int* ept, int* cluster, int* threads);
+int sgs_set_sweep_shape(sgs_handle* h, int ept, int cluster, int threads);
+
+typedef struct {
+  int sweep_ept, sweep_cluster, sweep_threads; /* chosen scan shape */
+  float sweep_ms;                              /* its forward + backward scan time, all instances */
+  int candidates;                              /* shapes timed */
+  int sum_warps, sum_units, sum_blocks;        /* spectral-sum decomposition (set at setup) */
+} sgs_tuning;
+
+/* Autotuner. Times every valid scan shape on the bound instances (reps forward + backward
+ * scan pairs each, after one untimed pair, CUDA events on the stream), keeps the fastest
+ * for all later scans and reports it. The timed scans are real SGS scans: f advances by
+ * (reps + 1) symmetric sweeps with the given P per candidate. Synchronises the stream; not
+ * graph-capturable (call it before capturing). */
+int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning* out, void* stream);
 
 /* Synchronises the stream and reads the accumulated status and counters. */
 int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream);

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_rescale_apply(AuxArgs a, double* f, con
   int c = blockIdx.x;
   int q = a.cell_inst[c];
   const InstDev& I = a.inst[q];
-  if (!(I.total_mass > 0.0)) return;
+  if (!(I.total_mass > 0.0) || (a.active && !a.active[q])) return;
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int j = 0; j < I.J; j++) s += mass[I.cell0 + j];
@@ -200,6 +200,31 @@ cudaError_t launch_prolong_add(double* fine, const double* fc, const double* fc0
 
 cudaError_t launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st) {
   k_axpby<<<blocks_for(n), 256, 0, st>>>(y, x, a, b, n);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Per-instance activity flags of a batch: an instance whose residual is below tol is
+// converged and its scans are skipped (a non-finite residual keeps it active).
+// ---------------------------------------------------------------------------------------
+__global__ void k_update_active(const double* res, int n, double tol, int* active) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) active[q] = res[q] < tol ? 0 : 1;
+}
+
+__global__ void k_fill_int(int* p, int n, int v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+cudaError_t launch_update_active(const double* res, int n, double tol, int* active, cudaStream_t st) {
+  k_update_active<<<(n + 127) / 128, 128, 0, st>>>(res, n, tol, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_int(int* p, int n, int value, cudaStream_t st) {
+  k_fill_int<<<(n + 127) / 128, 128, 0, st>>>(p, n, value);
   return cudaGetLastError();
 }
 

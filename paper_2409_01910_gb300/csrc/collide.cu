@@ -612,7 +612,7 @@ static cudaError_t launch_sum_t(const SumArgs<T>& a, int NW, int n_units, cudaSt
   constexpr int PW = (NP + VEC - 1) / VEC * VEC;
   constexpr int kRowBufs = sizeof(T) == 4 ? 1 : 2;
   size_t smem = 2 * PW * sizeof(T) + (size_t)kRowBufs * NW * 2 * n * kLanes * sizeof(CT);
-  cudaError_t e = cudaFuncSetAttribute(k_sum<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = func_attr((const void*)k_sum<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(n_units, (a.G + NW - 1) / NW);
   k_sum<T, H><<<grid, NW * 32, smem, st>>>(a);
@@ -644,14 +644,14 @@ cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, const DftMode& m
   int N = x.N, n = N - 1, C = x.C;
   cudaError_t e;
   size_t sm1 = dft_smem<T>(N, 0, 2 * N * N);
-  e = cudaFuncSetAttribute(k_dft_i3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  e = func_attr((const void*)k_dft_i3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
   if (e != cudaSuccess) return e;
   k_dft_i3<T><<<dim3(C, N), 256, sm1, st>>>(f, x.ct, x.theta, x.sb, N, x.dv, md);
   size_t sm2 = dft_smem<T>(N, 2 * N * n, 0);
-  e = cudaFuncSetAttribute(k_dft_i2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  e = func_attr((const void*)k_dft_i2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   if (e != cudaSuccess) return e;
   k_dft_i2<T><<<dim3(C, N), 256, sm2, st>>>(x.sb, N);
-  e = cudaFuncSetAttribute(k_dft_i1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  e = func_attr((const void*)k_dft_i1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   if (e != cudaSuccess) return e;
   // groups beyond the last cell keep the zeros written at bind time
   k_dft_i1<T><<<dim3(C, n), 256, sm2, st>>>(x.sb, N);
@@ -674,14 +674,14 @@ cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const Coll
   ra.partial2 = partial2;
   k_sum_reduce<T><<<dim3(x.red.n_rows, x.red.G), 256, 0, st>>>(ra);
   size_t sm3 = dft_smem<T>(N, n * n, 0);
-  e = cudaFuncSetAttribute(k_idft_k1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+  e = func_attr((const void*)k_idft_k1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
   if (e != cudaSuccess) return e;
   k_idft_k1<T><<<dim3(C, n), 256, sm3, st>>>(x.sb, N);
-  e = cudaFuncSetAttribute(k_idft_k2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+  e = func_attr((const void*)k_idft_k2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
   if (e != cudaSuccess) return e;
   k_idft_k2<T><<<dim3(C, N), 256, sm3, st>>>(x.sb, N);
   size_t sm4 = dft_smem<T>(N, N * n, 0);
-  e = cudaFuncSetAttribute(k_idft_k3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
+  e = func_attr((const void*)k_idft_k3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
   if (e != cudaSuccess) return e;
   k_idft_k3<T><<<dim3(C, N), 256, sm4, st>>>(x.sb, f, x.ct, x.theta, x.nu, Q, P, N, x.dv, Qadd);
   return cudaGetLastError();

@@ -111,6 +111,7 @@ struct SweepArgs {
   int N;
   double dv;
   int dir;                // +1 forward, -1 backward
+  const int* active;      // per instance: 0 = converged, its scans are skipped
 };
 
 struct AuxArgs {
@@ -120,7 +121,14 @@ struct AuxArgs {
   const long long* cell_off;
   const int* cell_inst;
   double* scratch;        // per-cell partials, per-instance values
+  const int* active;      // per instance: 0 = converged, its rescale is skipped
 };
+
+// cudaFuncSetAttribute through a per-device cache: the call is made once per (kernel,
+// attribute, value) and device, so launches stay free of it (also during stream capture).
+cudaError_t func_attr(const void* fn, cudaFuncAttribute attr, int value);
+cudaError_t launch_update_active(const double* res, int n, double tol, int* active, cudaStream_t st);
+cudaError_t launch_fill_int(int* p, int n, int value, cudaStream_t st);
 
 cudaError_t launch_moments(const double* f, const CellTables& ct, int C, int N, double dv, double tol, int maxit,
                            double* theta, double* nu, Counters* cnt, cudaStream_t st);
@@ -148,6 +156,10 @@ constexpr int kSweepDF64 = 1;  // double-float on the FP32 pipes (FP64-class acc
 constexpr int kSweepF32 = 2;   // plain FP32 (converges only to FP32 resolution)
 SweepShape sweep_shape(int N, int arith);
 bool sweep_shape_valid(int N, const SweepShape& sh);
+// Sweep launch shapes: nodes per thread with a compiled kernel, and the number of clusters of
+// the shape that fit on the device at once (0: the shape cannot run).
+bool sweep_ept_compiled(int ept);
+cudaError_t sweep_max_clusters(const SweepShape& sh, int arith, int* n);
 cudaError_t launch_sweep(const SweepArgs& a, const SweepShape& sh, int arith, cudaStream_t st);
 
 cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st);

@@ -7,6 +7,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -96,7 +99,7 @@ struct sgs_handle {
   struct {
     size_t inst, cell_off, cell_inst, cnt, theta, nu, scratch, tw_cos, tw_sin, G, Lo, units, step0, row_k, row_start,
         row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, partial2, f_ref, Q_ref, theta_ref,
-        ahat_ref, end;
+        ahat_ref, active, end;
   } off;
   bool dc_ref = false;  // FP32 collisions use the increment form against the stored reference
   // multigrid levels: lev[0] is the bound grid (tables at off.inst, off.cell_off, off.cell_inst);
@@ -232,6 +235,7 @@ void layout(sgs_handle* h) {
   f.cell_off = take(sizeof(long long) * C);
   f.cell_inst = take(sizeof(int) * C);
   f.cnt = take(sizeof(Counters) * h->n_inst);
+  f.active = take(sizeof(int) * h->n_inst);
   f.theta = take(sizeof(double) * 5 * C);
   f.nu = take(sizeof(double) * C);
   f.scratch = take(sizeof(double) * (2 * h->n_inst + 2 * C + 64));
@@ -388,14 +392,17 @@ struct Scope {
   cudaEvent_t a = nullptr, b = nullptr;
   Scope(sgs_handle* h_, int cls_, cudaStream_t st_, int n_launch) : h(h_), cls(cls_), st(st_) {
     h->launches += n_launch;
-    if (h->prof) {
+    // launches captured into a CUDA graph are not timed: an event recorded during capture
+    // becomes a graph node, not a timestamp
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (h->prof && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
       a = take_event(h);
       b = take_event(h);
       if (a && b) cudaEventRecord(a, st);
     }
   }
   ~Scope() {
-    if (h->prof && a && b) {
+    if (a && b) {
       cudaEventRecord(b, st);
       h->recs.push_back({cls, a, b});
     }
@@ -413,6 +420,7 @@ AuxArgs aux_args(const sgs_handle* h, int l = 0) {
   a.cell_off = h->at<long long>(L.cell_off);
   a.cell_inst = h->at<int>(L.cell_inst);
   a.scratch = h->at<double>(h->off.scratch);
+  a.active = h->at<int>(h->off.active);
   return a;
 }
 
@@ -555,6 +563,7 @@ int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int
   a.N = h->N;
   a.dv = h->dv;
   a.dir = dir;
+  a.active = h->at<int>(h->off.active);
   Scope sc(h, SGS_PROF_SWEEP, st, 1);
   return cuda_status(launch_sweep(a, h->sweep, h->sweep_arith, st));
 }
@@ -663,6 +672,48 @@ int vcycle_impl(sgs_handle* h, int l, int levels, double* f, const double* b, in
   for (int it = 0; it < post; it++)
     if ((r = iterate_impl(h, f, nullptr, Pl, b, 0, nullptr, st, l))) return r;
   return SGS_OK;
+}
+
+}  // namespace
+
+cudaError_t sgs::func_attr(const void* fn, cudaFuncAttribute attr, int value) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, int>, int> done;  // (kernel, attribute, device) -> value
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_tuple(fn, (int)attr, dev);
+  auto it = done.find(key);
+  if (it != done.end() && it->second == value) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, attr, value);
+  if (e == cudaSuccess) done[key] = value;
+  return e;
+}
+
+namespace {
+
+// Times `reps` forward + backward scans of the current launch shape (CUDA events on st).
+int time_sweeps(sgs_handle* h, double* f, const double* P, int reps, cudaStream_t st, float* ms) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return SGS_ERR_CUDA;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return SGS_ERR_CUDA;
+  }
+  int r = SGS_OK;
+  cudaError_t e = cudaEventRecord(a, st);
+  for (int i = 0; i < reps && r == SGS_OK && e == cudaSuccess; i++) {
+    r = sweep_impl(h, f, P, nullptr, +1, st);
+    if (r == SGS_OK) r = sweep_impl(h, f, P, nullptr, -1, st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (r != SGS_OK) return r;
+  return e == cudaSuccess ? SGS_OK : cuda_status(e);
 }
 
 }  // namespace
@@ -792,6 +843,10 @@ int sgs_bind_workspace(sgs_handle* h, void* device_ptr, size_t bytes) {
     if (e == cudaSuccess) e = up(L.cell_inst, L.hcell_inst.data(), sizeof(int) * L.hcell_inst.size());
   }
   if (e == cudaSuccess) e = cudaMemset(h->ws + h->off.cnt, 0, sizeof(Counters) * h->n_inst);
+  if (e == cudaSuccess) {
+    std::vector<int> on(h->n_inst, 1);
+    e = up(h->off.active, on.data(), sizeof(int) * on.size());
+  }
   if (e == cudaSuccess && h->spectral) {
     // spectral lanes beyond the last cell must hold zeros
     e = cudaMemset(h->ws + h->off.ahat, 0, h->off.qhat - h->off.ahat);
@@ -910,6 +965,106 @@ int sgs_vcycle(sgs_handle* h, double* f, int levels, int pre, int post, int coar
 }
 
 int sgs_max_levels(const sgs_handle* h) { return h ? (int)h->lev.size() : 0; }
+
+int sgs_update_active(sgs_handle* h, const double* res, double tol, void* stream) {
+  if (!h || !res || !(tol >= 0.0)) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return cuda_status(launch_update_active(res, h->n_inst, tol, h->at<int>(h->off.active), as_stream(stream)));
+}
+
+int sgs_activate_all(sgs_handle* h, void* stream) {
+  if (!h) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return cuda_status(launch_fill_int(h->at<int>(h->off.active), h->n_inst, 1, as_stream(stream)));
+}
+
+int sgs_read_active(sgs_handle* h, int* active, void* stream) {
+  if (!h || !active) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(active, h->ws + h->off.active, sizeof(int) * h->n_inst, cudaMemcpyDeviceToHost);
+  return cuda_status(e);
+}
+
+int sgs_get_sweep_shape(const sgs_handle* h, int* ept, int* cluster, int* threads) {
+  if (!h || !ept || !cluster || !threads) return SGS_ERR_ARG;
+  *ept = h->sweep.ept;
+  *cluster = h->sweep.cluster;
+  *threads = h->sweep.tpb;
+  return SGS_OK;
+}
+
+int sgs_set_sweep_shape(sgs_handle* h, int ept, int cluster, int threads) {
+  if (!h) return SGS_ERR_ARG;
+  SweepShape sh{ept, cluster, threads};
+  if (!sweep_ept_compiled(ept) || !sweep_shape_valid(h->N, sh)) return SGS_ERR_ARG;
+  int n = 0;
+  cudaError_t e = sweep_max_clusters(sh, h->sweep_arith, &n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SGS_ERR_UNSUPPORTED;
+  }
+  if (n < 1) return SGS_ERR_UNSUPPORTED;
+  h->sweep = sh;
+  return SGS_OK;
+}
+
+int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning* out, void* stream) {
+  if (!h || !f || !P || reps < 1) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  const bool prof = h->prof;
+  h->prof = false;
+  const SweepShape start = h->sweep;
+  const int K = h->N * h->N * h->N;
+  SweepShape best = start;
+  float best_ms = -1.0f;
+  int tried = 0, r = SGS_OK;
+  const int epts[] = {2, 4, 8, 12, 16, 20, 24, 28, 32};
+  for (int ept : epts) {
+    if (h->N % ept) continue;
+    for (int cs = 1; cs <= 16; cs *= 2) {
+      int per = (K + ept * cs - 1) / (ept * cs);
+      int tpb = (per + 31) / 32 * 32;
+      if (tpb < 128) tpb = 128;
+      SweepShape sh{ept, cs, tpb};
+      if (!sweep_shape_valid(h->N, sh)) continue;
+      if ((long long)(tpb - 32) * cs * ept >= K && tpb > 128) continue;  // a whole warp idle in every CTA
+      int n = 0;
+      if (sweep_max_clusters(sh, h->sweep_arith, &n) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (n < 1) continue;
+      h->sweep = sh;
+      float ms = 0.0f;
+      r = time_sweeps(h, f, P, 1, st, &ms);  // warm-up
+      if (r == SGS_OK) r = time_sweeps(h, f, P, reps, st, &ms);
+      if (r != SGS_OK) break;
+      tried++;
+      if (best_ms < 0.0f || ms < best_ms) {
+        best_ms = ms;
+        best = sh;
+      }
+    }
+    if (r != SGS_OK) break;
+  }
+  h->sweep = r == SGS_OK ? best : start;
+  h->prof = prof;
+  if (r != SGS_OK) return r;
+  if (out) {
+    out->sweep_ept = best.ept;
+    out->sweep_cluster = best.cluster;
+    out->sweep_threads = best.tpb;
+    out->sweep_ms = best_ms / reps;
+    out->candidates = tried;
+    out->sum_warps = h->NW;
+    out->sum_units = (int)h->units.size();
+    out->sum_blocks = (int)h->units.size() * ((h->G + h->NW - 1) / h->NW);
+  }
+  return SGS_OK;
+}
 
 int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream) {
   if (!h || !out) return SGS_ERR_ARG;

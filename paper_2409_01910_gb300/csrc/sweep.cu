@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int q = blockIdx.x / CS;
   if (q >= a.n_inst) return;  // whole cluster, uniformly
+  if (a.active && !a.active[q]) return;
   const InstDev& I = a.inst[q];
   __shared__ SweepSmem<E> sm;
   const int N = a.N, K = N * N * N;
@@ -550,7 +551,7 @@ SweepShape sweep_shape(int N, int arith) {
 
 template <typename E, int EPT>
 static cudaError_t launch_sweep_t(const SweepArgs& a, const SweepShape& sh, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_sweep<E, EPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = func_attr((const void*)k_sweep<E, EPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.n_inst * sh.cluster);
@@ -581,6 +582,51 @@ static cudaError_t launch_sweep_e(const SweepArgs& a, const SweepShape& sh, cuda
     case 32: return launch_sweep_t<E, 32>(a, sh, st);
   }
   return cudaErrorInvalidConfiguration;
+}
+
+template <typename E, int EPT>
+static cudaError_t max_clusters_t(const SweepShape& sh, int* n) {
+  cudaError_t e = func_attr((const void*)k_sweep<E, EPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sh.cluster);
+  cfg.blockDim = dim3(sh.tpb);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = sh.cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(n, k_sweep<E, EPT>, &cfg);
+}
+
+template <typename E>
+static cudaError_t max_clusters_e(const SweepShape& sh, int* n) {
+  switch (sh.ept) {
+    case 2: return max_clusters_t<E, 2>(sh, n);
+    case 4: return max_clusters_t<E, 4>(sh, n);
+    case 8: return max_clusters_t<E, 8>(sh, n);
+    case 12: return max_clusters_t<E, 12>(sh, n);
+    case 16: return max_clusters_t<E, 16>(sh, n);
+    case 20: return max_clusters_t<E, 20>(sh, n);
+    case 24: return max_clusters_t<E, 24>(sh, n);
+    case 28: return max_clusters_t<E, 28>(sh, n);
+    case 32: return max_clusters_t<E, 32>(sh, n);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+bool sweep_ept_compiled(int ept) {
+  return ept == 2 || ept == 4 || ept == 8 || ept == 12 || ept == 16 || ept == 20 || ept == 24 || ept == 28 ||
+         ept == 32;
+}
+
+cudaError_t sweep_max_clusters(const SweepShape& sh, int arith, int* n) {
+  *n = 0;
+  if (arith == kSweepF64) return max_clusters_e<double>(sh, n);
+  if (arith == kSweepDF64) return max_clusters_e<dfloat>(sh, n);
+  return max_clusters_e<float>(sh, n);
 }
 
 bool sweep_shape_valid(int N, const SweepShape& sh) {

@@ -82,3 +82,22 @@ def heat_64cells_32v(seed: int = 0) -> Workload:
     TR = float(rng.uniform(1.5, 2.5))
     return Workload("heat1d_J64_N32_eps0.01", J=64, N=32, L=8.0, eps=0.01, T_left=TL, T_right=TR,
                     T_init=0.5 * (TL + TR), seed=seed, tol=1e-8)
+
+
+def heat_batch(n: int = 64, seed: int = 0, J_range=(32, 256), N_choices=(24, 32), eps_range=(1e-3, 1.0),
+               L: float = 8.0) -> list:
+    """Independent heat-transfer instances of a batch: cells uniform in J_range (inclusive),
+    velocity grid drawn from N_choices, eps log-uniform in eps_range, wall temperatures
+    T_L ~ U[0.8, 1.2], T_R ~ U[1.5, 2.5], box [-L, L]^3; each instance's initial state has its
+    own seed (seed * 1000 + index)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(n):
+        J = int(rng.integers(J_range[0], J_range[1] + 1))
+        N = int(N_choices[int(rng.integers(0, len(N_choices)))])
+        eps = float(np.exp(rng.uniform(np.log(eps_range[0]), np.log(eps_range[1]))))
+        TL = float(rng.uniform(0.8, 1.2))
+        TR = float(rng.uniform(1.5, 2.5))
+        out.append(Workload(f"heat1d_batch{q}_J{J}_N{N}", J=J, N=N, L=L, eps=eps, T_left=TL, T_right=TR,
+                            T_init=0.5 * (TL + TR), seed=seed * 1000 + q, tol=1e-8))
+    return out

@@ -54,6 +54,19 @@ class _Problem(C.Structure):
     ]
 
 
+class _Tuning(C.Structure):
+    _fields_ = [
+        ("sweep_ept", C.c_int),
+        ("sweep_cluster", C.c_int),
+        ("sweep_threads", C.c_int),
+        ("sweep_ms", C.c_float),
+        ("candidates", C.c_int),
+        ("sum_warps", C.c_int),
+        ("sum_units", C.c_int),
+        ("sum_blocks", C.c_int),
+    ]
+
+
 class _Stats(C.Structure):
     _fields_ = [
         ("status", C.c_uint),
@@ -138,6 +151,12 @@ def lib(build: bool = True):
             "sgs_vcycle": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]),
             "sgs_max_levels": (C.c_int, [vp]),
             "sgs_residual_noalloc": (C.c_int, [C.POINTER(_Problem), vp, vp, vp, vp, vp]),
+            "sgs_update_active": (C.c_int, [vp, vp, C.c_double, vp]),
+            "sgs_activate_all": (C.c_int, [vp, vp]),
+            "sgs_read_active": (C.c_int, [vp, C.POINTER(C.c_int), vp]),
+            "sgs_get_sweep_shape": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "sgs_set_sweep_shape": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+            "sgs_autotune": (C.c_int, [vp, vp, vp, C.c_int, C.POINTER(_Tuning), vp]),
             "sgs_read_status": (C.c_int, [vp, C.POINTER(_Stats), vp]),
             "sgs_reset_stats": (C.c_int, [vp, vp]),
             "sgs_destroy": (None, [vp]),
@@ -264,6 +283,30 @@ class Solver:
     def max_levels(self) -> int:
         return int(lib().sgs_max_levels(self.h))
 
+    def update_active(self, res, tol, stream=None):
+        _check(lib().sgs_update_active(self.h, _ptr(res), tol, _stream(stream)), "sgs_update_active")
+
+    def activate_all(self, stream=None):
+        _check(lib().sgs_activate_all(self.h, _stream(stream)), "sgs_activate_all")
+
+    def read_active(self, stream=None) -> list:
+        a = (C.c_int * self.n_inst)()
+        _check(lib().sgs_read_active(self.h, a, _stream(stream)), "sgs_read_active")
+        return [int(x) for x in a]
+
+    def sweep_shape(self):
+        e, c, t = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().sgs_get_sweep_shape(self.h, C.byref(e), C.byref(c), C.byref(t)), "sgs_get_sweep_shape")
+        return int(e.value), int(c.value), int(t.value)
+
+    def set_sweep_shape(self, ept, cluster, threads):
+        _check(lib().sgs_set_sweep_shape(self.h, ept, cluster, threads), "sgs_set_sweep_shape")
+
+    def autotune(self, f, P, reps=1, stream=None) -> dict:
+        t = _Tuning()
+        _check(lib().sgs_autotune(self.h, _ptr(f), _ptr(P), reps, C.byref(t), _stream(stream)), "sgs_autotune")
+        return {k: (float(getattr(t, k)) if k == "sweep_ms" else int(getattr(t, k))) for k, _ in _Tuning._fields_}
+
     def read_status(self, stream=None) -> dict:
         st = _Stats()
         _check(lib().sgs_read_status(self.h, C.byref(st), _stream(stream)), "sgs_read_status")
@@ -282,3 +325,104 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Independent steady problems of mixed velocity grids solved together.
+
+    Kernels are compiled per velocity grid, so the problems are grouped by nv: one handle
+    (one persistent scan launch, one CTA cluster per instance) per group, each group on its
+    own stream. A defect-correction cycle of every group is captured in one CUDA graph:
+    FP64 collision and residual per instance, deactivation of the converged instances, then
+    lo_iters mixed-precision SGS iterations."""
+
+    def __init__(self, problems, device="cuda"):
+        import torch
+
+        self.problems = list(problems)
+        self.groups = {}
+        for i, p in enumerate(self.problems):
+            self.groups.setdefault(p.nv, []).append(i)
+        self.solvers, self.f, self.Q, self.P, self.res, self.streams = {}, {}, {}, {}, {}, {}
+        for nv, idx in self.groups.items():
+            s = Solver([self.problems[i] for i in idx], device=device)
+            self.solvers[nv] = s
+            self.f[nv], self.Q[nv], self.P[nv] = s.field(), s.field(), s.field()
+            self.res[nv] = torch.zeros(len(idx), dtype=torch.float64, device=device)
+            self.streams[nv] = torch.cuda.Stream(device=device)
+        self.graph = None
+
+    def view(self, i: int):
+        """The cells of problem i inside its group's field."""
+        nv = self.problems[i].nv
+        return self.solvers[nv].view(self.f[nv], self.groups[nv].index(i))
+
+    def load(self, states):
+        """Copies the initial distribution of every problem (arrays of shape (nx, nv, nv, nv))."""
+        import torch
+
+        for i, x in enumerate(states):
+            self.view(i).copy_(torch.as_tensor(x))
+        for s in self.solvers.values():
+            s.activate_all()
+
+    def _cycle(self, lo_iters: int, tol: float):
+        import torch
+
+        cur = torch.cuda.current_stream()
+        for nv, s in self.solvers.items():
+            st = self.streams[nv]
+            st.wait_stream(cur)
+            with torch.cuda.stream(st):
+                s.dc_step(self.f[nv], self.Q[nv], self.P[nv], 0, res=self.res[nv], stream=st)
+                s.update_active(self.res[nv], tol, stream=st)
+                for it in range(lo_iters):
+                    s.iterate(self.f[nv], self.Q[nv], self.P[nv], flags=IT_P_VALID if it == 0 else 0, stream=st)
+        for st in self.streams.values():
+            cur.wait_stream(st)
+
+    def autotune(self, reps: int = 1) -> dict:
+        """Scan-shape autotuner per velocity grid (advances the iterates; see sgs_autotune)."""
+        out = {}
+        for nv, s in self.solvers.items():
+            s.collide(self.f[nv], self.Q[nv], self.P[nv])
+            out[nv] = s.autotune(self.f[nv], self.P[nv], reps=reps)
+        return out
+
+    def capture(self, lo_iters: int, tol: float = 1e-8):
+        """Records one defect-correction cycle of all groups in a CUDA graph (after one eager
+        warm-up cycle)."""
+        import torch
+
+        self._cycle(lo_iters, tol)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._cycle(lo_iters, tol)
+        self.graph = g
+        return g
+
+    def step(self, lo_iters: int = 10, tol: float = 1e-8):
+        """One cycle: replays the captured graph if there is one, else runs eagerly."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._cycle(lo_iters, tol)
+
+    def residuals(self):
+        """FP64 residual of every problem at the last evaluation, in problem order."""
+        import torch
+
+        torch.cuda.synchronize()
+        out = [0.0] * len(self.problems)
+        for nv, idx in self.groups.items():
+            r = self.res[nv].cpu().tolist()
+            for k, i in enumerate(idx):
+                out[i] = r[k]
+        return out
+
+    def status(self) -> int:
+        st = 0
+        for s in self.solvers.values():
+            st |= s.read_status()["status"]
+        return st

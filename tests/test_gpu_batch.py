@@ -1,0 +1,159 @@
+"""GPU tests of batches: several independent problems in one handle (one cluster per
+instance in the persistent scan), mixed velocity grids in one CUDA graph, per-instance
+deactivation of converged problems, and the scan-shape autotuner (any shape it may pick
+keeps oracle parity)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2409_01910_gb300 import inputs as I
+from paper_2409_01910_gb300 import sgs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sgs.lib()
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def problems(N=8, precision=sgs.FP64, inner_fixed=4):
+    out = []
+    for J, eps, TL, TR in ((4, 0.05, 1.0, 1.6), (6, 0.3, 0.9, 2.2), (8, 1.0, 1.1, 1.8)):
+        out.append(sgs.Problem(nx=J, nv=N, v_max=6.0, eps=eps, bc_T=(TL, TR), precision=precision,
+                               inner_fixed=inner_fixed, total_mass=1.0))
+    return out
+
+
+def states(ps, seed=1):
+    return [I.initial_state(p.nx, p.nv, p.v_max, T=1.4, seed=seed + q) for q, p in enumerate(ps)]
+
+
+def test_batched_instances_match_single_problems():
+    """Each instance of a 3-instance handle evolves as it does alone (FP64)."""
+    ps = problems()
+    f0 = states(ps)
+    s = sgs.Solver(ps)
+    f, Q, P = s.field(), s.field(), s.field()
+    for q in range(3):
+        s.view(f, q).copy_(torch.from_numpy(f0[q]))
+    for it in range(2):
+        s.iterate(f, Q, P, flags=sgs.IT_EVAL | (sgs.IT_P_VALID if it else 0))
+    assert s.read_status()["status"] == 0
+    for q, p in enumerate(ps):
+        s1 = sgs.Solver(p)
+        g, Q1, P1 = s1.field(), s1.field(), s1.field()
+        g.copy_(torch.from_numpy(f0[q].reshape(-1)))
+        for it in range(2):
+            s1.iterate(g, Q1, P1, flags=sgs.IT_EVAL | (sgs.IT_P_VALID if it else 0))
+        assert rel(s.view(f, q).cpu().numpy(), g.view(p.nx, p.nv, p.nv, p.nv).cpu().numpy()) <= 1e-13
+
+
+def test_inactive_instance_is_frozen():
+    ps = problems()
+    s = sgs.Solver(ps)
+    f, Q, P = s.field(), s.field(), s.field()
+    for q, x in enumerate(states(ps)):
+        s.view(f, q).copy_(torch.from_numpy(x))
+    s.collide(f, Q, P)
+    res = torch.tensor([1e-9, 1.0, 2e-8], dtype=torch.float64, device="cuda")
+    s.update_active(res, 1e-8)
+    assert s.read_active() == [0, 1, 1]
+    before = f.clone()
+    s.iterate(f, Q, P, flags=sgs.IT_P_VALID)
+    assert torch.equal(s.view(f, 0), s.view(before, 0))
+    assert not torch.equal(s.view(f, 1), s.view(before, 1))
+    assert not torch.equal(s.view(f, 2), s.view(before, 2))
+    st = s.read_status()
+    assert st["visits"] == 2 * (6 + 8)
+    s.activate_all()
+    assert s.read_active() == [1, 1, 1]
+
+
+def test_mixed_grid_batch_graph_replay_is_bitwise_eager():
+    """Two velocity grids (8^3, 12^3), mixed precision: replaying the captured cycle gives
+    exactly the eager result, and each problem matches its own solver."""
+    ps = problems(8, sgs.FP32, inner_fixed=0) + problems(12, sgs.FP32, inner_fixed=0)[:2]
+    f0 = states(ps, seed=7)
+    eager = sgs.Batch(ps)
+    eager.load(f0)
+    for _ in range(3):
+        eager.step(lo_iters=3)
+    graphed = sgs.Batch(ps)
+    graphed.load(f0)
+    graphed.capture(lo_iters=3)  # runs one eager warm-up cycle, then records one
+    for _ in range(2):
+        graphed.step()
+    torch.cuda.synchronize()
+    assert eager.status() == 0 and graphed.status() == 0
+    for i in range(len(ps)):
+        assert torch.equal(eager.view(i), graphed.view(i)), i
+    assert eager.residuals() == graphed.residuals()
+    # problem 3 (12^3 grid) against a solver of its own
+    p = ps[3]
+    s = sgs.Solver(p)
+    g, Q, P = s.field(), s.field(), s.field()
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.copy_(torch.from_numpy(f0[3].reshape(-1)))
+    for _ in range(3):
+        s.dc_step(g, Q, P, 0, res=res)
+        for it in range(3):
+            s.iterate(g, Q, P, flags=sgs.IT_P_VALID if it == 0 else 0)
+    # a different lane grouping of the FP32 sums leaves FP32-rounding differences only
+    assert rel(eager.view(3).cpu().numpy(), g.view(p.nx, p.nv, p.nv, p.nv).cpu().numpy()) <= 1e-6
+
+
+def test_batch_converges_and_freezes_converged_problems():
+    ps = problems(8, sgs.FP32, inner_fixed=0)
+    ps = [sgs.Problem(**{**p.__dict__, "inner_tol": 1e-11}) for p in ps]
+    tol = 1e-6
+    b = sgs.Batch(ps)
+    b.load(states(ps, seed=3))
+    b.capture(lo_iters=8, tol=tol)
+    res = None
+    for cycle in range(40):
+        b.step()
+        res = b.residuals()
+        if max(res) < tol:
+            break
+    assert max(res) < tol, res
+    assert b.status() == 0
+    assert b.solvers[8].read_active() == [0, 0, 0]
+    # every problem is frozen now: another cycle changes no iterate
+    before = [b.view(i).clone() for i in range(len(ps))]
+    b.step()
+    torch.cuda.synchronize()
+    for i in range(len(ps)):
+        assert torch.equal(before[i], b.view(i)), i
+
+
+def test_autotuned_shape_keeps_oracle_parity(oracle):
+    N, J, L = 8, 5, 6.0
+    d = dict(N=N, L=L, J=J, eps=0.1, bc_T=(1.0, 1.7), total_mass=1.0, inner_fixed=5)
+    f0 = I.initial_state(J, N, L, T=1.4, seed=11)
+    po = oracle.Problem(**d)
+    Qo, Po, nuo = oracle.collide(po, f0)
+    fo = f0.copy()
+    oracle.sweep(po, fo, Po, nuo, 1)
+    s = sgs.Solver(sgs.Problem(nx=J, nv=N, v_max=L, eps=0.1, bc_T=(1.0, 1.7), inner_fixed=5))
+    scratch, Q, P = s.field(), s.field(), s.field()
+    scratch.copy_(torch.from_numpy(f0.reshape(-1)))
+    s.collide(scratch, Q, P)
+    t = s.autotune(scratch, P, reps=1)
+    assert t["candidates"] >= 2 and t["sweep_ms"] > 0
+    assert (t["sweep_ept"], t["sweep_cluster"], t["sweep_threads"]) == s.sweep_shape()
+    for shape in (s.sweep_shape(), (2, 2, 128), (4, 1, 128)):
+        s.set_sweep_shape(*shape)
+        f = torch.from_numpy(f0.reshape(-1)).cuda()
+        s.collide(f, Q, P)
+        s.sweep_forward(f, torch.from_numpy(Po.reshape(-1)).cuda())
+        assert rel(f.cpu().numpy().reshape(f0.shape), fo) <= 1e-12, shape
+    assert s.read_status()["status"] == 0

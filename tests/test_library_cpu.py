@@ -85,3 +85,44 @@ def test_closed_form_weights_match_oracle_quadrature(oracle, kernel, L_):
     for a2, b2 in pairs:
         g = sgs.host_weight(N, L_, kernel, b0, a2, b2)
         assert abs(g - oracle.G(N, L_, kernel, b0, a2, b2)) <= 2e-14 * scale, (a2, b2)
+
+
+def test_batch_api_on_host(L):
+    """Batch and tuning entry points: host-side validation and the default scan shape."""
+    ps = [sgs.Problem(nx=J, nv=16) for J in (4, 9)]
+    arr = (sgs._Problem * 2)(*[p.c() for p in ps])
+    h, ws = C.c_void_p(), C.c_size_t()
+    assert L.sgs_setup(arr, 2, C.byref(h), C.byref(ws)) == sgs.OK
+    e, c, t = C.c_int(), C.c_int(), C.c_int()
+    assert L.sgs_get_sweep_shape(h, C.byref(e), C.byref(c), C.byref(t)) == sgs.OK
+    # every node of a cell has an owner thread; warps 0-3 exist for the Newton evaluations
+    assert 16 % e.value == 0 and c.value in (1, 2, 4, 8, 16) and 128 <= t.value <= 256 and t.value % 32 == 0
+    assert e.value * c.value * t.value >= 16**3
+    assert L.sgs_get_sweep_shape(h, None, C.byref(c), C.byref(t)) == sgs.ERR_ARG
+    # nothing is enqueued before a workspace is bound
+    assert L.sgs_update_active(h, C.c_void_p(16), 1e-8, None) == sgs.ERR_WORKSPACE
+    assert L.sgs_update_active(h, C.c_void_p(16), -1.0, None) == sgs.ERR_ARG
+    assert L.sgs_activate_all(h, None) == sgs.ERR_WORKSPACE
+    assert L.sgs_autotune(h, C.c_void_p(16), C.c_void_p(16), 1, None, None) == sgs.ERR_WORKSPACE
+    assert L.sgs_autotune(h, C.c_void_p(16), C.c_void_p(16), 0, None, None) == sgs.ERR_ARG
+    # shapes that leave nodes without an owner, or break the cluster/thread rules
+    for bad in ((3, 4, 256), (8, 3, 256), (8, 16, 100), (4, 1, 256), (8, 32, 128)):
+        assert L.sgs_set_sweep_shape(h, *bad) == sgs.ERR_ARG, bad
+    L.sgs_destroy(h)
+
+
+def test_batch_inputs_follow_their_distributions():
+    from paper_2409_01910_gb300 import inputs as I
+
+    b = I.heat_batch(64, seed=0)
+    assert len(b) == 64
+    assert all(32 <= w.J <= 256 and w.N in (24, 32) and 1e-3 <= w.eps <= 1.0 for w in b)
+    assert all(0.8 <= w.T_left <= 1.2 and 1.5 <= w.T_right <= 2.5 and w.L == 8.0 for w in b)
+    assert {w.N for w in b} == {24, 32}
+    # log-uniform eps: about half the instances below sqrt(1e-3)
+    below = sum(w.eps < 10**-1.5 for w in b)
+    assert 16 <= below <= 48
+    # reproducible, and distinct seeds per instance
+    b2 = I.heat_batch(64, seed=0)
+    assert [(w.J, w.N, w.eps) for w in b] == [(w.J, w.N, w.eps) for w in b2]
+    assert len({w.seed for w in b}) == 64
