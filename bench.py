@@ -31,7 +31,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "cell-updates/s (SGS-PFP, mixed FP32 collision + FP64 defect correction)"
+METRIC = ("cell-updates/s (mixed-precision SGS-PFP; time to residual 1e-8, mixed vs FP64, under "
+          "time_to_residual_1e-8)")
 UNIT = "cell-updates/s"
 L2_BYTES = 129 * 2**20
 
@@ -48,7 +49,7 @@ def parse():
     ap.add_argument("--no-t2tol", action="store_true", help="skip the time-to-residual runs")
     ap.add_argument("--t2tol-all", action="store_true", help="also time the plain FP64 SGS form to 1e-8")
     ap.add_argument("--t2tol-cap", type=float, default=150.0, help="seconds allowed per time-to-residual run")
-    ap.add_argument("--case", choices=["sweep", "sum", "sum64"], default=None,
+    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf"], default=None,
                     help="run a small case of one kernel class (for profiler captures) and exit")
     return ap.parse_args()
 
@@ -189,7 +190,7 @@ def run_native(args, rank, world, local):
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     dom = max(prof, key=lambda k: prof[k][0])
-    roofs = {k: roofline(k, prof, wl, sm_mhz) for k in ("sweep", "sum", "sum_fp64") if prof[k][1] > 0}
+    roofs = {k: roofline(k, prof, wl, sm_mhz) for k in ("sweep", "sum", "sum_fp64", "sum_df64") if prof[k][1] > 0}
     roof = roofs.get(dom) or roofline(dom, prof, wl, sm_mhz)
 
     # end to end through the C ABI with host buffers: H2D of the state (f, P), one step,
@@ -224,9 +225,10 @@ def run_native(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": wl.name, "cells": wl.J, "nv": wl.N, "v_max": wl.L, "eps": wl.eps,
                        "T_walls": [round(wl.T_left, 6), round(wl.T_right, 6)], "collision": "maxwell",
-                       "precision": ("mixed: FP32 direct spectral sums in increment form against the last FP64 "
-                                     "evaluation, double-float (FP32 pair) scans with FP64 scalar decisions, FP64 "
-                                     "moments/residual/defect correction"),
+                       "precision": ("mixed: FP32 direct spectral sums in increment form against the last "
+                                     "high-precision evaluation; defect-correction sums in double-float (FP32 "
+                                     "pairs); double-float scans with FP64 scalar decisions; FP64 moments, "
+                                     "transforms and residual"),
                        "dc_every": args.dc_every, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
@@ -290,6 +292,16 @@ def roofline(cls, prof, wl, sm_mhz):
         return {"kernel": "k_sum<double> (direct spectral sum, FP64)", "bound": "alu", "achieved": ach,
                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                 "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (of nominal)"}
+    if cls == "sum_df64":
+        # FP32-pipe operations of one pair in the double-float sum: 8 for w b (two
+        # two-products with cross terms) + 4 x 12 for the products with a and their two-sum
+        # accumulation
+        ops = 56 * 0.5 * pairs_per_cell(wl.N) * wl.J
+        ach = ops / (avg * 1e-3) / 1e12
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+        return {"kernel": "k_sum_df (direct spectral sum, double-float on the FP32 pipes)", "bound": "alu",
+                "achieved": ach, "peak": peak, "unit": "T FP32-pipe op/s", "frac": ach / peak, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 1 op x {sm_mhz:.0f} MHz (median sampled)"}
     if cls == "sweep":
         byts = 5 * K * 8 * wl.J  # read f_{j-1}, f_j, f_{j+1}, P_j; write f_j per visit
         ach = byts / (avg * 1e-3) / 1e9
@@ -483,6 +495,8 @@ def profile_case(which):
         if which == "sweep":
             g = f.clone()
             s.sweep_forward(g, P)
+        elif which == "sumdf":
+            s.collide(f, Q, P, precision=sgs.DF64)
         else:
             s.collide(f, Q, P)
     torch.cuda.synchronize()

@@ -51,7 +51,10 @@ extern "C" {
 
 enum sgs_collision { SGS_MAXWELL = 0, SGS_HARD_SPHERE = 1, SGS_BGK = 2 };
 enum sgs_bc_kind { SGS_DIFFUSE = 0, SGS_INFLOW = 1 };
-enum sgs_precision { SGS_FP64 = 0, SGS_FP32 = 1 };
+/* SGS_DF64 is an arithmetic for sgs_collide_prec and sgs_set_dc_precision only (not a problem
+ * precision): double-float spectral sums, each value a pair of FP32 numbers (hi + lo), on the
+ * FP32 pipes, about 2^-48 relative error per term; available on SGS_FP32 handles. */
+enum sgs_precision { SGS_FP64 = 0, SGS_FP32 = 1, SGS_DF64 = 2 };
 enum sgs_inner_method { SGS_PFP = 0, SGS_FP = 1 };
 
 /* Boundary data of one side: a diffuse wall at temperature T moving with tangential
@@ -147,8 +150,9 @@ int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* 
 int sgs_residual_noalloc(const sgs_problem* p, const double* f, const double* Q, const double* rhs, double* res,
                          void* stream);
 
-/* Collision step in a chosen arithmetic (SGS_FP32 needs a handle set up with precision
- * SGS_FP32, whose workspace then carries both weight tables). Same fields as sgs_collide. */
+/* Collision step in a chosen arithmetic (SGS_FP32 and SGS_DF64 need a handle set up with
+ * precision SGS_FP32, whose workspace then carries the FP64 and FP32 weight tables and the
+ * FP32 remainder table). Same fields as sgs_collide. */
 int sgs_collide_prec(sgs_handle* h, const double* f, double* Q, double* P, int precision, void* stream);
 
 /* One full SGS iteration (eq. (29)): [collide], forward scan, collide, backward scan,
@@ -163,16 +167,21 @@ int sgs_iterate(sgs_handle* h, double* f, double* Q, double* P, const double* rh
                 void* stream);
 
 /* One step of FP64 defect correction for the mixed solver (handle set up with SGS_FP32):
- *   Q, P = FP64 collision of the current iterate f_k; res = its FP64 residual (device,
- *   n_inst doubles, nullable); f_k becomes the reference state; then lo_iters SGS
- *   iterations in which every FP32 collision is evaluated in increment form
- *     Q(f) = Q_FP64(f_k) + [Q_s(a - a_k, b) + Q_s(a_k, b - b_k)]_FP32,  a = f - M, b = f + M,
+ *   Q, P = high-precision collision of the current iterate f_k (double-float or FP64 sums,
+ *   sgs_set_dc_precision); res = its FP64 residual (device, n_inst doubles, nullable); f_k
+ *   becomes the reference state; then lo_iters SGS iterations in which every FP32
+ *   collision is evaluated in increment form
+ *     Q(f) = Q_hi(f_k) + [Q_s(a - a_k, b) + Q_s(a_k, b - b_k)]_FP32,  a = f - M, b = f + M,
  *   an exact identity of the symmetric bilinear form whose FP32 rounding error scales with
  *   f - f_k. Each step therefore moves f towards the FP64 solution R_FP64(f) = 0 without an
  *   FP32 noise floor. The reference stays in force for later FP32 collisions on this handle
  *   until sgs_dc_clear() or the next sgs_dc_step(). Q and P are caller-owned device fields. */
 int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, int lo_iters, double* res, void* stream);
 int sgs_dc_clear(sgs_handle* h);
+/* Arithmetic of the high-precision collision in sgs_dc_step: SGS_DF64 (default on SGS_FP32
+ * handles: double-float sums on the FP32 pipes) or SGS_FP64 (FP64 sums). Moments, discrete
+ * Maxwellians, transforms and the residual are FP64 in both. */
+int sgs_set_dc_precision(sgs_handle* h, int precision);
 
 /* One FAS V-cycle (eq. (30)) on every instance, on 2 <= levels <= sgs_max_levels(h) grids
  * with H = 2h: pre SGS-PFP iterations, restriction of f and of the residual field (mean of
@@ -199,7 +208,8 @@ enum sgs_prof_class {
   SGS_PROF_RESIDUAL = 5,    /* outer residual */
   SGS_PROF_RESCALE = 6,     /* mass rescale, grid transfers and other vector updates */
   SGS_PROF_SUM_FP64 = 7,    /* direct spectral sum, FP64 */
-  SGS_PROF_CLASSES = 8
+  SGS_PROF_SUM_DF64 = 8,    /* direct spectral sum, double-float */
+  SGS_PROF_CLASSES = 9
 };
 int sgs_profile(sgs_handle* h, int enable);
 int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, int n_classes);

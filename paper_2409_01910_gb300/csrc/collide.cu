@@ -1,3 +1,4 @@
+#include <algorithm>
 // Collision step (eqs. (13)-(16), (28)) for every cell of every instance.
 //
 // Q = Q^FSM[f,f] - Q^FSM[M,M] is evaluated as the single symmetric bilinear sum
@@ -389,6 +390,152 @@ __global__ void __launch_bounds__(128) k_sum(SumArgs<T> a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Direct spectral sum in double-float arithmetic on the FP32 pipes (the high-precision
+// evaluation of the defect correction). Same units, steps and weight order as k_sum; the
+// transformed rows arrive split into (hi, lo) float pairs (k_split_spec) and the weights as
+// the FP32 table (hi) plus its FP32 remainder table (lo). Products are formed exactly in
+// their leading part (FMA two-product) with first-order cross terms, and accumulated by
+// error-free two-sums into (hi, lo) accumulators, so each term carries about 2^-48 relative
+// error instead of FP32's 2^-24.
+// One block of KW warps serves one group of 32 cells (lane = cell); warp w accumulates the
+// outputs k3 = -H + w + KW j. Rows and weights are double-buffered in shared memory by
+// bulk copies, as in k_sum.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void df_mul_acc(float xh, float xl, float yh, float yl, float& ah, float& al) {
+  // (ah, al) += (xh + xl)(yh + yl), to first order in the low parts
+  float q = xh * yh;
+  float e = fmaf(xh, yh, -q);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  float s = ah + q;
+  float z = s - ah;
+  float err = (ah - (s - z)) + (q - z);
+  ah = s;
+  al += err + e;
+}
+
+template <int H, int KW>
+__global__ void __launch_bounds__(KW * 32, 2) k_sum_df(SumDfArgs a) {
+  constexpr int n = 2 * H + 1;
+  constexpr int NP = 3 * H * H + 3 * H + 1;
+  constexpr int PW = (NP + 3) / 4 * 4;
+  constexpr int NJ = (n + KW - 1) / KW;  // outputs per warp
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* Wb = (float*)smraw;                            // [2][2][PW]: buffer, (hi, lo)
+  float4* rows = (float4*)(smraw + 4 * PW * sizeof(float));  // [2][2][n][32]: buffer, (a, b)
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int s_err;
+
+  const int4 ud = a.units[blockIdx.x];
+  const long long step0 = a.unit_step0[blockIdx.x];
+  const int k1 = ud.x, k2 = ud.y, m1lo = ud.z, m1hi = ud.w;
+  const int m2lo = max(-H, k2 - H), m2hi = min(H, k2 + H);
+  const int nm2 = m2hi - m2lo + 1;
+  const int S = (m1hi - m1lo + 1) * nm2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.y;
+  const uint32_t row_bytes = n * kLanes * sizeof(float4);
+  const uint32_t stage_bytes = 2 * PW * sizeof(float) + 2 * row_bytes;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    s_err = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int s) {
+    int m1 = m1lo + s / nm2, m2 = m2lo + s % nm2;
+    int b = s & 1;
+    mbar_arrive_expect_tx(&bar[b], stage_bytes);
+    bulk_g2s(Wb + (2 * b) * PW, a.Whi + (step0 + s) * PW, PW * sizeof(float), &bar[b]);
+    bulk_g2s(Wb + (2 * b + 1) * PW, a.Wlo + (step0 + s) * PW, PW * sizeof(float), &bar[b]);
+    long long ga = (((long long)g * n + (k1 - m1 + H)) * n + (k2 - m2 + H)) * n * kLanes;
+    long long gb = (((long long)g * n + (m1 + H)) * n + (m2 + H)) * n * kLanes;
+    float4* dst = rows + (2 * b) * n * kLanes;
+    bulk_g2s(dst, a.ahat + ga, row_bytes, &bar[b]);
+    bulk_g2s(dst + n * kLanes, a.bhat + gb, row_bytes, &bar[b]);
+  };
+
+  if (threadIdx.x == 0 && S > 0) issue(0);
+
+  float rh[NJ], rl[NJ], ih[NJ], il[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; j++) rh[j] = rl[j] = ih[j] = il[j] = 0.0f;
+
+  int fail_b = 0, fail_par = 0;
+  for (int s = 0; s < S; s++) {
+    const int b = s & 1;
+    if (!mbar_wait(&bar[b], (s >> 1) & 1, a.spin_max)) {
+      s_err = 1;
+      fail_b = b;
+      fail_par = (s >> 1) & 1;
+    }
+    __syncthreads();
+    if (s_err) break;
+    // the other buffer was released by the barrier above: prefetch the next step into it
+    if (threadIdx.x == 0 && s + 1 < S) issue(s + 1);
+    const float* Wh = Wb + (2 * b) * PW;
+    const float* Wl = Wh + PW;
+    const float4* ra = rows + (2 * b) * n * kLanes;
+    const float4* rb = ra + n * kLanes;
+    int off = 0;  // first weight of the current m3 in the packed (m3, k3) order
+#pragma unroll
+    for (int m3 = -H; m3 <= H; m3++) {
+      const int lo = m3 - H > -H ? m3 - H : -H, hi = m3 + H < H ? m3 + H : H;
+      const float4 bv = rb[(m3 + H) * kLanes + lane];
+#pragma unroll
+      for (int j = 0; j < NJ; j++) {
+        const int k3 = -H + warp + KW * j;
+        if (k3 >= lo && k3 <= hi) {
+          const int p = off + k3 - lo;
+          const float wh = Wh[p], wl = Wl[p];
+          const float4 av = ra[(k3 - m3 + H) * kLanes + lane];
+          // w b = (w b_re, w b_im), leading parts exact
+          float brh = wh * bv.x, brl = fmaf(wh, bv.x, -brh);
+          brl = fmaf(wh, bv.y, brl);
+          brl = fmaf(wl, bv.x, brl);
+          float bih = wh * bv.z, bil = fmaf(wh, bv.z, -bih);
+          bil = fmaf(wh, bv.w, bil);
+          bil = fmaf(wl, bv.z, bil);
+          // a (w b): re += a_re br - a_im bi, im += a_re bi + a_im br
+          df_mul_acc(av.x, av.y, brh, brl, rh[j], rl[j]);
+          df_mul_acc(-av.z, -av.w, bih, bil, rh[j], rl[j]);
+          df_mul_acc(av.x, av.y, bih, bil, ih[j], il[j]);
+          df_mul_acc(av.z, av.w, brh, brl, ih[j], il[j]);
+        }
+      }
+      off += hi - lo + 1;
+    }
+  }
+  if (s_err) {
+    if (threadIdx.x == 0) {
+      atomicOr(&a.cnt[0].status, SGS_ST_TIMEOUT);
+      mbar_wait(&bar[fail_b], fail_par, a.spin_max);
+    }
+    return;
+  }
+  double2* out = a.partial + ((long long)blockIdx.x * a.G + g) * n * kLanes;
+#pragma unroll
+  for (int j = 0; j < NJ; j++) {
+    const int k3 = -H + warp + KW * j;
+    if (k3 <= H)
+      out[(k3 + H) * kLanes + lane] = make_double2((double)rh[j] + (double)rl[j], (double)ih[j] + (double)il[j]);
+  }
+}
+
+// In place: every complex FP64 value of the transformed rows becomes its (hi, lo) float pairs
+// (re_hi, re_lo, im_hi, im_lo), the layout k_sum_df reads.
+__global__ void k_split_spec(double2* x, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    double2 v = x[i];
+    dfloat r = df_split(v.x), m = df_split(v.y);
+    reinterpret_cast<float4*>(x)[i] = make_float4(r.hi, r.lo, m.hi, m.lo);
+  }
+}
+
 // Fixed-order sum of a row's unit partials (FP64 accumulation), written to qhat at (k1, k2,
 // k3) and conjugated at (-k1, -k2, -k3); row (0, 0) is computed in full and not mirrored.
 template <typename T>
@@ -551,7 +698,7 @@ __global__ void __launch_bounds__(256) k_collide_bgk(const double* __restrict__ 
 // Setup: weight blocks W[step][p] = beta_s for the (m3, k3) pairs of each (k1, k2, m1, m2)
 // step, in the loop order of k_sum, from the tables G[a2][b2] and Lo[m2] = G(2|m|, 0).
 // ---------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool LO>
 __global__ void k_build_weights(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
                                 const double* G, long long nb, const double* Lo, T* W) {
   int u = blockIdx.x;
@@ -588,7 +735,9 @@ __global__ void k_build_weights(const int4* units, const long long* unit_step0, 
       long long ll = l1 * l1 + l2 * l2 + l3 * l3;
       long long mm = (long long)m1 * m1 + (long long)m2 * m2 + (long long)m3 * m3;
       double w = G[a2 * nb + b2] - 0.5 * (Lo[ll] + Lo[mm]);
-      out[p] = (T)w;
+      // LO: the FP32 remainder w - (float)w, the low half of a double-float weight whose high
+      // half is the FP32 weight table
+      out[p] = LO ? (T)(w - (double)(float)w) : (T)w;
     }
   }
 }
@@ -637,6 +786,37 @@ cudaError_t launch_sum(const SumArgs<T>& a, int H, int NW, int n_units, cudaStre
     case 15: return launch_sum_t<T, 15>(a, NW, n_units, st);
   }
   return cudaErrorInvalidValue;
+}
+
+template <int H>
+static cudaError_t launch_sum_df_t(const SumDfArgs& a, int n_units, cudaStream_t st) {
+  constexpr int n = 2 * H + 1;
+  constexpr int NP = 3 * H * H + 3 * H + 1;
+  constexpr int PW = (NP + 3) / 4 * 4;
+  constexpr int KW = H >= 7 ? 8 : 4;
+  size_t smem = 4 * PW * sizeof(float) + 4 * (size_t)n * kLanes * sizeof(float4);
+  cudaError_t e = func_attr((const void*)k_sum_df<H, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_sum_df<H, KW><<<dim3(n_units, a.G), KW * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_df(const SumDfArgs& a, int H, int n_units, cudaStream_t st) {
+  switch (H) {
+    case 3: return launch_sum_df_t<3>(a, n_units, st);
+    case 5: return launch_sum_df_t<5>(a, n_units, st);
+    case 7: return launch_sum_df_t<7>(a, n_units, st);
+    case 9: return launch_sum_df_t<9>(a, n_units, st);
+    case 11: return launch_sum_df_t<11>(a, n_units, st);
+    case 13: return launch_sum_df_t<13>(a, n_units, st);
+    case 15: return launch_sum_df_t<15>(a, n_units, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_split_spec(double2* x, long long count, cudaStream_t st) {
+  k_split_spec<<<(int)std::min<long long>((count + 255) / 256, 152 * 16), 256, 0, st>>>(x, count);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -702,7 +882,13 @@ cudaError_t launch_collide_bgk(const double* f, const CellTables& ct, int C, int
 template <typename T>
 cudaError_t launch_build_weights(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
                                  const double* G, long long nb, const double* Lo, T* W, cudaStream_t st) {
-  k_build_weights<T><<<dim3(n_units, 8), 256, 0, st>>>(units, unit_step0, n_units, H, PW, G, nb, Lo, W);
+  k_build_weights<T, false><<<dim3(n_units, 8), 256, 0, st>>>(units, unit_step0, n_units, H, PW, G, nb, Lo, W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_weights_lo(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
+                                    const double* G, long long nb, const double* Lo, float* W, cudaStream_t st) {
+  k_build_weights<float, true><<<dim3(n_units, 8), 256, 0, st>>>(units, unit_step0, n_units, H, PW, G, nb, Lo, W);
   return cudaGetLastError();
 }
 

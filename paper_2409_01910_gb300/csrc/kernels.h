@@ -88,6 +88,21 @@ struct RedArgs {
   int n, G, n_rows;
 };
 
+// Double-float spectral sum: weights as (FP32 table, FP32 remainder table) in the packed
+// layout of the FP32 sum; rows as (re_hi, re_lo, im_hi, im_lo); partials in FP64.
+struct SumDfArgs {
+  const int4* units;
+  const long long* unit_step0;
+  const float* Whi;   // [steps][PW32]
+  const float* Wlo;   // [steps][PW32]
+  const float4* ahat;
+  const float4* bhat;
+  double2* partial;   // [units][G][n][32]
+  int G;
+  Counters* cnt;
+  long long spin_max;
+};
+
 template <typename T>
 struct CollideCtx {
   int N, C, H, NW, n_units;
@@ -141,6 +156,10 @@ cudaError_t launch_spectral_sum(const CollideCtx<T>& x, typename CplxOf<T>::type
 template <typename T>
 cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const CollideCtx<T>& x,
                                const typename CplxOf<T>::type* partial2, const double* Qadd, cudaStream_t st);
+cudaError_t launch_sum_df(const SumDfArgs& a, int H, int n_units, cudaStream_t st);
+cudaError_t launch_split_spec(double2* x, long long count, cudaStream_t st);
+cudaError_t launch_build_weights_lo(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
+                                    const double* G, long long nb, const double* Lo, float* W, cudaStream_t st);
 template <typename T>
 cudaError_t launch_build_weights(const int4* units, const long long* unit_step0, int n_units, int H, int PW,
                                  const double* G, long long nb, const double* Lo, T* W, cudaStream_t st);

@@ -99,9 +99,10 @@ struct sgs_handle {
   struct {
     size_t inst, cell_off, cell_inst, cnt, theta, nu, scratch, tw_cos, tw_sin, G, Lo, units, step0, row_k, row_start,
         row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, partial2, f_ref, Q_ref, theta_ref,
-        ahat_ref, active, end;
+        ahat_ref, active, W32lo, end;
   } off;
   bool dc_ref = false;  // FP32 collisions use the increment form against the stored reference
+  int dc_prec = SGS_DF64;  // arithmetic of the high-precision evaluation in sgs_dc_step
   // multigrid levels: lev[0] is the bound grid (tables at off.inst, off.cell_off, off.cell_inst);
   // level l has every instance's cell count halved l times and its own tables and fields
   struct Level {
@@ -269,6 +270,7 @@ void layout(sgs_handle* h) {
   f.Q_ref = take(dc ? sizeof(double) * h->field : 0);
   f.theta_ref = take(dc ? sizeof(double) * 5 * C : 0);
   f.ahat_ref = take(dc ? (size_t)G * n * n * n * kLanes * sizeof(float2) : 0);
+  f.W32lo = take(dc ? sizeof(float) * h->steps * h->PW32 : 0);
   size_t K = (size_t)N * N * N;
   int nl = (int)h->lev.size();
   for (int l = 0; l < nl; l++) {
@@ -543,6 +545,37 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 4);
     return cuda_status(launch_reduce_idft(f, Q, P, x, part2, h->at<double>(Lv.rQ), st));
   };
+  if (precision == SGS_DF64) {
+    if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
+    CollideCtx<double> x = collide_ctx<double>(h, l);
+    cudaError_t er;
+    {
+      Scope sc(h, SGS_PROF_DFT, st, 5);
+      er = launch_dft(f, x, DftMode{0, nullptr, nullptr}, st);
+      const long long cnt = (long long)h->lev[l].G * h->n * h->n * h->n * kLanes;
+      if (er == cudaSuccess) er = launch_split_spec(x.sb.ahat, cnt, st);
+      if (er == cudaSuccess) er = launch_split_spec(x.sb.bhat, cnt, st);
+    }
+    if (er != cudaSuccess) return cuda_status(er);
+    {
+      Scope sc(h, SGS_PROF_SUM_DF64, st, 1);
+      SumDfArgs d;
+      d.units = x.sum.units;
+      d.unit_step0 = x.sum.unit_step0;
+      d.Whi = h->at<float>(h->off.W32);
+      d.Wlo = h->at<float>(h->off.W32lo);
+      d.ahat = reinterpret_cast<const float4*>(x.sb.ahat);
+      d.bhat = reinterpret_cast<const float4*>(x.sb.bhat);
+      d.partial = x.sum.partial;
+      d.G = x.sum.G;
+      d.cnt = x.sum.cnt;
+      d.spin_max = x.sum.spin_max;
+      er = launch_sum_df(d, h->H, x.n_units, st);
+    }
+    if (er != cudaSuccess) return cuda_status(er);
+    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 4);
+    return cuda_status(launch_reduce_idft(f, Q, P, x, nullptr, nullptr, st));
+  }
   if (precision == SGS_FP32) {
     if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
     if (l == 0 ? h->dc_ref : h->lev[l].ref) return run_inc(collide_ctx<float>(h, l));
@@ -858,6 +891,10 @@ int sgs_bind_workspace(sgs_handle* h, void* device_ptr, size_t bytes) {
       e = launch_build_weights<float>(h->at<int4>(h->off.units), h->at<long long>(h->off.step0), (int)h->units.size(),
                                       h->H, h->PW32, h->at<double>(h->off.G), h->nb, h->at<double>(h->off.Lo),
                                       h->at<float>(h->off.W32), 0);
+    if (e == cudaSuccess && h->precision == SGS_FP32)
+      e = launch_build_weights_lo(h->at<int4>(h->off.units), h->at<long long>(h->off.step0), (int)h->units.size(),
+                                  h->H, h->PW32, h->at<double>(h->off.G), h->nb, h->at<double>(h->off.Lo),
+                                  h->at<float>(h->off.W32lo), 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   return cuda_status(e);
@@ -880,9 +917,9 @@ int sgs_collide(sgs_handle* h, const double* f, double* Q, double* P, void* stre
 }
 
 int sgs_collide_prec(sgs_handle* h, const double* f, double* Q, double* P, int precision, void* stream) {
-  if (!h || !f || (precision != SGS_FP64 && precision != SGS_FP32)) return SGS_ERR_ARG;
+  if (!h || !f || (precision != SGS_FP64 && precision != SGS_FP32 && precision != SGS_DF64)) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;
-  if (precision == SGS_FP32 && h->precision != SGS_FP32) return SGS_ERR_ARG;
+  if (precision != SGS_FP64 && (h->precision != SGS_FP32 || !h->spectral)) return SGS_ERR_ARG;
   return collide_impl(h, f, Q, P, precision, as_stream(stream));
 }
 
@@ -925,7 +962,7 @@ int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, int lo_iters, do
   int r;
   // FP64 collision and residual of the current iterate f_k: the convergence test
   h->dc_ref = false;
-  if ((r = collide_impl(h, f, Q, P, SGS_FP64, st))) return r;
+  if ((r = collide_impl(h, f, Q, P, h->dc_prec, st))) return r;
   if (res && (r = residual_impl(h, f, Q, nullptr, res, st))) return r;
   // new reference: f_ref = f_k, theta_ref = theta(f_k), Q_ref = Q_FP64(f_k), ahat_ref = FP32 DFT of f_k - M_k
   cudaError_t e = cudaMemcpyAsync(h->ws + h->off.f_ref, f, sizeof(double) * h->field, cudaMemcpyDeviceToDevice, st);
@@ -948,6 +985,12 @@ int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, int lo_iters, do
   // P from the FP64 collision is P of f_k in the increment form as well (zero increments)
   for (int it = 0; it < lo_iters; it++)
     if ((r = iterate_impl(h, f, Q, P, nullptr, it == 0 ? SGS_IT_P_VALID : 0, nullptr, st))) return r;
+  return SGS_OK;
+}
+
+int sgs_set_dc_precision(sgs_handle* h, int precision) {
+  if (!h || (precision != SGS_FP64 && precision != SGS_DF64)) return SGS_ERR_ARG;
+  h->dc_prec = precision;
   return SGS_OK;
 }
 

@@ -20,10 +20,10 @@ OK, ERR_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE, ERR_NOMEM = 0, -1, -2, -3
 ST_NEWTON_FAIL, ST_INNER_CAP, ST_NONPOSITIVE, ST_NONFINITE, ST_TIMEOUT = 1, 2, 4, 8, 16
 MAXWELL, HARD_SPHERE, BGK = 0, 1, 2
 DIFFUSE, INFLOW = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, DF64 = 0, 1, 2
 PFP, FP = 0, 1
 IT_P_VALID, IT_EVAL = 1, 2
-PROF_NAMES = ("moments", "dft", "sum", "reduce_idft", "sweep", "residual", "rescale", "sum_fp64")
+PROF_NAMES = ("moments", "dft", "sum", "reduce_idft", "sweep", "residual", "rescale", "sum_fp64", "sum_df64")
 PROF_CLASSES = len(PROF_NAMES)
 
 
@@ -145,6 +145,7 @@ def lib(build: bool = True):
             "sgs_iterate": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, vp, vp]),
             "sgs_dc_step": (C.c_int, [vp, vp, vp, vp, C.c_int, vp, vp]),
             "sgs_dc_clear": (C.c_int, [vp]),
+            "sgs_set_dc_precision": (C.c_int, [vp, C.c_int]),
             "sgs_profile": (C.c_int, [vp, C.c_int]),
             "sgs_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_ulonglong), C.c_int]),
             "sgs_launch_count": (C.c_ulonglong, [vp]),
@@ -261,6 +262,9 @@ class Solver:
     def dc_step(self, f, Q, P, lo_iters, res=None, stream=None):
         _check(lib().sgs_dc_step(self.h, _ptr(f), _ptr(Q), _ptr(P), lo_iters, _ptr(res), _stream(stream)),
                "sgs_dc_step")
+
+    def set_dc_precision(self, precision):
+        _check(lib().sgs_set_dc_precision(self.h, precision), "sgs_set_dc_precision")
 
     def dc_clear(self):
         _check(lib().sgs_dc_clear(self.h), "sgs_dc_clear")

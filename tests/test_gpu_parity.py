@@ -244,7 +244,39 @@ def test_sweep_df64_parity(oracle, N, J, eps, direction):
     assert rel(fd.cpu().numpy().reshape(f0.shape), fo) <= 1e-11
 
 
-def test_defect_correction_tracks_fp64_iteration():
+@pytest.mark.parametrize("N,J,L", [(8, 40, 6.0), (16, 16, 6.0), (12, 3, 6.0)])
+def test_collide_df64_parity(oracle, N, J, L):
+    """Double-float spectral sums (pairs of FP32 values on the FP32 pipes) against the FP64
+    oracle: about 2^-48 per term, far inside the FP32 form's 1e-5."""
+    d = spec(nx=J, nv=N, v_max=L, precision=sgs.FP32)
+    f = varied_state(J, N, L, seed=2)
+    s = sgs.Solver(gpu_problem(d))
+    fd = to_dev(f)
+    Q, P = s.field(), s.field()
+    s.collide(fd, Q, P, precision=sgs.DF64)
+    Qo, Po, nuo = oracle.collide(oracle_problem(oracle, d), f)
+    assert rel(Q.cpu().numpy().reshape(f.shape), Qo) <= 1e-11
+    assert rel(P.cpu().numpy().reshape(f.shape), Po) <= 1e-11
+    assert s.read_status()["status"] == 0
+
+
+def test_collide_df64_parity_full_size_sampled(oracle):
+    N, J, L = 32, 64, 8.0
+    d = spec(nx=J, nv=N, v_max=L, eps=0.01, precision=sgs.FP32)
+    f = varied_state(J, N, L, seed=3)
+    s = sgs.Solver(gpu_problem(d))
+    Q, P = s.field(), s.field()
+    s.collide(to_dev(f), Q, P, precision=sgs.DF64)
+    Qd = Q.cpu().numpy().reshape(f.shape)
+    po = oracle_problem(oracle, d)
+    for j in (0, 45):
+        Qo, Po, nuo = oracle.collide(po, f[j:j + 1])
+        assert rel(Qd[j], Qo[0]) <= 1e-11, j
+    assert s.read_status()["status"] == 0
+
+
+@pytest.mark.parametrize("dc_prec", [sgs.DF64, sgs.FP64])
+def test_defect_correction_tracks_fp64_iteration(dc_prec):
     """Mixed solver (FP32 collision sums in increment form + double-float scans + FP64
     defect correction) against the FP64 solver after the same number of SGS iterations from
     the same state: the iterates agree far below the FP32 resolution of the sums."""
@@ -259,6 +291,7 @@ def test_defect_correction_tracks_fp64_iteration():
     for it in range(48):
         s64.iterate(f64, Q, P, flags=sgs.IT_EVAL | (sgs.IT_P_VALID if it else 0), res=res64)
     s32 = sgs.Solver(gpu_problem(dict(d, precision=sgs.FP32)))
+    s32.set_dc_precision(dc_prec)
     fdc = to_dev(f0)
     Q2, P2 = s32.field(), s32.field()
     res = torch.zeros(1, dtype=torch.float64, device="cuda")
