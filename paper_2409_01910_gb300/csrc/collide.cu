@@ -482,7 +482,9 @@ __global__ void __launch_bounds__(KW * 32, 2) k_sum_df(SumDfArgs a) {
     const float4* ra = rows + (2 * b) * n * kLanes;
     const float4* rb = ra + n * kLanes;
     int off = 0;  // first weight of the current m3 in the packed (m3, k3) order
-#pragma unroll
+    // m3 stays a loop (the body, unrolled over the warp's outputs, is long enough to
+    // hide latency; unrolling m3 as well overflows the instruction cache)
+#pragma unroll 1
     for (int m3 = -H; m3 <= H; m3++) {
       const int lo = m3 - H > -H ? m3 - H : -H, hi = m3 + H < H ? m3 + H : H;
       const float4 bv = rb[(m3 + H) * kLanes + lane];

@@ -189,7 +189,13 @@ __device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, bool wv1, c
     if (tid == 0) sm.fn = fnv;
   }
   __syncthreads();
+  // Converged as well once the scaled moment residual |F|/rho is at the arithmetic's
+  // resolution (double-float and FP64 evaluate F to about 1e-14; 1e-13 bounds the relative
+  // error of the Maxwellian near 1e-12 or below): with the residual already
+  // there, a further step could only confirm it.
+  constexpr float ftol = sizeof(E) == 4 ? 0.0f : 1e-13f;
   float fn_cur = sm.fn;
+  if (fn_cur <= ftol) return 0;
   for (int it = 0; it < maxit; it++) {
     if (wid == 0) {
       float y[5], Ff[5];
@@ -238,7 +244,7 @@ __device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, bool wv1, c
       const float step = lam * sm.stepf;
 #pragma unroll
       for (int k = 0; k < 5; k++) th[k] = sm.th_try[k];
-      sm.ctl = !(step == step) ? -1 : (step <= (float)tol ? 1 : 0);
+      sm.ctl = !(step == step) ? -1 : ((step <= (float)tol || fn_cur <= ftol) ? 1 : 0);
     }
     __syncthreads();
     int c = sm.ctl;
@@ -476,7 +482,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           // the last evaluation is M[g]'s: reused as the first one of step 1
           int n1 = newton_cta<E>(sm, N, w, true, sv, sm.thp, L, ntol, I.newton_max, true);
           c_solves++;
-          if (n1 > 0) {
+          if (n1 >= 0) {
             c_newton += n1;
             used = true;
             copy_factors<E>(sm, sm.Ep);
