@@ -10,7 +10,11 @@ mass rescale, collision (the collision sums in FP32, moments/Newton/residual in 
 the FP64 defect-correction evaluation (FP64 collision + FP64 residual + right-hand side)
 every --dc-every steps. One cell update is one cell visit of a scan; a step makes 2 x 64.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload heat|shock]
+
+--workload shock runs the same measurements on the Mach-2 normal shock (128 cells on
+[-20, 20], 32^3 velocities on [-10, 10]^3, hard spheres, eps = 0.1, Rankine-Hugoniot inflow
+data, V-cycles on 128/64/32/16 cells) and records the shock position.
 
 N > 1 runs independent replicas (one per GPU, launched by torchrun): the method is a
 sequential scan per problem, so work is replicated, not sharded ("scaling": "weak").
@@ -44,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--dc-every", type=int, default=10)
+    ap.add_argument("--workload", choices=["heat", "shock"], default="heat",
+                    help="heat: 64-cell heat transfer (default); shock: 128-cell Mach-2 normal shock")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-t2tol", action="store_true", help="skip the time-to-residual runs")
@@ -115,18 +121,42 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- native
+WORKLOAD = "heat"
+
+
 def workload():
     from paper_2409_01910_gb300 import inputs as I
 
+    if WORKLOAD == "shock":
+        return I.shock_128cells_32v()
     return I.heat_64cells_32v(seed=0)
+
+
+def is_shock(wl):
+    return hasattr(wl, "up")
 
 
 def make_solver(wl, precision):
     from paper_2409_01910_gb300 import sgs
 
-    p = sgs.Problem(nx=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, nv=wl.N, v_max=wl.L, eps=wl.eps,
-                    bc_T=(wl.T_left, wl.T_right), total_mass=wl.total_mass, precision=precision)
+    if is_shock(wl):
+        (r1, u1, T1), (r2, u2, T2) = wl.up, wl.down
+        p = sgs.Problem(nx=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, nv=wl.N, v_max=wl.L, collision=sgs.HARD_SPHERE,
+                        eps=wl.eps, bc_kind=(sgs.INFLOW, sgs.INFLOW), bc_rho=(r1, r2),
+                        bc_u=((u1, 0.0, 0.0), (u2, 0.0, 0.0)), bc_T=(T1, T2), total_mass=0.0, precision=precision)
+    else:
+        p = sgs.Problem(nx=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, nv=wl.N, v_max=wl.L, eps=wl.eps,
+                        bc_T=(wl.T_left, wl.T_right), total_mass=wl.total_mass, precision=precision)
     return sgs.Solver(p)
+
+
+def config_of(wl):
+    if is_shock(wl):
+        return {"workload": wl.name, "cells": wl.J, "x": [wl.x_lo, wl.x_hi], "nv": wl.N, "v_max": wl.L,
+                "eps": wl.eps, "collision": "hard spheres", "inflow_up": [round(float(x), 6) for x in wl.up],
+                "inflow_down": [round(float(x), 6) for x in wl.down], "multigrid_levels": 4}
+    return {"workload": wl.name, "cells": wl.J, "nv": wl.N, "v_max": wl.L, "eps": wl.eps,
+            "T_walls": [round(wl.T_left, 6), round(wl.T_right, 6)], "collision": "maxwell"}
 
 
 def pairs_per_cell(N):
@@ -223,8 +253,7 @@ def run_native(args, rank, world, local):
             "vs_baseline": None,
             "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": wl.name, "cells": wl.J, "nv": wl.N, "v_max": wl.L, "eps": wl.eps,
-                       "T_walls": [round(wl.T_left, 6), round(wl.T_right, 6)], "collision": "maxwell",
+            "config": {**config_of(wl),
                        "precision": ("mixed: FP32 direct spectral sums in increment form against the last "
                                      "high-precision evaluation; defect-correction sums in double-float (FP32 "
                                      "pairs); double-float scans with FP64 scalar decisions; FP64 moments, "
@@ -326,6 +355,7 @@ def time_to_tol(wl, f0, dev, kind, cap_s, tol=1e-8):
     from paper_2409_01910_gb300 import sgs
 
     s = make_solver(wl, sgs.FP32 if kind.startswith("mixed") else sgs.FP64)
+    levels = 4 if is_shock(wl) else 2  # shock: 128/64/32/16 cells
     f = f0.clone()
     Q, P = s.field(), s.field()
     res = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -350,13 +380,23 @@ def time_to_tol(wl, f0, dev, kind, cap_s, tol=1e-8):
             break
         if kind == "mixed_mg" or kind == "fp64_mg":
             for _ in range(2 if kind == "mixed_mg" else 1):
-                s.vcycle(f, 2, 1, 1, 4)
+                s.vcycle(f, levels, 1, 1, 4)
                 iters += 1
     sec = time.perf_counter() - t0
     st = s.read_status()
+    out = {"seconds": round(sec, 3), "reached": reached, "residual": r,
+           ("V-cycles" if kind.endswith("mg") else "SGS iterations"): iters, "status": st["status"]}
+    if is_shock(wl):
+        # shock position: where the density crosses the mean of the two inflow densities
+        K = wl.N ** 3
+        rho = (f.view(wl.J, K).sum(1) * (2 * wl.L / wl.N) ** 3).cpu().numpy()
+        mid = 0.5 * (wl.up[0] + wl.down[0])
+        j = int(np.argmax(rho > mid))
+        dx = (wl.x_hi - wl.x_lo) / wl.J
+        if 0 < j < wl.J:
+            out["shock_x"] = round(wl.x_lo + (j - 0.5) * dx + dx * (mid - rho[j - 1]) / (rho[j] - rho[j - 1]), 5)
     s.close()
-    unit = "V-cycles" if kind.endswith("mg") else "SGS iterations"
-    return {"seconds": round(sec, 3), "reached": reached, "residual": r, unit: iters, "status": st["status"]}
+    return out
 
 
 def end_to_end(s, f, Q, P, wl, args, stream):
@@ -430,7 +470,14 @@ def oracle_sample(wl, n_collide_cells=None, n_visits=2):
     O.build()
     cores = os.cpu_count() or 1
     S = n_collide_cells or min(8, cores)
-    prob = O.Problem(N=wl.N, L=wl.L, J=wl.J, eps=wl.eps, bc_T=(wl.T_left, wl.T_right), total_mass=wl.total_mass)
+    if is_shock(wl):
+        (r1, u1, T1), (r2, u2, T2) = wl.up, wl.down
+        prob = O.Problem(N=wl.N, L=wl.L, J=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, eps=wl.eps, kernel=O.HARD_SPHERE,
+                         bc_kind=(O.INFLOW, O.INFLOW), bc_rho=(r1, r2), bc_u=((u1, 0.0, 0.0), (u2, 0.0, 0.0)),
+                         bc_T=(T1, T2), total_mass=0.0)
+    else:
+        prob = O.Problem(N=wl.N, L=wl.L, J=wl.J, eps=wl.eps, bc_T=(wl.T_left, wl.T_right),
+                         total_mass=wl.total_mass)
     f = wl.initial_state()
     O.collide(prob, f[:1])  # builds the weight table (not timed)
     t = time.perf_counter()
@@ -504,7 +551,9 @@ def profile_case(which):
 
 
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = args.workload
     if args.case:
         profile_case(args.case)
         return

@@ -525,18 +525,20 @@ void or_eval_maxwellian(int N, double L, const double* th, double* M) {
 
 /* ------------------------------------------------------------------------------------
  * Collision frequency nu of the BGK penalty (eq. (28)). Maxwell molecules: the loss
- * rate int int B dw f(v_*) dv_* = 4 pi b0 rho. Hard spheres (B = b0 |q|): the loss rate
- * averaged over the local Maxwellian, 4 pi b0 * 4 rho sqrt(T/pi). BGK mode uses the
- * Maxwell value.
+ * rate int int B dw f(v_*) dv_* = 4 pi b0 rho. Hard spheres (B = b0 |q|, truncated at
+ * |q| <= 2R): the supremum of the loss rate, 4 pi b0 rho 2R, so that P keeps no stiff part
+ * of the loss term (the loss rate grows with |v - U|; with its Maxwellian average the
+ * explicitly treated remainder makes SGS diverge on a Mach-2 shock). nu only shapes the
+ * iterates, not the converged solution. BGK mode uses the Maxwell value.
  * ---------------------------------------------------------------------------------- */
 double or_collision_frequency(const or_problem* p, const double* f) {
   double m[5];
   or_moments(p->N, p->L, f, m);
   double rho = m[0];
   if (p->kernel == OR_HARD_SPHERE) {
-    double U2 = (m[1] * m[1] + m[2] * m[2] + m[3] * m[3]) / (rho * rho);
-    double T = (m[4] / rho - U2) / 3.0;
-    return 4.0 * M_PI * p->b0 * 4.0 * rho * sqrt(T / M_PI);
+    /* sup of the loss frequency of the truncated kernel b0 |q|, |q| <= 2R */
+    double R = 2.0 * p->L / (3.0 * sqrt(2.0) + 1.0);
+    return 4.0 * M_PI * p->b0 * rho * 2.0 * R;
   }
   return 4.0 * M_PI * p->b0 * rho;
 }

@@ -66,8 +66,12 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ f, C
     it = maxwellian_newton<double>(N, dv, w, false, 0.0, m, th, newton_tol, newton_max, ev);
   double rho = m[0];
   double T = (m[4] / rho - (m[1] * m[1] + m[2] * m[2] + m[3] * m[3]) / (rho * rho)) / 3.0;
+  // penalty frequency of eq. (28): the loss frequency 4 pi b0 rho for Maxwell molecules;
+  // for hard spheres its supremum over the truncated kernel |q| <= 2R, 4 pi b0 rho 2R with
+  // R = 2L / (3 sqrt 2 + 1) and 2L = N dv, so that no stiff part of the loss term is left
+  // in P (a mean loss frequency lets the explicit remainder grow at large |v|)
   double nuv = 4.0 * kPi * I.b0 * rho;
-  if (I.collision == SGS_HARD_SPHERE) nuv *= 4.0 * sqrt(T / kPi);
+  if (I.collision == SGS_HARD_SPHERE) nuv *= 2.0 * (N * dv) / (3.0 * sqrt(2.0) + 1.0);
   if (lane == 0) {
     for (int q = 0; q < 5; q++) theta[5 * c + q] = th[q];
     nu[c] = nuv;

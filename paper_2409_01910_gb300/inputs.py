@@ -101,3 +101,51 @@ def heat_batch(n: int = 64, seed: int = 0, J_range=(32, 256), N_choices=(24, 32)
         out.append(Workload(f"heat1d_batch{q}_J{J}_N{N}", J=J, N=N, L=L, eps=eps, T_left=TL, T_right=TR,
                             T_init=0.5 * (TL + TR), seed=seed * 1000 + q, tol=1e-8))
     return out
+
+
+def rankine_hugoniot(mach: float = 2.0, rho1: float = 1.0, T1: float = 1.0, gamma: float = 5.0 / 3.0):
+    """Upstream and downstream states (rho, u, T) of a stationary normal shock of a
+    monatomic gas (the Maxwellian exp(-|v-u|^2 / (2T)) has sound speed sqrt(gamma T))."""
+    u1 = mach * np.sqrt(gamma * T1)
+    m2 = mach * mach
+    r = (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    t = (2.0 * gamma * m2 - (gamma - 1.0)) * ((gamma - 1.0) * m2 + 2.0) / ((gamma + 1.0) ** 2 * m2)
+    return (rho1, u1, T1), (rho1 * r, u1 / r, T1 * t)
+
+
+@dataclass
+class ShockWorkload:
+    """1-D stationary normal shock between Rankine-Hugoniot inflow Maxwellians."""
+
+    name: str
+    J: int
+    N: int
+    L: float
+    eps: float
+    up: tuple
+    down: tuple
+    x_lo: float = -20.0
+    x_hi: float = 20.0
+    width: float = 1.0
+    tol: float = 1e-8
+
+    def initial_state(self) -> np.ndarray:
+        """Maxwellians of a tanh profile centred at x = 0: density and temperature blend the
+        two states, the velocity keeps the mass flux rho u of the upstream state."""
+        (r1, u1, T1), (r2, u2, T2) = self.up, self.down
+        dx = (self.x_hi - self.x_lo) / self.J
+        out = np.empty((self.J, self.N, self.N, self.N))
+        for j in range(self.J):
+            x = self.x_lo + (j + 0.5) * dx
+            s = 0.5 * (1.0 + np.tanh(x / self.width))
+            rho = r1 + (r2 - r1) * s
+            T = T1 + (T2 - T1) * s
+            out[j] = sampled_maxwellian(self.N, self.L, rho, (r1 * u1 / rho, 0.0, 0.0), T)
+        return out
+
+
+def shock_128cells_32v(mach: float = 2.0) -> ShockWorkload:
+    """Mach-2 normal shock: 128 cells on [-20, 20], 32^3 velocities on [-10, 10]^3, hard
+    spheres, eps = 0.1, Rankine-Hugoniot inflow data on both sides."""
+    up, down = rankine_hugoniot(mach)
+    return ShockWorkload(f"shock1d_M{mach:g}_J128_N32_eps0.1", J=128, N=32, L=10.0, eps=0.1, up=up, down=down)
