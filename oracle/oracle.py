@@ -20,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
 SRC = os.path.join(HERE, "sgs_oracle.c")
+SRC2D = os.path.join(HERE, "sgs_oracle2d.c")
 
 MAXWELL, HARD_SPHERE, BGK = 0, 1, 2
 DIFFUSE, INFLOW = 0, 1
@@ -30,11 +31,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle (plain C17, -O2, OpenMP over cells in the collision step)."""
     os.makedirs(BUILD, exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "sgs_oracle.h"))
+        os.path.getmtime(SRC), os.path.getmtime(SRC2D), os.path.getmtime(os.path.join(HERE, "sgs_oracle.h"))
     ):
         tmp = LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-std=c17", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
+            ["gcc", "-std=c17", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, SRC, SRC2D, "-lm"]
         )
         os.replace(tmp, LIB)
     return LIB
@@ -120,6 +121,54 @@ class Problem:
         return p
 
 
+class _Problem2D(C.Structure):
+    _fields_ = [
+        ("p", _Problem),
+        ("ny", C.c_int),
+        ("y_lo", C.c_double),
+        ("y_hi", C.c_double),
+        ("bc_kind_y", C.c_int * 2),
+        ("bc_rho_y", C.c_double * 2),
+        ("bc_u_y", (C.c_double * 3) * 2),
+        ("bc_T_y", C.c_double * 2),
+    ]
+
+
+@dataclass
+class Problem2D:
+    """A 2-D-space problem: nx = base.J cells on [base.x_lo, base.x_hi] with the x sides of
+    base, ny cells on [y_lo, y_hi] with the y sides given here."""
+
+    base: Problem
+    ny: int = 16
+    y_lo: float = 0.0
+    y_hi: float = 1.0
+    bc_kind_y: tuple = (DIFFUSE, DIFFUSE)
+    bc_rho_y: tuple = (1.0, 1.0)
+    bc_u_y: tuple = ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0))
+    bc_T_y: tuple = (1.0, 1.0)
+
+    @property
+    def nx(self) -> int:
+        return self.base.J
+
+    @property
+    def cells(self) -> int:
+        return self.base.J * self.ny
+
+    def c(self) -> _Problem2D:
+        q = _Problem2D()
+        q.p = self.base.c()
+        q.ny, q.y_lo, q.y_hi = self.ny, self.y_lo, self.y_hi
+        for s in range(2):
+            q.bc_kind_y[s] = self.bc_kind_y[s]
+            q.bc_rho_y[s] = self.bc_rho_y[s]
+            q.bc_T_y[s] = self.bc_T_y[s]
+            for d in range(3):
+                q.bc_u_y[s][d] = self.bc_u_y[s][d]
+        return q
+
+
 _lib = None
 
 
@@ -129,6 +178,7 @@ def lib():
         _lib = C.CDLL(build())
         d = C.POINTER(C.c_double)
         P = C.POINTER(_Problem)
+        P2 = C.POINTER(_Problem2D)
         S = C.POINTER(_Stats)
         sig = {
             "or_velocity_nodes": (None, [C.c_int, C.c_double, d]),
@@ -152,6 +202,13 @@ def lib():
             "or_residual": (C.c_double, [P, C.c_int, C.c_double, d, d, d, d]),
             "or_sgs_iteration": (None, [P, C.c_int, C.c_double, d, d, C.c_int, S]),
             "or_vcycle": (None, [P, d, C.c_int, C.c_int, C.c_int, C.c_int, S]),
+            "or_cell_solve_c": (C.c_int, [P, d, d, C.c_double, d, S]),
+            "or_ghost2d": (None, [P2, C.c_int, d, d]),
+            "or_sweep2d": (None, [P2, C.c_int, d, d, d, d, S]),
+            "or_rescale2d": (None, [P2, d]),
+            "or_residual2d": (C.c_double, [P2, d, d, d, d]),
+            "or_sgs_iteration2d": (None, [P2, d, d, C.c_int, S]),
+            "or_vcycle2d": (None, [P2, d, C.c_int, C.c_int, C.c_int, C.c_int, S]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -329,3 +386,56 @@ def solve_residual(prob: Problem, f):
     """Residual of f after a fresh collision evaluation (no rescale)."""
     Q, _, _ = collide(prob, f)
     return residual(prob, f, Q)
+
+
+# ------------------------------------------------------------------------------ 2-D space
+def collide2d(prob: Problem2D, f):
+    """Collision step of every cell (cells are independent): (Q, P, nu)."""
+    return collide(prob.base, f)
+
+
+def ghost2d(prob: Problem2D, side, f_adj):
+    q = prob.c()
+    g = np.empty_like(_arr(f_adj))
+    lib().or_ghost2d(C.byref(q), side, _p(_arr(f_adj)), _p(g))
+    return g
+
+
+def sweep2d(prob: Problem2D, f, P, nu, ordering, b=None):
+    q = prob.c()
+    st = _Stats()
+    lib().or_sweep2d(C.byref(q), ordering, _p(f), _p(_arr(P)), _p(_arr(nu)), _p(None if b is None else _arr(b)),
+                     C.byref(st))
+    return st.as_dict()
+
+
+def rescale2d(prob: Problem2D, f):
+    q = prob.c()
+    lib().or_rescale2d(C.byref(q), _p(f))
+
+
+def residual2d(prob: Problem2D, f, Q, b=None, return_field=False):
+    q = prob.c()
+    R = np.empty_like(_arr(f)) if return_field else None
+    res = lib().or_residual2d(C.byref(q), _p(_arr(f)), _p(_arr(Q)), _p(None if b is None else _arr(b)), _p(R))
+    return (res, R) if return_field else res
+
+
+def sgs_iteration2d(prob: Problem2D, f, b=None, rescale=True):
+    q = prob.c()
+    st = _Stats()
+    lib().or_sgs_iteration2d(C.byref(q), _p(f), _p(None if b is None else _arr(b)), 1 if rescale else 0,
+                             C.byref(st))
+    return st.as_dict()
+
+
+def vcycle2d(prob: Problem2D, f, levels, pre=1, post=1, coarse_iters=10):
+    q = prob.c()
+    st = _Stats()
+    lib().or_vcycle2d(C.byref(q), _p(f), levels, pre, post, coarse_iters, C.byref(st))
+    return st.as_dict()
+
+
+def solve_residual2d(prob: Problem2D, f):
+    Q, _, _ = collide2d(prob, f)
+    return residual2d(prob, f, Q)

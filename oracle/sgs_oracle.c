@@ -607,14 +607,30 @@ void or_collide(const or_problem* p, int J, const double* f, double* Q, double* 
 int or_cell_solve(const or_problem* p, double dx, const double* r, double nu, double* g, or_stats* st) {
   int N = p->N;
   long K = (long)N * N * N;
+  double* v = (double*)malloc(sizeof(double) * N);
+  double* c = (double*)malloc(sizeof(double) * K);
+  or_velocity_nodes(N, p->L, v);
+  for (int i1 = 0; i1 < N; i1++)
+    for (long t = 0; t < (long)N * N; t++) c[(long)i1 * N * N + t] = fabs(v[i1]) / dx;
+  int it = or_cell_solve_c(p, c, r, nu, g, st);
+  free(v);
+  free(c);
+  return it;
+}
+
+/* The cell equation with a general transport weight c_k >= 0 per node (|v1|/dx in 1-D,
+ * |v1|/dx + |v2|/dy in 2-D): c g + r = (nu/eps)(M[g] - g). Step 1 of PFP (eq. (24)) uses
+ * the weights w c_k. */
+int or_cell_solve_c(const or_problem* p, const double* c, const double* r, double nu, double* g, or_stats* st) {
+  int N = p->N;
+  long K = (long)N * N * N;
   double L = p->L, w = weight(N, L), eps = p->eps;
   double* v = (double*)malloc(sizeof(double) * N);
   double* wk = (double*)malloc(sizeof(double) * K);
   double* Mg = (double*)malloc(sizeof(double) * K);
   double* Mp = (double*)malloc(sizeof(double) * K);
   or_velocity_nodes(N, L, v);
-  for (int i1 = 0; i1 < N; i1++)
-    for (long t = 0; t < (long)N * N; t++) wk[(long)i1 * N * N + t] = w * fabs(v[i1]) / dx;
+  for (long i = 0; i < K; i++) wk[i] = w * c[i];
   double a = nu / eps;
   int it;
   for (it = 0;; it++) {
@@ -634,7 +650,7 @@ int or_cell_solve(const or_problem* p, double dx, const double* r, double nu, do
       for (int i1 = 0; i1 < N; i1++)
         for (long t = 0; t < (long)N * N; t++) {
           long i = (long)i1 * N * N + t;
-          double e = fabs(v[i1]) / dx * g[i] + r[i] - a * (Mg[i] - g[i]);
+          double e = c[i] * g[i] + r[i] - a * (Mg[i] - g[i]);
           res += w * e * e;
         }
       if (sqrt(res) < p->inner_tol) break;
@@ -648,7 +664,7 @@ int or_cell_solve(const or_problem* p, double dx, const double* r, double nu, do
         for (int i2 = 0; i2 < N; i2++)
           for (int i3 = 0; i3 < N; i3++) {
             long i = ((long)i1 * N + i2) * N + i3;
-            double e = w * (fabs(v[i1]) / dx * (Mg[i] - g[i]) - r[i]);
+            double e = w * (c[i] * (Mg[i] - g[i]) - r[i]);
             double vv = v[i1] * v[i1] + v[i2] * v[i2] + v[i3] * v[i3];
             s[0] += e;
             s[1] += e * v[i1];
@@ -679,7 +695,7 @@ int or_cell_solve(const or_problem* p, double dx, const double* r, double nu, do
     for (int i1 = 0; i1 < N; i1++)
       for (long t = 0; t < (long)N * N; t++) {
         long i = (long)i1 * N * N + t;
-        g[i] = (a * Mplus[i] - r[i]) / (fabs(v[i1]) / dx + a);
+        g[i] = (a * Mplus[i] - r[i]) / (c[i] + a);
       }
   }
   if (st) {

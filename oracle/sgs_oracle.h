@@ -75,6 +75,8 @@ void or_collide_cell(const or_problem* p, const double* f, double* Q, double* P,
 void or_collide(const or_problem* p, int J, const double* f, double* Q, double* P, double* nu);
 /* Cell equation (|v1|/dx) g + r = (nu/eps)(M[g] - g), solved by PFP or FP. */
 int or_cell_solve(const or_problem* p, double dx, const double* r, double nu, double* g, or_stats* st);
+/* The same with a per-node transport weight c (|v1|/dx in 1-D, |v1|/dx + |v2|/dy in 2-D). */
+int or_cell_solve_c(const or_problem* p, const double* c, const double* r, double nu, double* g, or_stats* st);
 /* Ghost density of a diffuse wall from the zero-mass-flux condition. */
 double or_wall_density(const or_problem* p, int side, const double* f_adj);
 void or_ghost(const or_problem* p, int side, const double* f_adj, double* ghost);
@@ -90,6 +92,33 @@ void or_sgs_iteration(const or_problem* p, int J, double dx, double* f, const do
                       or_stats* st);
 /* One FAS V-cycle on the finest level (J cells). */
 void or_vcycle(const or_problem* p, double* f, int levels, int pre, int post, int coarse_iters, or_stats* st);
+
+/* ------------------------------------------------------------------------------------
+ * 2-D space (sgs_oracle2d.c). The 1-D problem p describes the velocity grid, kernel, eps,
+ * tolerances, the x extent (J = nx cells on [x_lo, x_hi]) and the x_lo / x_hi sides;
+ * the y extent and the y_lo / y_hi sides are added here. Cell (i, j) at index j nx + i.
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+  or_problem p;
+  int ny;
+  double y_lo, y_hi;
+  int bc_kind_y[2]; /* y_lo, y_hi */
+  double bc_rho_y[2], bc_u_y[2][3], bc_T_y[2];
+} or_problem2d;
+
+double or_dx2d(const or_problem2d* q);
+double or_dy2d(const or_problem2d* q);
+/* Ghost of side s (0 x_lo, 1 x_hi, 2 y_lo, 3 y_hi) next to the cell f_adj. */
+void or_ghost2d(const or_problem2d* q, int s, const double* f_adj, double* ghost);
+/* One sweep in ordering o: 0 SW->NE, 1 NE->SW, 2 NW->SE, 3 SE->NW. */
+void or_sweep2d(const or_problem2d* q, int o, double* f, const double* P, const double* nu, const double* b,
+                or_stats* st);
+void or_rescale2d(const or_problem2d* q, double* f);
+double or_residual2d(const or_problem2d* q, const double* f, const double* Q, const double* b, double* Rout);
+/* Four sweeps, each after a collision evaluation, then the rescale. */
+void or_sgs_iteration2d(const or_problem2d* q, double* f, const double* b, int rescale, or_stats* st);
+/* FAS V-cycle with 2 x 2 coarsening (nx, ny divisible by 2^(levels-1)). */
+void or_vcycle2d(const or_problem2d* q, double* f, int levels, int pre, int post, int coarse_iters, or_stats* st);
 
 #ifdef __cplusplus
 }
