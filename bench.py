@@ -12,6 +12,9 @@ every --dc-every steps. One cell update is one cell visit of a scan; a step make
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload heat|shock]
 
+--workload cavity runs them on the 2-D lid-driven cavity (64 x 64 cells on [0, 1]^2, 24^3
+velocities on [-6, 6]^3, Maxwell molecules, eps = 0.05, lid speed 0.5, walls at T = 1,
+four orderings per SGS iteration, V-cycles on 64^2/32^2/16^2 cells).
 --workload shock runs the same measurements on the Mach-2 normal shock (128 cells on
 [-20, 20], 32^3 velocities on [-10, 10]^3, hard spheres, eps = 0.1, Rankine-Hugoniot inflow
 data, V-cycles on 128/64/32/16 cells) and records the shock position.
@@ -48,8 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--dc-every", type=int, default=10)
-    ap.add_argument("--workload", choices=["heat", "shock"], default="heat",
-                    help="heat: 64-cell heat transfer (default); shock: 128-cell Mach-2 normal shock")
+    ap.add_argument("--workload", choices=["heat", "shock", "cavity"], default="heat",
+                    help="heat: 64-cell heat transfer (default); shock: 128-cell Mach-2 normal shock; "
+                         "cavity: 64 x 64 lid-driven cavity (2-D space)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-t2tol", action="store_true", help="skip the time-to-residual runs")
@@ -129,6 +133,8 @@ def workload():
 
     if WORKLOAD == "shock":
         return I.shock_128cells_32v()
+    if WORKLOAD == "cavity":
+        return I.cavity_64x64_24v()
     return I.heat_64cells_32v(seed=0)
 
 
@@ -136,10 +142,23 @@ def is_shock(wl):
     return hasattr(wl, "up")
 
 
+def is_cavity(wl):
+    return hasattr(wl, "ny")
+
+
+def visits_per_iteration(wl):
+    """Cell visits of one SGS iteration: two scans in 1-D, four orderings in 2-D."""
+    return (4 if is_cavity(wl) else 2) * wl.J
+
+
 def make_solver(wl, precision):
     from paper_2409_01910_gb300 import sgs
 
-    if is_shock(wl):
+    if is_cavity(wl):
+        p = sgs.Problem(space_dim=2, nx=wl.nx, ny=wl.ny, nv=wl.N, v_max=wl.L, eps=wl.eps,
+                        bc_T=(wl.T_wall, wl.T_wall), bc_T_y=(wl.T_wall, wl.T_wall),
+                        bc_u_y=((0.0, 0.0, 0.0), (wl.lid, 0.0, 0.0)), total_mass=wl.total_mass, precision=precision)
+    elif is_shock(wl):
         (r1, u1, T1), (r2, u2, T2) = wl.up, wl.down
         p = sgs.Problem(nx=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, nv=wl.N, v_max=wl.L, collision=sgs.HARD_SPHERE,
                         eps=wl.eps, bc_kind=(sgs.INFLOW, sgs.INFLOW), bc_rho=(r1, r2),
@@ -151,6 +170,10 @@ def make_solver(wl, precision):
 
 
 def config_of(wl):
+    if is_cavity(wl):
+        return {"workload": wl.name, "cells": [wl.nx, wl.ny], "domain": [[0.0, 1.0], [0.0, 1.0]], "nv": wl.N,
+                "v_max": wl.L, "eps": wl.eps, "collision": "maxwell", "lid_speed": wl.lid, "T_walls": wl.T_wall,
+                "orderings": 4, "multigrid_levels": 3}
     if is_shock(wl):
         return {"workload": wl.name, "cells": wl.J, "x": [wl.x_lo, wl.x_hi], "nv": wl.N, "v_max": wl.L,
                 "eps": wl.eps, "collision": "hard spheres", "inflow_up": [round(float(x), 6) for x in wl.up],
@@ -179,7 +202,7 @@ def run_native(args, rank, world, local):
     Q, P = s.field(), s.field()
     res_hi = torch.zeros(1, dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    visits_per_step = 2 * wl.J
+    visits_per_step = visits_per_iteration(wl)
 
     def step(i):
         if i % args.dc_every == 0:
@@ -332,7 +355,9 @@ def roofline(cls, prof, wl, sm_mhz):
                 "achieved": ach, "peak": peak, "unit": "T FP32-pipe op/s", "frac": ach / peak, "traffic": None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 1 op x {sm_mhz:.0f} MHz (median sampled)"}
     if cls == "sweep":
-        byts = 5 * K * 8 * wl.J  # read f_{j-1}, f_j, f_{j+1}, P_j; write f_j per visit
+        # per visit: read the upwind/downwind neighbours, f_j and P_j, write f_j (1-D: 5 K
+        # doubles; 2-D: 7 K doubles); one profiled group = one scan over every cell
+        byts = (7 if is_cavity(wl) else 5) * K * 8 * wl.J
         ach = byts / (avg * 1e-3) / 1e9
         return {"kernel": "k_sweep<dfloat,8> (persistent SGS scan, one cluster of 16 CTAs)", "bound": "hbm",
                 "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
@@ -355,7 +380,7 @@ def time_to_tol(wl, f0, dev, kind, cap_s, tol=1e-8):
     from paper_2409_01910_gb300 import sgs
 
     s = make_solver(wl, sgs.FP32 if kind.startswith("mixed") else sgs.FP64)
-    levels = 4 if is_shock(wl) else 2  # shock: 128/64/32/16 cells
+    levels = 4 if is_shock(wl) else (3 if is_cavity(wl) else 2)  # shock 128/64/32/16; cavity 64^2/32^2/16^2
     f = f0.clone()
     Q, P = s.field(), s.field()
     res = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -400,6 +425,10 @@ def time_to_tol(wl, f0, dev, kind, cap_s, tol=1e-8):
 
 
 def end_to_end(s, f, Q, P, wl, args, stream):
+    """The timed step through the public API with host buffers: every step copies the state
+    (f, P) from pinned host memory, runs the same work as a timed step (the defect-correction
+    evaluation every --dc-every steps, one SGS iteration with its residual) and reads the
+    residual back."""
     import torch
 
     from paper_2409_01910_gb300 import sgs
@@ -408,29 +437,33 @@ def end_to_end(s, f, Q, P, wl, args, stream):
     hP = P.cpu().pin_memory()
     hres = torch.zeros(1, dtype=torch.float64).pin_memory()
     res = torch.zeros(1, dtype=torch.float64, device=f.device)
-    steps = max(3, args.steps // 2)
-    for _ in range(2):
+
+    def step(i):
         f.copy_(hf, non_blocking=True)
         P.copy_(hP, non_blocking=True)
+        if i % args.dc_every == 0:
+            s.dc_step(f, Q, P, 0, res=res)
         s.iterate(f, Q, P, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
         hres.copy_(res, non_blocking=True)
+
+    for i in range(2):
+        step(i + 1)
         torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     total = 0.0
-    for _ in range(steps):
+    steps = args.steps
+    for i in range(steps):
         t0.record(stream)
-        f.copy_(hf, non_blocking=True)
-        P.copy_(hP, non_blocking=True)
-        s.iterate(f, Q, P, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
-        hres.copy_(res, non_blocking=True)
+        step(i)
         t1.record(stream)
         t1.synchronize()
         total += t0.elapsed_time(t1)
     ms = total / steps
-    return {"value": 2 * wl.J / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 2 * hf.numel() * 8,
+    return {"value": visits_per_iteration(wl) / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 2 * hf.numel() * 8,
             "d2h_bytes_per_step": 8, "ms_per_step": ms,
-            "note": "state (f, P) copied from pinned host memory and the residual read back every step"}
+            "note": ("state (f, P) copied from pinned host memory and the residual read back every step; "
+                     "same work per step as the timed region")}
 
 
 def fp64_form(wl, args, f0, dev, stream):
@@ -456,7 +489,7 @@ def fp64_form(wl, args, f0, dev, stream):
     ms = t0.elapsed_time(t1) / args.fp64_steps
     prof = s.profile_read()
     s.close()
-    return {"value": 2 * wl.J / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": args.fp64_steps,
+    return {"value": visits_per_iteration(wl) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": args.fp64_steps,
             "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()}}
 
 
@@ -470,7 +503,11 @@ def oracle_sample(wl, n_collide_cells=None, n_visits=2):
     O.build()
     cores = os.cpu_count() or 1
     S = n_collide_cells or min(8, cores)
-    if is_shock(wl):
+    if is_cavity(wl):
+        # the cell solve of a 2-D visit costs what a 1-D one costs on the same velocity grid
+        prob = O.Problem(N=wl.N, L=wl.L, J=wl.nx, eps=wl.eps, bc_T=(wl.T_wall, wl.T_wall),
+                         total_mass=wl.total_mass)
+    elif is_shock(wl):
         (r1, u1, T1), (r2, u2, T2) = wl.up, wl.down
         prob = O.Problem(N=wl.N, L=wl.L, J=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, eps=wl.eps, kernel=O.HARD_SPHERE,
                          bc_kind=(O.INFLOW, O.INFLOW), bc_rho=(r1, r2), bc_u=((u1, 0.0, 0.0), (u2, 0.0, 0.0)),
@@ -485,6 +522,7 @@ def oracle_sample(wl, n_collide_cells=None, n_visits=2):
     t_coll = (time.perf_counter() - t) / S
     dx = prob.dx
     V = (np.arange(wl.N) - wl.N // 2 + 1) * (2 * wl.L / wl.N)
+    f = f[: max(S, n_visits + 2)]
     vp = np.maximum(V, 0)[:, None, None]
     vm = np.minimum(V, 0)[:, None, None]
     t = time.perf_counter()
@@ -517,7 +555,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "cells": wl.J, "nv": wl.N, "eps": wl.eps},
+            "config": config_of(wl),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "per step: collision step of min(8, cores) cells + 1 cell visit, FP64 C oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -66,17 +66,22 @@ typedef struct {
   double T;
 } sgs_bc;
 
-/* One steady problem instance (1-D space, 3-D velocity). */
+/* One steady problem instance (1-D or 2-D space, 3-D velocity). In 2-D the cells form an
+ * nx x ny grid stored row by row (cell (i, j) at j nx + i, i along x); one SGS iteration is
+ * the four corner-to-corner orderings, and a handle holds one 2-D instance. */
 typedef struct {
-  int space_dim;      /* must be 1 */
-  int nx;             /* cells, >= 1 */
-  double x_lo, x_hi;  /* domain */
+  int space_dim;      /* 1 or 2 */
+  int nx;             /* cells along x, >= 1 */
+  double x_lo, x_hi;  /* domain along x */
+  int ny;             /* cells along y (2-D; ignored in 1-D) */
+  double y_lo, y_hi;  /* domain along y (2-D) */
   int nv;             /* N: velocity points per dimension, one of 8, 12, 16, 20, 24, 28, 32 */
   double v_max;       /* L; the support radius is R = 2L / (3 sqrt 2 + 1) (Section 4.2) */
   int collision;      /* SGS_MAXWELL (B = b0), SGS_HARD_SPHERE (B = b0 |q|), SGS_BGK (P = 0) */
   double b0;          /* kernel constant; 1/(4 pi) gives nu = rho for Maxwell molecules */
   double eps;         /* Knudsen number, > 0 */
-  sgs_bc bc[2];       /* bc[0] at x_lo, bc[1] at x_hi */
+  sgs_bc bc[4];       /* x_lo, x_hi, y_lo, y_hi (the y sides in 2-D only); diffuse walls move
+                         tangentially (u[0] = 0 on x walls, u[1] = 0 on y walls) */
   double total_mass;  /* C of eq. (32); <= 0 disables the rescale */
   int precision;      /* arithmetic of the collision sum: SGS_FP64 or SGS_FP32 */
   double inner_tol;   /* cell-equation residual tolerance (discrete L2 norm), e.g. 1e-8 */
@@ -126,6 +131,12 @@ int sgs_collide(sgs_handle* h, const double* f, double* Q, double* P, void* stre
  * nullable) is the b of R(f) = b (multigrid / defect correction). */
 int sgs_sweep_forward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream);
 int sgs_sweep_backward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream);
+/* One scan in a given ordering. 1-D: 0 forward, 1 backward. 2-D (eq. (29) in each
+ * direction): 0 SW->NE, 1 NE->SW, 2 NW->SE, 3 SE->NW; the cells of one anti-diagonal
+ * wavefront are independent and visited concurrently (one cluster per cell), wavefront
+ * after wavefront, which equals the row-by-row Gauss-Seidel order of that ordering.
+ * sgs_sweep_forward / sgs_sweep_backward are orderings 0 / 1. */
+int sgs_sweep_ordering(sgs_handle* h, double* f, const double* P, const double* rhs, int ordering, void* stream);
 
 /* Uniform rescale of each instance to its total mass (eq. (32)); no-op where <= 0. */
 int sgs_rescale(sgs_handle* h, double* f, void* stream);
@@ -148,7 +159,7 @@ int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* 
  * stream capture. All calls share the array: calls that overlap on the GPU race, so order
  * them on one stream. Every slot a call reads is written earlier in the same call. */
 int sgs_residual_noalloc(const sgs_problem* p, const double* f, const double* Q, const double* rhs, double* res,
-                         void* stream);
+                         void* stream);  /* 1-D problems only (SGS_ERR_ARG otherwise) */
 
 /* Collision step in a chosen arithmetic (SGS_FP32 and SGS_DF64 need a handle set up with
  * precision SGS_FP32, whose workspace then carries the FP64 and FP32 weight tables and the
@@ -156,7 +167,8 @@ int sgs_residual_noalloc(const sgs_problem* p, const double* f, const double* Q,
 int sgs_collide_prec(sgs_handle* h, const double* f, double* Q, double* P, int precision, void* stream);
 
 /* One full SGS iteration (eq. (29)): [collide], forward scan, collide, backward scan,
- * rescale. Q and P are caller-owned device fields.
+ * rescale; in 2-D: [collide], ordering 0, then collide + ordering 1, 2, 3, rescale (cell
+ * measure dx dy). Q and P are caller-owned device fields.
  *   flags & SGS_IT_P_VALID: P already holds P[f] of the incoming f (skips the first collide).
  *   flags & SGS_IT_EVAL:    afterwards Q, P hold Q[f], P[f] of the new f and, when res
  *                           (device, n_inst doubles) is not NULL, res the outer residual.
@@ -228,7 +240,7 @@ int sgs_read_active(sgs_handle* h, int* active, void* stream);
 
 /* Launch shape of the persistent scan: nodes per thread (ept, a divisor of nv with a
  * compiled kernel: 2, 4, 8, 12, ..., 32), CTAs per cluster (a power of two <= 16; one
- * cluster walks one instance) and threads per CTA (a multiple of 32 in [128, 256]) with
+ * cluster walks one instance) and threads per CTA (a multiple of 32 in [160, 256]) with
  * ept * cluster * threads >= nv^3. sgs_set_sweep_shape returns SGS_ERR_ARG for an invalid
  * shape and SGS_ERR_UNSUPPORTED for one that cannot be resident on the device. */
 int sgs_get_sweep_shape(const sgs_handle* h, int* ept, int* cluster, int* threads);

@@ -76,13 +76,88 @@ __global__ void k_residual_final(const InstDev* inst, int n_inst, const double* 
   const InstDev& I = inst[q];
   double s = 0.0;
   for (int j = 0; j < I.J; j++) s += part[I.cell0 + j];
-  res[q] = sqrt(I.dx * s);
+  res[q] = sqrt(I.dx * I.dy * s);
+}
+
+// ---------------------------------------------------------------------------------------
+// 2-D residual (one instance, nx x ny cells, row by row): face index of the boundary faces
+// x_lo: j, x_hi: ny + j, y_lo: 2 ny + i, y_hi: 2 ny + nx + i. flux = w sum of (v.n) f over the
+// velocities leaving the domain through the face.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_wall_flux2d(AuxArgs a, const double* __restrict__ f, double* flux) {
+  __shared__ double sh[32];
+  const InstDev& I = a.inst[0];
+  const int nx = a.nx, ny = a.ny, N = a.N, K = N * N * N;
+  int face = blockIdx.x, side, cell;
+  if (face < ny) {
+    side = 0;
+    cell = face * nx;
+  } else if (face < 2 * ny) {
+    side = 1;
+    cell = (face - ny) * nx + nx - 1;
+  } else if (face < 2 * ny + nx) {
+    side = 2;
+    cell = face - 2 * ny;
+  } else {
+    side = 3;
+    cell = (ny - 1) * nx + (face - 2 * ny - nx);
+  }
+  const double* fc = f + I.f_off + (long long)cell * K;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    double vn = node(side < 2 ? e / (N * N) : (e / N) % N, N, a.dv);
+    bool out = side % 2 == 0 ? vn < 0.0 : vn > 0.0;
+    if (out) acc += vn * fc[e];
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) flux[face] = a.dv * a.dv * a.dv * t;
+}
+
+__global__ void __launch_bounds__(256) k_residual_cells2d(AuxArgs a, const double* __restrict__ f,
+                                                           const double* __restrict__ Q,
+                                                           const double* __restrict__ rhs, const double* flux,
+                                                           double* part, double* Rout) {
+  __shared__ double sh[32];
+  const InstDev& I = a.inst[0];
+  const int nx = a.nx, ny = a.ny, N = a.N, K = N * N * N;
+  const int c = blockIdx.x, ci = c % nx, cj = c / nx;
+  const long long base = I.f_off + (long long)c * K;
+  const double w = a.dv * a.dv * a.dv, inv_dx = 1.0 / I.dx, inv_dy = 1.0 / I.dy, inv_eps = 1.0 / I.eps;
+  double rw[4];
+  const int fidx[4] = {cj, ny + cj, 2 * ny + ci, 2 * ny + nx + ci};
+  for (int s = 0; s < 4; s++) rw[s] = I.bc_kind[s] == SGS_INFLOW ? I.bc_rho[s] : -flux[fidx[s]] / I.wall_denom[s];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    int i1 = e / (N * N), i2 = (e / N) % N, i3 = e % N;
+    double v1 = node(i1, N, a.dv), v2 = node(i2, N, a.dv);
+    double fc = f[base + e];
+    double gh[4];
+    for (int s = 0; s < 4; s++) gh[s] = rw[s] * I.wall[s][0][i1] * I.wall[s][1][i2] * I.wall[s][2][i3];
+    double fw = ci == 0 ? gh[0] : f[base - K + e];
+    double fe = ci == nx - 1 ? gh[1] : f[base + K + e];
+    double fs = cj == 0 ? gh[2] : f[base - (long long)nx * K + e];
+    double fn = cj == ny - 1 ? gh[3] : f[base + (long long)nx * K + e];
+    double R = (fmax(v1, 0.0) * (fc - fw) + fmin(v1, 0.0) * (fe - fc)) * inv_dx +
+               (fmax(v2, 0.0) * (fc - fs) + fmin(v2, 0.0) * (fn - fc)) * inv_dy - Q[base + e] * inv_eps;
+    if (rhs) R -= rhs[base + e];
+    if (Rout) Rout[base + e] = R;
+    acc += R * R;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[c] = w * t;
 }
 
 cudaError_t launch_residual_impl(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
                                  double* R, cudaStream_t st) {
   double* flux = a.scratch;                  // [2 n_inst]
   double* part = a.scratch + 2 * a.n_inst;   // [C]
+  if (a.two_d) {
+    double* flux2 = a.scratch + 2 * a.n_inst + 2 * a.C;  // [2 (nx + ny)], after the mass slots
+    k_wall_flux2d<<<2 * (a.nx + a.ny), 256, 0, st>>>(a, f, flux2);
+    k_residual_cells2d<<<a.C, 256, 0, st>>>(a, f, Q, rhs, flux2, part, R);
+    if (res) k_residual_final<<<1, 32, 0, st>>>(a.inst, 1, part, res);
+    return cudaGetLastError();
+  }
   k_wall_flux<<<2 * a.n_inst, 256, 0, st>>>(a.inst, f, a.N, a.dv, flux);
   k_residual_cells<<<a.C, 256, 0, st>>>(a, f, Q, rhs, flux, part, R);
   if (res) k_residual_final<<<(a.n_inst + 127) / 128, 128, 0, st>>>(a.inst, a.n_inst, part, res);
@@ -122,7 +197,7 @@ __global__ void __launch_bounds__(256) k_rescale_apply(AuxArgs a, double* f, con
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int j = 0; j < I.J; j++) s += mass[I.cell0 + j];
-    lam_s = I.total_mass / (I.dx * s);
+    lam_s = I.total_mass / (I.dx * I.dy * s);
   }
   __syncthreads();
   double lam = lam_s;
@@ -176,6 +251,35 @@ __global__ void k_prolong_add(double* __restrict__ fine, const double* __restric
   }
 }
 
+__global__ void k_restrict2d(const double* __restrict__ fine, double* __restrict__ coarse, long long K, int nx,
+                             long long n) {
+  const int cx = nx / 2;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i < n; i += (long long)gridDim.x * blockDim.x) {
+    long long c = i / K, k = i % K;
+    long long ic = c % cx, jc = c / cx;
+    long long f00 = (2 * jc) * nx + 2 * ic;
+    coarse[i] = 0.25 * (fine[f00 * K + k] + fine[(f00 + 1) * K + k] + fine[(f00 + nx) * K + k] +
+                        fine[(f00 + nx + 1) * K + k]);
+  }
+}
+
+__global__ void k_prolong_add2d(double* __restrict__ fine, const double* __restrict__ fc,
+                                const double* __restrict__ fc0, long long K, int nx, long long n) {
+  const int cx = nx / 2;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i < n; i += (long long)gridDim.x * blockDim.x) {
+    long long c = i / K, k = i % K;
+    long long ic = c % cx, jc = c / cx;
+    long long f00 = (2 * jc) * nx + 2 * ic;
+    double d = fc[i] - fc0[i];
+    fine[f00 * K + k] += d;
+    fine[(f00 + 1) * K + k] += d;
+    fine[(f00 + nx) * K + k] += d;
+    fine[(f00 + nx + 1) * K + k] += d;
+  }
+}
+
 __global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   for (; i < n; i += (long long)gridDim.x * blockDim.x) y[i] = a * y[i] + b * x[i];
@@ -195,6 +299,19 @@ cudaError_t launch_restrict(const double* fine, double* coarse, long long K, int
 cudaError_t launch_prolong_add(double* fine, const double* fc, const double* fc0, long long K, int Jc, cudaStream_t st) {
   long long n = K * Jc;
   k_prolong_add<<<blocks_for(n), 256, 0, st>>>(fine, fc, fc0, K, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict2d(const double* fine, double* coarse, long long K, int nx, int ny, cudaStream_t st) {
+  long long n = K * (nx / 2) * (ny / 2);
+  k_restrict2d<<<blocks_for(n), 256, 0, st>>>(fine, coarse, K, nx, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add2d(double* fine, const double* fc, const double* fc0, long long K, int nx, int ny,
+                                 cudaStream_t st) {
+  long long n = K * (nx / 2) * (ny / 2);
+  k_prolong_add2d<<<blocks_for(n), 256, 0, st>>>(fine, fc, fc0, K, nx, n);
   return cudaGetLastError();
 }
 

@@ -20,21 +20,24 @@ constexpr double kPi = 3.14159265358979323846;
 // ---------------------------------------------------------------------------------------
 struct InstDev {
   long long f_off;       // element offset of cell 0 in every field
-  int J;                 // cells
+  int J;                 // cells (nx ny in 2-D)
+  int nx, ny;            // grid (ny = 1 in 1-D)
+  int space_dim;
   int cell0;             // global index of cell 0 (collision-step cell list)
   int collision;         // sgs_collision
-  int bc_kind[2];
-  double dx, eps;
+  int bc_kind[4];        // x_lo, x_hi, y_lo, y_hi
+  double dx, dy, eps;    // dy = 1 in 1-D (cell measure dx dy)
   double b0;
-  double bc_rho[2];      // inflow density (unused for diffuse walls)
-  double wall_denom[2];  // sum over incoming v of w v1 Mhat_wall (diffuse walls)
+  double bc_rho[4];      // inflow density (unused for diffuse walls)
+  double wall_denom[4];  // sum over incoming v of w (v.n) Mhat_wall (diffuse walls)
   double total_mass;
   double inner_tol;
   int inner_max, inner_fixed, inner_method, newton_max;
   double newton_tol;
-  // Unit wall Maxwellian, separable: Mhat(v) = W[s][0][i1] W[s][1][i2] W[s][2][i3], with the
-  // incoming half of v1 kept and the outgoing half zeroed in W[s][0].
-  double wall[2][3][kMaxN];
+  // Unit wall Maxwellian of side s, separable: Mhat(v) = W[s][0][i1] W[s][1][i2] W[s][2][i3],
+  // with the incoming half of the normal component kept and the outgoing half zeroed (in
+  // W[s][0] for the x sides, W[s][1] for the y sides).
+  double wall[4][3][kMaxN];
 };
 
 struct Counters {

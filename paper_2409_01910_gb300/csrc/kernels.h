@@ -127,6 +127,7 @@ struct SweepArgs {
   double dv;
   int dir;                // +1 forward, -1 backward
   const int* active;      // per instance: 0 = converged, its scans are skipped
+  const double* theta;    // per global cell: Maxwellian exponents of the last collision step
 };
 
 struct AuxArgs {
@@ -137,6 +138,8 @@ struct AuxArgs {
   const int* cell_inst;
   double* scratch;        // per-cell partials, per-instance values
   const int* active;      // per instance: 0 = converged, its rescale is skipped
+  int two_d;              // 2-D space (one instance): grid nx x ny
+  int nx, ny;
 };
 
 // cudaFuncSetAttribute through a per-device cache: the call is made once per (kernel,
@@ -179,6 +182,9 @@ bool sweep_shape_valid(int N, const SweepShape& sh);
 // the shape that fit on the device at once (0: the shape cannot run).
 bool sweep_ept_compiled(int ept);
 cudaError_t sweep_max_clusters(const SweepShape& sh, int arith, int* n);
+// 2-D: one wavefront (anti-diagonal wf of ordering 0..3) of the single 2-D instance.
+cudaError_t launch_sweep2d(const SweepArgs& a, const SweepShape& sh, int arith, int ordering, int wf, int ncells,
+                           cudaStream_t st);
 cudaError_t launch_sweep(const SweepArgs& a, const SweepShape& sh, int arith, cudaStream_t st);
 
 cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st);
@@ -186,6 +192,10 @@ cudaError_t launch_dc_rhs(const AuxArgs& a, const double* Qhi, double* Qlo_b, cu
 cudaError_t launch_residual(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
                             cudaStream_t st);
 cudaError_t launch_restrict(const double* fine, double* coarse, long long K, int Jc, cudaStream_t st);
+// 2 x 2 coarsening of an nx x ny grid (2-D)
+cudaError_t launch_restrict2d(const double* fine, double* coarse, long long K, int nx, int ny, cudaStream_t st);
+cudaError_t launch_prolong_add2d(double* fine, const double* fc, const double* fc0, long long K, int nx, int ny,
+                                 cudaStream_t st);
 cudaError_t launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st);
 cudaError_t launch_prolong_add(double* fine, const double* fc, const double* fc0, long long K, int Jc,
                                cudaStream_t st);

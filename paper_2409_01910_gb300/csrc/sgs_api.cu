@@ -103,6 +103,7 @@ struct sgs_handle {
   } off;
   bool dc_ref = false;  // FP32 collisions use the increment form against the stored reference
   int dc_prec = SGS_DF64;  // arithmetic of the high-precision evaluation in sgs_dc_step
+  bool two_d = false;      // 2-D space: one instance, wavefront scans, four orderings
   // multigrid levels: lev[0] is the bound grid (tables at off.inst, off.cell_off, off.cell_inst);
   // level l has every instance's cell count halved l times and its own tables and fields
   struct Level {
@@ -112,6 +113,7 @@ struct sgs_handle {
     // levels the restricted iterate I f and its FP32 collision operator
     size_t rf = 0, rQ = 0, rth = 0, rah = 0;
     bool ref = false;
+    InstDev hinst0;  // host copy of instance 0 on this level (2-D grid sizes)
     std::vector<InstDev> hinst;
     std::vector<long long> hcell_off;
     std::vector<int> hcell_inst;
@@ -239,7 +241,9 @@ void layout(sgs_handle* h) {
   f.active = take(sizeof(int) * h->n_inst);
   f.theta = take(sizeof(double) * 5 * C);
   f.nu = take(sizeof(double) * C);
-  f.scratch = take(sizeof(double) * (2 * h->n_inst + 2 * C + 64));
+  // per instance: 2 wall fluxes; per cell: residual partial and mass; 2-D: one outgoing
+  // flux per boundary face
+  f.scratch = take(sizeof(double) * (2 * h->n_inst + 2 * C + 2 * (h->inst[0].nx + h->inst[0].ny) + 64));
   f.tw_cos = take(sizeof(double) * n * N);
   f.tw_sin = take(sizeof(double) * n * N);
   bool sp = h->spectral;
@@ -307,8 +311,17 @@ void layout(sgs_handle* h) {
 }
 
 int check_problem(const sgs_problem& p) {
-  if (p.space_dim != 1) return p.space_dim == 2 ? SGS_ERR_UNSUPPORTED : SGS_ERR_ARG;
+  if (p.space_dim != 1 && p.space_dim != 2) return SGS_ERR_ARG;
   if (p.nx < 1 || !(p.x_hi > p.x_lo)) return SGS_ERR_ARG;
+  if (p.space_dim == 2) {
+    if (p.ny < 1 || !(p.y_hi > p.y_lo)) return SGS_ERR_ARG;
+    for (int s = 2; s < 4; s++) {
+      if (p.bc[s].kind != SGS_DIFFUSE && p.bc[s].kind != SGS_INFLOW) return SGS_ERR_ARG;
+      if (!(p.bc[s].T > 0.0)) return SGS_ERR_ARG;
+      if (p.bc[s].kind == SGS_INFLOW && !(p.bc[s].rho > 0.0)) return SGS_ERR_ARG;
+      if (p.bc[s].kind == SGS_DIFFUSE && p.bc[s].u[1] != 0.0) return SGS_ERR_UNSUPPORTED;  // tangential walls
+    }
+  }
   if (!valid_nv(p.nv) || !(p.v_max > 0.0)) return SGS_ERR_ARG;
   if (p.collision < SGS_MAXWELL || p.collision > SGS_BGK) return SGS_ERR_ARG;
   if (!(p.b0 > 0.0) || !(p.eps > 0.0)) return SGS_ERR_ARG;
@@ -326,9 +339,14 @@ int check_problem(const sgs_problem& p) {
 
 void fill_inst(const sgs_problem& p, int N, double dv, InstDev& I) {
   memset(&I, 0, sizeof(I));
-  I.J = p.nx;
+  const bool two_d = p.space_dim == 2;
+  I.space_dim = two_d ? 2 : 1;
+  I.nx = p.nx;
+  I.ny = two_d ? p.ny : 1;
+  I.J = I.nx * I.ny;
   I.collision = p.collision;
   I.dx = (p.x_hi - p.x_lo) / p.nx;
+  I.dy = two_d ? (p.y_hi - p.y_lo) / p.ny : 1.0;
   I.eps = p.eps;
   I.b0 = p.b0;
   I.total_mass = p.total_mass;
@@ -339,8 +357,9 @@ void fill_inst(const sgs_problem& p, int N, double dv, InstDev& I) {
   I.newton_max = p.newton_max;
   I.newton_tol = p.newton_tol;
   double w = dv * dv * dv;
-  for (int s = 0; s < 2; s++) {
+  for (int s = 0; s < (two_d ? 4 : 2); s++) {
     const sgs_bc& b = p.bc[s];
+    const int dn = s < 2 ? 0 : 1;  // normal velocity component of the side
     I.bc_kind[s] = b.kind;
     I.bc_rho[s] = b.rho;
     double T = b.T;
@@ -349,20 +368,18 @@ void fill_inst(const sgs_problem& p, int N, double dv, InstDev& I) {
       for (int i = 0; i < N; i++) {
         double v = node(i, N, dv);
         double x = std::exp(-(v - b.u[d]) * (v - b.u[d]) / (2.0 * T));
-        if (d == 0) {
-          bool incoming = s == 0 ? v > 0.0 : v < 0.0;
-          x = incoming ? norm * x : 0.0;
+        if (d == 0) x *= norm;
+        if (d == dn) {
+          bool incoming = s % 2 == 0 ? v > 0.0 : v < 0.0;
+          x = incoming ? x : 0.0;
         }
         I.wall[s][d][i] = x;
       }
-    // sum over incoming v of w v1 Mhat
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int i = 0; i < N; i++) {
-      s1 += node(i, N, dv) * I.wall[s][0][i];
-      s2 += I.wall[s][1][i];
-      s3 += I.wall[s][2][i];
-    }
-    I.wall_denom[s] = w * s1 * s2 * s3;
+    // sum over incoming v of w (v.n) Mhat with the normal component n of the side
+    double sd[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < 3; d++)
+      for (int i = 0; i < N; i++) sd[d] += (d == dn ? node(i, N, dv) : 1.0) * I.wall[s][d][i];
+    I.wall_denom[s] = w * sd[0] * sd[1] * sd[2];
   }
 }
 
@@ -423,6 +440,9 @@ AuxArgs aux_args(const sgs_handle* h, int l = 0) {
   a.cell_inst = h->at<int>(L.cell_inst);
   a.scratch = h->at<double>(h->off.scratch);
   a.active = h->at<int>(h->off.active);
+  a.two_d = h->two_d ? 1 : 0;
+  a.nx = L.hinst0.nx;
+  a.ny = L.hinst0.ny;
   return a;
 }
 
@@ -584,7 +604,10 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
   return run(collide_ctx<double>(h, l));
 }
 
-int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int dir, cudaStream_t st, int l = 0) {
+// One scan: in 1-D dir +1 / -1 walks the cells forward / backward (ordering 0 / 1); in 2-D
+// the ordering o in 0..3 is launched wavefront by wavefront.
+int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int dir, cudaStream_t st, int l = 0,
+               int ordering = -1) {
   SweepArgs a;
   a.inst = h->at<InstDev>(h->lev[l].inst);
   a.n_inst = h->n_inst;
@@ -597,6 +620,19 @@ int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int
   a.dv = h->dv;
   a.dir = dir;
   a.active = h->at<int>(h->off.active);
+  a.theta = h->at<double>(h->off.theta);
+  if (h->two_d) {
+    const InstDev& I = h->lev[l].hinst0;
+    const int o = ordering >= 0 ? ordering : (dir > 0 ? 0 : 1);
+    const int nwf = I.nx + I.ny - 1;
+    Scope sc(h, SGS_PROF_SWEEP, st, nwf);
+    for (int wf = 0; wf < nwf; wf++) {
+      int ncells = std::min(I.nx - 1, wf) - std::max(0, wf - (I.ny - 1)) + 1;
+      cudaError_t e = launch_sweep2d(a, h->sweep, h->sweep_arith, o, wf, ncells, st);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    return SGS_OK;
+  }
   Scope sc(h, SGS_PROF_SWEEP, st, 1);
   return cuda_status(launch_sweep(a, h->sweep, h->sweep_arith, st));
 }
@@ -625,9 +661,17 @@ int iterate_impl(sgs_handle* h, double* f, double* Q, double* P, const double* r
     r = collide_impl(h, f, nullptr, P, h->precision, st, l);
     if (r) return r;
   }
-  if ((r = sweep_impl(h, f, P, rhs, +1, st, l))) return r;
-  if ((r = collide_impl(h, f, nullptr, P, h->precision, st, l))) return r;
-  if ((r = sweep_impl(h, f, P, rhs, -1, st, l))) return r;
+  if (h->two_d) {
+    // the four corner-to-corner orderings, each after a collision evaluation
+    for (int o = 0; o < 4; o++) {
+      if (o > 0 && (r = collide_impl(h, f, nullptr, P, h->precision, st, l))) return r;
+      if ((r = sweep_impl(h, f, P, rhs, 0, st, l, o))) return r;
+    }
+  } else {
+    if ((r = sweep_impl(h, f, P, rhs, +1, st, l))) return r;
+    if ((r = collide_impl(h, f, nullptr, P, h->precision, st, l))) return r;
+    if ((r = sweep_impl(h, f, P, rhs, -1, st, l))) return r;
+  }
   if (l == 0 && (r = rescale_impl(h, f, st))) return r;
   if (flags & SGS_IT_EVAL) {
     if (!Q) return SGS_ERR_ARG;
@@ -667,8 +711,14 @@ int vcycle_impl(sgs_handle* h, int l, int levels, double* f, const double* b, in
   if ((r = residual_field_impl(h, f, Ql, b, R, st, l))) return r;
   {
     Scope sc(h, SGS_PROF_RESCALE, st, 2);
-    cudaError_t e = launch_restrict(f, fH0, K, H.C, st);
-    if (e == cudaSuccess) e = launch_restrict(R, bH, K, H.C, st);
+    cudaError_t e;
+    if (h->two_d) {
+      e = launch_restrict2d(f, fH0, K, L.hinst0.nx, L.hinst0.ny, st);
+      if (e == cudaSuccess) e = launch_restrict2d(R, bH, K, L.hinst0.nx, L.hinst0.ny, st);
+    } else {
+      e = launch_restrict(f, fH0, K, H.C, st);
+      if (e == cudaSuccess) e = launch_restrict(R, bH, K, H.C, st);
+    }
     if (e != cudaSuccess) return cuda_status(e);
   }
   // b_H = R_H(I f) - I(R_h), with R_H(I f) the coarse residual field of the restricted iterate
@@ -699,7 +749,8 @@ int vcycle_impl(sgs_handle* h, int l, int levels, double* f, const double* b, in
   if ((r = vcycle_impl(h, l + 1, levels, fH, bH, pre, post, coarse_iters, st))) return r;
   {
     Scope sc(h, SGS_PROF_RESCALE, st, 1);
-    cudaError_t e = launch_prolong_add(f, fH, fH0, K, H.C, st);
+    cudaError_t e = h->two_d ? launch_prolong_add2d(f, fH, fH0, K, L.hinst0.nx, L.hinst0.ny, st)
+                             : launch_prolong_add(f, fH, fH0, K, H.C, st);
     if (e != cudaSuccess) return cuda_status(e);
   }
   for (int it = 0; it < post; it++)
@@ -765,6 +816,7 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
         (problems[q].collision != SGS_BGK && problems[q].collision != problems[0].collision))
       return SGS_ERR_UNSUPPORTED;
   }
+  if (problems[0].space_dim == 2 && n_inst != 1) return SGS_ERR_UNSUPPORTED;  // one 2-D instance per handle
   sgs_handle* h = new (std::nothrow) sgs_handle();
   if (!h) return SGS_ERR_NOMEM;
   h->n_inst = n_inst;
@@ -774,6 +826,7 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
   h->dv = 2.0 * h->L / h->N;
   h->precision = problems[0].precision;
   h->spectral = problems[0].collision != SGS_BGK;
+  h->two_d = problems[0].space_dim == 2;
   long long K = (long long)h->N * h->N * h->N;
   h->inst.resize(n_inst);
   long long off = 0;
@@ -782,12 +835,13 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
     fill_inst(problems[q], h->N, h->dv, h->inst[q]);
     h->inst[q].f_off = off;
     h->inst[q].cell0 = cell;
-    for (int j = 0; j < problems[q].nx; j++) {
+    const int Jq = h->inst[q].J;
+    for (int j = 0; j < Jq; j++) {
       h->cell_off.push_back(off + j * K);
       h->cell_inst.push_back(q);
     }
-    off += (long long)problems[q].nx * K;
-    cell += problems[q].nx;
+    off += (long long)Jq * K;
+    cell += Jq;
   }
   h->field = off;
   h->C = cell;
@@ -795,11 +849,14 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
     sgs_handle::Level L0;
     L0.C = cell;
     L0.G = (cell + kLanes - 1) / kLanes;
+    L0.hinst0 = h->inst[0];
     h->lev.push_back(L0);
     for (int l = 1;; l++) {
       bool ok = true;
-      for (int q = 0; q < n_inst; q++)
+      for (int q = 0; q < n_inst; q++) {
         if (problems[q].nx % (1 << l) != 0) ok = false;
+        if (h->two_d && problems[q].ny % (1 << l) != 0) ok = false;  // 2 x 2 coarsening
+      }
       if (!ok || l > 12) break;
       sgs_handle::Level L;
       long long loff = 0;
@@ -807,19 +864,21 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
       for (int q = 0; q < n_inst; q++) {
         sgs_problem pc = problems[q];
         pc.nx = problems[q].nx >> l;
+        if (h->two_d) pc.ny = problems[q].ny >> l;
         pc.total_mass = 0.0;  // no rescale on coarse levels
         InstDev I;
         fill_inst(pc, h->N, h->dv, I);
         I.f_off = loff;
         I.cell0 = lcell;
         L.hinst.push_back(I);
-        for (int j = 0; j < pc.nx; j++) {
+        for (int j = 0; j < I.J; j++) {
           L.hcell_off.push_back(loff + j * K);
           L.hcell_inst.push_back(q);
         }
-        loff += (long long)pc.nx * K;
-        lcell += pc.nx;
+        loff += (long long)I.J * K;
+        lcell += I.J;
       }
+      L.hinst0 = L.hinst[0];
       L.C = lcell;
       L.G = (lcell + kLanes - 1) / kLanes;
       h->lev.push_back(L);
@@ -933,6 +992,12 @@ int sgs_sweep_backward(sgs_handle* h, double* f, const double* P, const double* 
   if (!h || !f || !P) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;
   return sweep_impl(h, f, P, rhs, -1, as_stream(stream));
+}
+
+int sgs_sweep_ordering(sgs_handle* h, double* f, const double* P, const double* rhs, int ordering, void* stream) {
+  if (!h || !f || !P || ordering < 0 || ordering > (h->two_d ? 3 : 1)) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return sweep_impl(h, f, P, rhs, ordering == 0 ? +1 : -1, as_stream(stream), 0, ordering);
 }
 
 int sgs_rescale(sgs_handle* h, double* f, void* stream) {
@@ -1070,10 +1135,10 @@ int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning
     for (int cs = 1; cs <= 16; cs *= 2) {
       int per = (K + ept * cs - 1) / (ept * cs);
       int tpb = (per + 31) / 32 * 32;
-      if (tpb < 128) tpb = 128;
+      if (tpb < 160) tpb = 160;  // warps 0-4 serve the Newton evaluations
       SweepShape sh{ept, cs, tpb};
       if (!sweep_shape_valid(h->N, sh)) continue;
-      if ((long long)(tpb - 32) * cs * ept >= K && tpb > 128) continue;  // a whole warp idle in every CTA
+      if ((long long)(tpb - 32) * cs * ept >= K && tpb > 160) continue;  // a whole warp idle in every CTA
       int n = 0;
       if (sweep_max_clusters(sh, h->sweep_arith, &n) != cudaSuccess) {
         cudaGetLastError();

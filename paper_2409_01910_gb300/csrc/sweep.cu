@@ -23,11 +23,14 @@
 
 namespace sgs {
 
+constexpr int kRedMax = 10;  // values per cluster reduction
+
 template <typename E>
 struct SweepSmem {
   E vv[kMaxN];         // nodes v_i
   E vq[kMaxN];         // v_i^2
-  E c1e[kMaxN];        // |v_i| / dx (step-1 weights)
+  E c1e[kMaxN];        // |v_i| / dx (step-1 weights, x part)
+  E c2e[kMaxN];        // |v_i| / dy (step-1 weights, y part; 2-D)
   E den[kMaxN];        // 1 / (|v_i|/dx + nu/eps) of the current cell
   E c1A[kMaxN];        // |v_i|/dx + nu/eps of the current cell
   E ef[3][kMaxN];      // factors of the last Newton evaluation (ef[0] carries exp(alpha))
@@ -35,19 +38,21 @@ struct SweepSmem {
   E Ep[3][kMaxN];      // factors of the step-1 Maxwellian
   E S[3][5];           // 1-D sums of the last evaluation (unweighted)
   E S1w[5];            // dimension-1 sums with the step-1 weights |v1|/dx, same evaluation
+  E S2w[5];            // dimension-2 sums with the weights |v2|/dy (2-D), same evaluation
   E svE[5];            // step-1 target s
-  E W3[2][kMaxN];      // third factor of each wall's unit Maxwellian
-  E red_warp[32][8];
-  E red_tote[8];
+  E W3[4][kMaxN];      // third factor of each wall's unit Maxwellian
+  E red_warp[32][kRedMax];
+  E red_tote[kRedMax];
   E thE[5];            // trial theta in E
-  E scal[4];           // per-visit scalars: rho_l, rho_r, nu/eps
-  double red_part[2][8];
-  double red_tot[8];
+  E scal[6];           // per-visit scalars: wall densities of the sides, nu/eps
+  double red_part[2][kRedMax];
+  double red_tot[kRedMax];
   double thg[5], thp[5], th_try[5], dir[5];
   float fn;
   float stepf;         // exponent change of the full Newton step
   int flag;
   int ctl;             // broadcast decisions of thread 0
+  int wdims;           // space dimensions of the step-1 weights (1: |v1|/dx; 2: + |v2|/dy)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -99,9 +104,10 @@ __device__ inline void cluster_reduce(E (&v)[NV], double (&tot)[NV], SweepSmem<E
 template <typename E>
 __device__ __noinline__ void eval_cta(SweepSmem<E>& sm, int N) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (wid < 4) {
-    // warps 0-2: dimension d; warp 3: dimension 1 again, weighted by |v1|/dx (step 1, eq. (24))
-    const int d = wid == 3 ? 0 : wid;
+  if (wid < 3 + sm.wdims) {
+    // warps 0-2: dimension d; warp 3: dimension 1 again, weighted by |v1|/dx; warp 4 (2-D):
+    // dimension 2 again, weighted by |v2|/dy (step 1, eq. (24))
+    const int d = wid == 3 ? 0 : (wid == 4 ? 1 : wid);
     E e = cvt<E>(0.0);
     if (lane < N) {
       E x = sm.thE[1 + d] * sm.vv[lane] - sm.thE[4] * sm.vq[lane];
@@ -110,6 +116,7 @@ __device__ __noinline__ void eval_cta(SweepSmem<E>& sm, int N) {
     }
     if (wid < 3) sm.ef[d][lane] = e;
     if (wid == 3) e = e * sm.c1e[lane];
+    if (wid == 4) e = e * sm.c2e[lane];
     E s[5];
     s[0] = e;
     s[1] = e * sm.vv[lane];
@@ -124,30 +131,24 @@ __device__ __noinline__ void eval_cta(SweepSmem<E>& sm, int N) {
         if (lane == q) t = s[q];
       if (wid < 3)
         sm.S[d][lane] = t;
-      else
+      else if (wid == 3)
         sm.S1w[lane] = t;
+      else
+        sm.S2w[lane] = t;
     }
   }
   __syncthreads();
 }
 
-// Warp 0: residual F (E), Jacobian (FP32) and the scaled residual norm from the 1-D sums.
+// Moments (E) and Jacobian (FP32) of the separable Maxwellian from its three 1-D sums.
 template <typename E>
-__device__ inline void combine(const SweepSmem<E>& sm, E w, bool wv1, const E* target, E (&F)[5], float (&A)[15],
-                               float& fn) {
-  const E* S1 = wv1 ? sm.S1w : sm.S[0];
-  const E* S2 = sm.S[1];
-  const E* S3 = sm.S[2];
+__device__ inline void moments_from_sums(const E* S1, const E* S2, const E* S3, E (&mom)[5], float (&Aa)[15]) {
   E s23 = S2[0] * S3[0];
-  E mom[5] = {S1[0] * s23, S1[1] * s23, S1[0] * (S2[1] * S3[0]), S1[0] * (S2[0] * S3[1]),
-              S1[2] * s23 + S1[0] * (S2[2] * S3[0] + S2[0] * S3[2])};
-  float amax = 0.0f;
-#pragma unroll
-  for (int i = 0; i < 5; i++) {
-    F[i] = w * mom[i] - target[i];
-    amax = fmaxf(amax, fabsf(tof(F[i])));
-  }
-  fn = amax / fabsf(tof(target[0]));
+  mom[0] = S1[0] * s23;
+  mom[1] = S1[1] * s23;
+  mom[2] = S1[0] * (S2[1] * S3[0]);
+  mom[3] = S1[0] * (S2[0] * S3[1]);
+  mom[4] = S1[2] * s23 + S1[0] * (S2[2] * S3[0] + S2[0] * S3[2]);
   float f1[5], f2[5], f3[5];
 #pragma unroll
   for (int p = 0; p < 5; p++) {
@@ -162,9 +163,38 @@ __device__ inline void combine(const SweepSmem<E>& sm, E w, bool wv1, const E* t
   float c3 = f1[2] * f2[0] * f3[1] + f1[0] * f2[2] * f3[1] + f1[0] * f2[0] * f3[3];
   float e4 = f1[4] * f2[0] * f3[0] + f1[0] * f2[4] * f3[0] + f1[0] * f2[0] * f3[4] +
              2.0f * (f1[2] * f2[2] * f3[0] + f1[2] * f2[0] * f3[2] + f1[0] * f2[2] * f3[2]);
+  float t[15] = {f1[0] * f2[0] * f3[0], f1[1] * f2[0] * f3[0], f1[0] * f2[1] * f3[0], f1[0] * f2[0] * f3[1],
+                 q11 + q22 + q33, q11, q12, q13, c1, q22, q23, c2, q33, c3, e4};
+#pragma unroll
+  for (int i = 0; i < 15; i++) Aa[i] = t[i];
+}
+
+// Warp 0: residual F (E), Jacobian (FP32) and the scaled residual norm from the 1-D sums.
+// wmode 0: plain weights w; 1: w |v1|/dx; 2: w (|v1|/dx + |v2|/dy), a sum of two separable
+// terms.
+template <typename E>
+__device__ inline void combine(const SweepSmem<E>& sm, E w, int wmode, const E* target, E (&F)[5], float (&A)[15],
+                               float& fn) {
+  E mom[5];
+  float Aa[15];
+  moments_from_sums<E>(wmode ? sm.S1w : sm.S[0], sm.S[1], sm.S[2], mom, Aa);
+  if (wmode == 2) {
+    E m2[5];
+    float A2[15];
+    moments_from_sums<E>(sm.S[0], sm.S2w, sm.S[2], m2, A2);
+#pragma unroll
+    for (int i = 0; i < 5; i++) mom[i] += m2[i];
+#pragma unroll
+    for (int i = 0; i < 15; i++) Aa[i] += A2[i];
+  }
+  float amax = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    F[i] = w * mom[i] - target[i];
+    amax = fmaxf(amax, fabsf(tof(F[i])));
+  }
+  fn = amax / fabsf(tof(target[0]));
   float cf = tof(w);
-  float Aa[15] = {f1[0] * f2[0] * f3[0], f1[1] * f2[0] * f3[0], f1[0] * f2[1] * f3[0], f1[0] * f2[0] * f3[1],
-                  q11 + q22 + q33, q11, q12, q13, c1, q22, q23, c2, q33, c3, e4};
 #pragma unroll
   for (int i = 0; i < 15; i++) A[i] = cf * Aa[i];
 }
@@ -174,7 +204,7 @@ __device__ inline void combine(const SweepSmem<E>& sm, E w, bool wv1, const E* t
 // evaluation is at th, and the return value is the iteration count; -1 on failure. Scalar
 // FP64 decisions are taken by thread 0 and broadcast (FP64 is scarce on this GPU).
 template <typename E>
-__device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, bool wv1, const E* target, double* th,
+__device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, int wmode, const E* target, double* th,
                                        double L, double tol, int maxit, bool have_eval) {
   const int wid = threadIdx.x >> 5, tid = threadIdx.x;
   if (!have_eval) {
@@ -185,7 +215,7 @@ __device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, bool wv1, c
   E F[5];
   float A[15], fnv = 0.0f;
   if (wid == 0) {
-    combine<E>(sm, w, wv1, target, F, A, fnv);
+    combine<E>(sm, w, wmode, target, F, A, fnv);
     if (tid == 0) sm.fn = fnv;
   }
   __syncthreads();
@@ -229,7 +259,7 @@ __device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, bool wv1, c
       __syncthreads();
       eval_cta<E>(sm, N);
       if (wid == 0) {
-        combine<E>(sm, w, wv1, target, F, A, fnv);
+        combine<E>(sm, w, wmode, target, F, A, fnv);
         if (tid == 0) sm.fn = fnv;
       }
       __syncthreads();
@@ -280,7 +310,7 @@ __device__ __noinline__ int solve_mg(SweepSmem<E>& sm, int N, E w, const E* mom,
   if (th0) {
     if (tid < 5) sm.thg[tid] = keep[tid];
     __syncthreads();
-    it = newton_cta<E>(sm, N, w, false, mom, sm.thg, L, tol, maxit, have_eval);
+    it = newton_cta<E>(sm, N, w, 0, mom, sm.thg, L, tol, maxit, have_eval);
   }
   if (it < 0) {
     if (tid == 0) {
@@ -292,7 +322,7 @@ __device__ __noinline__ int solve_mg(SweepSmem<E>& sm, int N, E w, const E* mom,
     }
     __syncthreads();
     if (sm.ctl) {
-      it = newton_cta<E>(sm, N, w, false, mom, sm.thg, L, tol, maxit, false);
+      it = newton_cta<E>(sm, N, w, 0, mom, sm.thg, L, tol, maxit, false);
     } else {
       status |= SGS_ST_NONPOSITIVE;
     }
@@ -335,9 +365,11 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     sm.vv[tid] = cvt<E>(v);
     sm.vq[tid] = cvt<E>(v * v);
     sm.c1e[tid] = cvt<E>(fabs(v) * inv_dx);
+    sm.c2e[tid] = zero;
     sm.W3[0][tid] = cvt<E>(tid < N ? I.wall[0][2][tid] : 0.0);
     sm.W3[1][tid] = cvt<E>(tid < N ? I.wall[1][2][tid] : 0.0);
   }
+  if (tid == 0) sm.wdims = 1;
   __syncthreads();
 
   // this thread's nodes: pencil (i1, i2), i3 in [i30, i30 + EPT)
@@ -480,7 +512,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           if (tid < 5) sm.thp[tid] = sm.thg[tid];
           __syncthreads();
           // the last evaluation is M[g]'s: reused as the first one of step 1
-          int n1 = newton_cta<E>(sm, N, w, true, sv, sm.thp, L, ntol, I.newton_max, true);
+          int n1 = newton_cta<E>(sm, N, w, 1, sv, sm.thp, L, ntol, I.newton_max, true);
           c_solves++;
           if (n1 >= 0) {
             c_newton += n1;
@@ -540,8 +572,257 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   if (tid == 0 && status) atomicOr(&a.cnt[q].status, status);
 }
 
+// ---------------------------------------------------------------------------------------
+// 2-D space: one sweep ordering is a sequence of anti-diagonal wavefronts. Cells on one
+// wavefront depend only on the previous wavefront (their upwind x and y neighbours) and on
+// not-yet-visited cells (downwind), so the cells of a wavefront are visited concurrently,
+// one thread-block cluster per cell, one launch per wavefront (the launch boundary orders
+// the wavefronts). The visit is the 1-D visit with the transport weight
+// c = |v1|/dx + |v2|/dy, four neighbours (or wall ghosts) and step-1 weights w c, whose
+// Newton sums are two separable terms. The M[g] solve of the stored value starts from the
+// Maxwellian of the collision step that preceded the sweep (same f, so it is converged).
+// Ordering o: 0 SW->NE, 1 NE->SW, 2 NW->SE, 3 SE->NW; wavefront index wf counts from the
+// ordering's starting corner.
+// ---------------------------------------------------------------------------------------
+template <typename E, int EPT>
+__global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int wf) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const InstDev& I = a.inst[0];
+  const int nx = I.nx, ny = I.ny;
+  const int amin = max(0, wf - (ny - 1)), amax = min(nx - 1, wf);
+  const int ak = amin + (int)(blockIdx.x / CS);
+  if (ak > amax) return;  // whole cluster, uniformly
+  if (a.active && !a.active[0]) return;
+  const int dirx = (ordering == 0 || ordering == 2) ? 1 : -1;
+  const int diry = (ordering == 0 || ordering == 3) ? 1 : -1;
+  const int ci = dirx > 0 ? ak : nx - 1 - ak;
+  const int bk = wf - ak;
+  const int cj = diry > 0 ? bk : ny - 1 - bk;
+  const int cell = cj * nx + ci;
+
+  __shared__ SweepSmem<E> sm;
+  const int N = a.N, K = N * N * N;
+  const double dv = a.dv, wd = a.dv * a.dv * a.dv;
+  const E w = cvt<E>(wd);
+  const double inv_dx = 1.0 / I.dx, inv_dy = 1.0 / I.dy;
+  const double L = node(N - 1, N, dv);
+  const int tid = threadIdx.x;
+  const bool pfp = I.inner_method == SGS_PFP;
+  const bool lowp = sizeof(E) == 4;
+  const double ntol = lowp ? fmax(I.newton_tol, 1e-5) : I.newton_tol;
+  const E inv_eps = cvt<E>(1.0 / I.eps);
+  const E zero = cvt<E>(0.0);
+  if (tid < kMaxN) {
+    double v = tid < N ? node(tid, N, dv) : 0.0;
+    sm.vv[tid] = cvt<E>(v);
+    sm.vq[tid] = cvt<E>(v * v);
+    sm.c1e[tid] = cvt<E>(fabs(v) * inv_dx);
+    sm.c2e[tid] = cvt<E>(fabs(v) * inv_dy);
+#pragma unroll
+    for (int sd = 0; sd < 4; sd++) sm.W3[sd][tid] = cvt<E>(tid < N ? I.wall[sd][2][tid] : 0.0);
+  }
+  if (tid == 0) sm.wdims = 2;
+  __syncthreads();
+
+  // this thread's nodes: pencil (i1, i2), i3 in [i30, i30 + EPT)
+  const int tg = rank * blockDim.x + tid;
+  const int e0 = tg * EPT;
+  const bool own = e0 < K;
+  const int pen = own ? e0 / N : 0, i30 = own ? e0 % N : 0;
+  const int i1 = pen / N, i2 = pen % N;
+  const double v1d = node(i1, N, dv), v2d = node(i2, N, dv);
+  const E v1 = sm.vv[i1], v2 = sm.vv[i2];
+  const E cw = sm.c1e[i1] + sm.c2e[i2];  // transport weight |v1|/dx + |v2|/dy
+  const E v1p = cvt<E>(fmax(v1d, 0.0) * inv_dx), v1m = cvt<E>(fmin(v1d, 0.0) * inv_dx);
+  const E v2p = cvt<E>(fmax(v2d, 0.0) * inv_dy), v2m = cvt<E>(fmin(v2d, 0.0) * inv_dy);
+  const E vq12 = sm.vq[i1] + sm.vq[i2];
+  E w12[4];
+#pragma unroll
+  for (int sd = 0; sd < 4; sd++) w12[sd] = cvt<E>(I.wall[sd][0][i1] * I.wall[sd][1][i2]);
+  const bool bnd[4] = {ci == 0, ci == nx - 1, cj == 0, cj == ny - 1};
+
+  E g[EPT], r[EPT];
+  int buf = 0;
+  unsigned long long c_newton = 0, c_solves = 0, c_fallback = 0;
+  unsigned int status = 0;
+  const long long cbase = I.f_off + (long long)cell * K + e0;
+  double* fj = a.f + cbase;
+  const int gcell = I.cell0 + cell;
+
+  // ---- reduction 1: moments of the stored value and its outgoing fluxes through wall faces
+  E a0 = zero, a3 = zero, a4 = zero;
+  if (own) {
+#pragma unroll
+    for (int t = 0; t < EPT; t++) {
+      E x = cvt<E>(fj[t]);
+      g[t] = x;
+      a0 += x;
+      a3 += x * sm.vv[i30 + t];
+      a4 += x * sm.vq[i30 + t];
+    }
+  }
+  E m9[9] = {a0,
+             v1 * a0,
+             v2 * a0,
+             a3,
+             vq12 * a0 + a4,
+             (bnd[0] && v1d < 0.0) ? v1 * a0 : zero,
+             (bnd[1] && v1d > 0.0) ? v1 * a0 : zero,
+             (bnd[2] && v2d < 0.0) ? v2 * a0 : zero,
+             (bnd[3] && v2d > 0.0) ? v2 * a0 : zero};
+  double t9[9];
+  cluster_reduce<9, E>(m9, t9, sm, buf, cl, CS);
+  E mom[5];
+#pragma unroll
+  for (int k = 0; k < 5; k++) mom[k] = w * sm.red_tote[k];
+  const double Ad = a.nu[gcell] / I.eps;
+  if (tid < 4) {
+    const int sd = tid;
+    sm.scal[sd] = cvt<E>(I.bc_kind[sd] == SGS_INFLOW ? I.bc_rho[sd] : -(wd * t9[5 + sd]) / I.wall_denom[sd]);
+  }
+  if (tid == 4) sm.scal[4] = cvt<E>(Ad);
+  __syncthreads();
+  const E Acoef = sm.scal[4];
+  const double cAd = fabs(v1d) * inv_dx + fabs(v2d) * inv_dy + Ad;
+  const E cA = cvt<E>(cAd), den = cvt<E>(1.0 / cAd);
+
+  // ---- r = (-v1^+ f_W + v1^- f_E)/dx + (-v2^+ f_S + v2^- f_N)/dy - P/eps - b (latest values)
+  if (own) {
+    const double* Pj = a.P + cbase;
+    const double* bj = a.rhs ? a.rhs + cbase : nullptr;
+#pragma unroll
+    for (int t = 0; t < EPT; t++) {
+      const int i3 = i30 + t;
+      E fw = bnd[0] ? sm.scal[0] * w12[0] * sm.W3[0][i3] : cvt<E>(fj[t - K]);
+      E fe = bnd[1] ? sm.scal[1] * w12[1] * sm.W3[1][i3] : cvt<E>(fj[t + K]);
+      E fs = bnd[2] ? sm.scal[2] * w12[2] * sm.W3[2][i3] : cvt<E>(fj[t - (long long)nx * K]);
+      E fn = bnd[3] ? sm.scal[3] * w12[3] * sm.W3[3][i3] : cvt<E>(fj[t + (long long)nx * K]);
+      E rv = v1m * fe - v1p * fw + v2m * fn - v2p * fs - cvt<E>(Pj[t]) * inv_eps;
+      if (bj) rv -= cvt<E>(bj[t]);
+      r[t] = rv;
+    }
+  }
+
+  // ---- M[g] of the stored value, from the collision step's Maxwellian of the same f
+  {
+    double th0[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) th0[k] = a.theta[5 * (long long)gcell + k];
+    int n0 = solve_mg<E>(sm, N, w, mom, th0, false, L, ntol, I.newton_max, status);
+    if (n0 > 0) c_newton += n0;
+    c_solves++;
+  }
+
+  int it = 0;
+  for (;;) {
+    // ---- pass B: cell-equation residual, its scale, and the step-1 target s (eq. (26))
+    E e12 = sm.Eg[0][i1] * sm.Eg[1][i2];
+    E rs = zero, sc = zero, b0 = zero, b3 = zero, b4 = zero;
+    if (own) {
+#pragma unroll
+      for (int t = 0; t < EPT; t++) {
+        E M = e12 * sm.Eg[2][i30 + t];
+        E res = cA * g[t] + r[t] - Acoef * M;
+        rs += res * res;
+        E mag = cA * g[t];
+        sc += mag * mag;
+        E tt = cw * (M - g[t]) - r[t];
+        b0 += tt;
+        b3 += tt * sm.vv[i30 + t];
+        b4 += tt * sm.vq[i30 + t];
+      }
+    }
+    E v7[7] = {rs, b0, v1 * b0, v2 * b0, b3, vq12 * b0 + b4, sc};
+    double t6[7];
+    cluster_reduce<7, E>(v7, t6, sm, buf, cl, CS);
+    if (tid == 0) {
+      const double res = sqrt(wd * t6[0]);
+      double tol = I.inner_tol;
+      if (lowp) tol = fmax(tol, 2e-6 * sqrt(wd * t6[6]));
+      bool stop;
+      if (I.inner_fixed > 0) {
+        stop = it >= I.inner_fixed;
+      } else {
+        stop = res < tol || it >= I.inner_max;
+        if (stop && !(res < tol)) status |= SGS_ST_INNER_CAP;
+      }
+      if (!(res == res)) {
+        status |= SGS_ST_NONFINITE;
+        stop = true;
+      }
+      double sd[5] = {wd * t6[1], wd * t6[2], wd * t6[3], wd * t6[4], wd * t6[5]};
+      bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+      sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
+    }
+    __syncthreads();
+    const int ctl = sm.ctl;
+    if (ctl & 1) break;
+
+    // ---- step 1 (eq. (24)) with the 2-D weights; else the plain fixed-point step (eq. (22))
+    bool used = false;
+    if (pfp) {
+      if (ctl & 2) {
+        E sv[5];
+#pragma unroll
+        for (int k = 0; k < 5; k++) sv[k] = w * sm.red_tote[1 + k];
+        if (tid < 5) sm.thp[tid] = sm.thg[tid];
+        __syncthreads();
+        int n1 = newton_cta<E>(sm, N, w, 2, sv, sm.thp, L, ntol, I.newton_max, true);
+        c_solves++;
+        if (n1 >= 0) {
+          c_newton += n1;
+          used = true;
+          copy_factors<E>(sm, sm.Ep);
+        }
+      }
+      if (!used) c_fallback++;
+    }
+    const bool eval_at_start = used || !(ctl & 2);
+    E (*Eu)[kMaxN] = used ? sm.Ep : sm.Eg;
+
+    // ---- step 2 (eq. (25)) and the moments of the new iterate
+    E ep = Eu[0][i1] * Eu[1][i2];
+    E c0 = zero, c3 = zero, c4 = zero;
+    if (own) {
+#pragma unroll
+      for (int t = 0; t < EPT; t++) {
+        E x = (Acoef * (ep * Eu[2][i30 + t]) - r[t]) * den;
+        g[t] = x;
+        c0 += x;
+        c3 += x * sm.vv[i30 + t];
+        c4 += x * sm.vq[i30 + t];
+      }
+    }
+    E m5[5] = {c0, v1 * c0, v2 * c0, c3, vq12 * c0 + c4};
+    double t5[5];
+    cluster_reduce<5, E>(m5, t5, sm, buf, cl, CS);
+    it++;
+    E mm[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) mm[k] = w * sm.red_tote[k];
+    int n2 = solve_mg<E>(sm, N, w, mm, used ? sm.thp : sm.thg, eval_at_start, L, ntol, I.newton_max, status);
+    if (n2 > 0) c_newton += n2;
+    c_solves++;
+  }
+
+  if (own) {
+#pragma unroll
+    for (int t = 0; t < EPT; t++) fj[t] = tod(g[t]);
+  }
+  if (rank == 0 && tid == 0) {
+    Counters* c = a.cnt;
+    atomicAdd(&c->visits, 1ULL);
+    atomicAdd(&c->inner_iters, (unsigned long long)it);
+    atomicAdd(&c->newton_iters, c_newton);
+    atomicAdd(&c->newton_solves, c_solves);
+    atomicAdd(&c->fallbacks, c_fallback);
+  }
+  if (tid == 0 && status) atomicOr(&a.cnt[0].status, status);
+}
+
 // Default launch shape: nodes per thread (a divisor of N), cluster size (a power of two, at
-// most 16) and threads per CTA (a multiple of 32 in [128, 256]; warps 0-3 serve the Newton
+// most 16) and threads per CTA (a multiple of 32 in [160, 256]; warps 0-4 serve the Newton
 // evaluations).
 SweepShape sweep_shape(int N, int arith) {
   SweepShape s;
@@ -551,7 +832,7 @@ SweepShape sweep_shape(int N, int arith) {
   s.cluster = 1;
   while (s.cluster < 16 && s.cluster * 256 < threads) s.cluster *= 2;
   s.tpb = ((threads + s.cluster - 1) / s.cluster + 31) / 32 * 32;
-  if (s.tpb < 128) s.tpb = 128;
+  if (s.tpb < 160) s.tpb = 160;
   return s;
 }
 
@@ -572,6 +853,50 @@ static cudaError_t launch_sweep_t(const SweepArgs& a, const SweepShape& sh, cuda
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_sweep<E, EPT>, a);
+}
+
+template <typename E, int EPT>
+static cudaError_t launch_sweep2d_t(const SweepArgs& a, const SweepShape& sh, int ordering, int wf, int ncells,
+                                    cudaStream_t st) {
+  cudaError_t e = func_attr((const void*)k_sweep2d<E, EPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ncells * sh.cluster);
+  cfg.blockDim = dim3(sh.tpb);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = sh.cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_sweep2d<E, EPT>, a, ordering, wf);
+}
+
+template <typename E>
+static cudaError_t launch_sweep2d_e(const SweepArgs& a, const SweepShape& sh, int ordering, int wf, int ncells,
+                                    cudaStream_t st) {
+  switch (sh.ept) {
+    case 2: return launch_sweep2d_t<E, 2>(a, sh, ordering, wf, ncells, st);
+    case 4: return launch_sweep2d_t<E, 4>(a, sh, ordering, wf, ncells, st);
+    case 8: return launch_sweep2d_t<E, 8>(a, sh, ordering, wf, ncells, st);
+    case 12: return launch_sweep2d_t<E, 12>(a, sh, ordering, wf, ncells, st);
+    case 16: return launch_sweep2d_t<E, 16>(a, sh, ordering, wf, ncells, st);
+    case 20: return launch_sweep2d_t<E, 20>(a, sh, ordering, wf, ncells, st);
+    case 24: return launch_sweep2d_t<E, 24>(a, sh, ordering, wf, ncells, st);
+    case 28: return launch_sweep2d_t<E, 28>(a, sh, ordering, wf, ncells, st);
+    case 32: return launch_sweep2d_t<E, 32>(a, sh, ordering, wf, ncells, st);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_sweep2d(const SweepArgs& a, const SweepShape& sh, int arith, int ordering, int wf, int ncells,
+                           cudaStream_t st) {
+  if (arith == kSweepF64) return launch_sweep2d_e<double>(a, sh, ordering, wf, ncells, st);
+  if (arith == kSweepDF64) return launch_sweep2d_e<dfloat>(a, sh, ordering, wf, ncells, st);
+  return launch_sweep2d_e<float>(a, sh, ordering, wf, ncells, st);
 }
 
 template <typename E>
@@ -639,8 +964,8 @@ bool sweep_shape_valid(int N, const SweepShape& sh) {
   int K = N * N * N;
   if (sh.ept <= 0 || N % sh.ept != 0) return false;
   if (sh.cluster < 1 || sh.cluster > 16 || (sh.cluster & (sh.cluster - 1))) return false;
-  if (sh.tpb < 128 || sh.tpb > 256 || sh.tpb % 32) return false;
-  if (sh.tpb < 32 * ((8 * sh.cluster + 31) / 32)) return false;  // warps for the cluster gather
+  if (sh.tpb < 160 || sh.tpb > 256 || sh.tpb % 32) return false;
+  if (sh.tpb < 32 * ((kRedMax * sh.cluster + 31) / 32)) return false;  // warps for the cluster gather
   if ((long long)sh.cluster * sh.tpb * sh.ept < K) return false;
   int e[] = {2, 4, 8, 12, 16, 20, 24, 28, 32};
   for (int x : e)

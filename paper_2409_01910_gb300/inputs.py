@@ -149,3 +149,38 @@ def shock_128cells_32v(mach: float = 2.0) -> ShockWorkload:
     spheres, eps = 0.1, Rankine-Hugoniot inflow data on both sides."""
     up, down = rankine_hugoniot(mach)
     return ShockWorkload(f"shock1d_M{mach:g}_J128_N32_eps0.1", J=128, N=32, L=10.0, eps=0.1, up=up, down=down)
+
+
+@dataclass
+class CavityWorkload:
+    """2-D lid-driven cavity on [0, 1]^2: diffuse walls at temperature T_wall, the top wall
+    (y = 1) moving with speed lid along x; initial state the Maxwellian M(1, 0, T_wall)
+    sampled at the nodes in every cell."""
+
+    name: str
+    nx: int
+    ny: int
+    N: int
+    L: float
+    eps: float
+    lid: float = 0.5
+    T_wall: float = 1.0
+    tol: float = 1e-8
+
+    @property
+    def J(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def total_mass(self) -> float:
+        return 1.0  # density 1 on the unit square
+
+    def initial_state(self) -> np.ndarray:
+        M = sampled_maxwellian(self.N, self.L, 1.0, (0.0, 0.0, 0.0), self.T_wall)
+        return np.ascontiguousarray(np.repeat(M[None], self.J, 0))
+
+
+def cavity_64x64_24v() -> CavityWorkload:
+    """64 x 64 cells, 24^3 velocities on [-6, 6]^3, Maxwell molecules, eps = 0.05, lid speed
+    0.5, walls at T = 1."""
+    return CavityWorkload("cavity2d_64x64_N24_eps0.05", nx=64, ny=64, N=24, L=6.0, eps=0.05)

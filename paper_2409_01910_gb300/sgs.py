@@ -37,12 +37,15 @@ class _Problem(C.Structure):
         ("nx", C.c_int),
         ("x_lo", C.c_double),
         ("x_hi", C.c_double),
+        ("ny", C.c_int),
+        ("y_lo", C.c_double),
+        ("y_hi", C.c_double),
         ("nv", C.c_int),
         ("v_max", C.c_double),
         ("collision", C.c_int),
         ("b0", C.c_double),
         ("eps", C.c_double),
-        ("bc", _BC * 2),
+        ("bc", _BC * 4),
         ("total_mass", C.c_double),
         ("precision", C.c_int),
         ("inner_tol", C.c_double),
@@ -103,19 +106,35 @@ class Problem:
     newton_max: int = 50
     inner_method: int = PFP
     space_dim: int = 1
+    ny: int = 1
+    y_lo: float = 0.0
+    y_hi: float = 1.0
+    # y_lo, y_hi sides (2-D): kind, density, velocity, temperature
+    bc_kind_y: Sequence[int] = (DIFFUSE, DIFFUSE)
+    bc_rho_y: Sequence[float] = (1.0, 1.0)
+    bc_u_y: Sequence[Sequence[float]] = ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0))
+    bc_T_y: Sequence[float] = (1.0, 1.0)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * (self.ny if self.space_dim == 2 else 1)
 
     def c(self) -> _Problem:
         p = _Problem()
-        for name in ("space_dim", "nx", "x_lo", "x_hi", "nv", "v_max", "collision", "b0", "eps", "total_mass",
-                     "precision", "inner_tol", "inner_max", "inner_fixed", "newton_tol", "newton_max",
-                     "inner_method"):
+        for name in ("space_dim", "nx", "x_lo", "x_hi", "ny", "y_lo", "y_hi", "nv", "v_max", "collision", "b0",
+                     "eps", "total_mass", "precision", "inner_tol", "inner_max", "inner_fixed", "newton_tol",
+                     "newton_max", "inner_method"):
             setattr(p, name, getattr(self, name))
-        for s in range(2):
-            p.bc[s].kind = self.bc_kind[s]
-            p.bc[s].rho = self.bc_rho[s]
-            p.bc[s].T = self.bc_T[s]
+        kinds = list(self.bc_kind) + list(self.bc_kind_y)
+        rhos = list(self.bc_rho) + list(self.bc_rho_y)
+        us = list(self.bc_u) + list(self.bc_u_y)
+        Ts = list(self.bc_T) + list(self.bc_T_y)
+        for s in range(4):
+            p.bc[s].kind = kinds[s]
+            p.bc[s].rho = rhos[s]
+            p.bc[s].T = Ts[s]
             for d in range(3):
-                p.bc[s].u[d] = self.bc_u[s][d]
+                p.bc[s].u[d] = us[s][d]
         return p
 
 
@@ -140,6 +159,7 @@ def lib(build: bool = True):
             "sgs_collide_prec": (C.c_int, [vp, vp, vp, vp, C.c_int, vp]),
             "sgs_sweep_forward": (C.c_int, [vp, vp, vp, vp, vp]),
             "sgs_sweep_backward": (C.c_int, [vp, vp, vp, vp, vp]),
+            "sgs_sweep_ordering": (C.c_int, [vp, vp, vp, vp, C.c_int, vp]),
             "sgs_rescale": (C.c_int, [vp, vp, vp]),
             "sgs_residual": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "sgs_iterate": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, vp, vp]),
@@ -248,6 +268,10 @@ class Solver:
 
     def sweep_backward(self, f, P, rhs=None, stream=None):
         _check(lib().sgs_sweep_backward(self.h, _ptr(f), _ptr(P), _ptr(rhs), _stream(stream)), "sgs_sweep_backward")
+
+    def sweep_ordering(self, f, P, ordering, rhs=None, stream=None):
+        _check(lib().sgs_sweep_ordering(self.h, _ptr(f), _ptr(P), _ptr(rhs), ordering, _stream(stream)),
+               "sgs_sweep_ordering")
 
     def rescale(self, f, stream=None):
         _check(lib().sgs_rescale(self.h, _ptr(f), _stream(stream)), "sgs_rescale")

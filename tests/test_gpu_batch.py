@@ -150,7 +150,7 @@ def test_autotuned_shape_keeps_oracle_parity(oracle):
     t = s.autotune(scratch, P, reps=1)
     assert t["candidates"] >= 2 and t["sweep_ms"] > 0
     assert (t["sweep_ept"], t["sweep_cluster"], t["sweep_threads"]) == s.sweep_shape()
-    for shape in (s.sweep_shape(), (2, 2, 128), (4, 1, 128)):
+    for shape in (s.sweep_shape(), (2, 2, 160), (4, 1, 160)):
         s.set_sweep_shape(*shape)
         f = torch.from_numpy(f0.reshape(-1)).cuda()
         s.collide(f, Q, P)

@@ -51,9 +51,23 @@ def test_problem_validation_on_host(L):
         q = sgs.Problem(**bad)
         arr = (sgs._Problem * 1)(q.c())
         assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.ERR_ARG, bad
-    q = sgs.Problem(space_dim=2)
+    q = sgs.Problem(space_dim=3)
     arr = (sgs._Problem * 1)(q.c())
-    assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.ERR_UNSUPPORTED
+    assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.ERR_ARG
+    # 2-D: one instance per handle; y extent and y walls validated
+    q2 = sgs.Problem(space_dim=2, nx=4, ny=3)
+    arr = (sgs._Problem * 2)(q2.c(), q2.c())
+    assert L.sgs_setup(arr, 2, C.byref(h), C.byref(ws)) == sgs.ERR_UNSUPPORTED
+    for bad in (dict(ny=0), dict(y_hi=-1.0), dict(bc_T_y=(1.0, 0.0))):
+        arr = (sgs._Problem * 1)(sgs.Problem(**{"space_dim": 2, "nx": 4, "ny": 3, **bad}).c())
+        assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.ERR_ARG, bad
+    arr = (sgs._Problem * 1)(sgs.Problem(space_dim=2, nx=4, ny=3, bc_u_y=((0, 0, 0), (0, 0.2, 0))).c())
+    assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.ERR_UNSUPPORTED  # normal wall velocity
+    arr = (sgs._Problem * 1)(sgs.Problem(space_dim=2, nx=4, ny=3).c())
+    assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.OK
+    off, J, nv = C.c_size_t(), C.c_int(), C.c_int()
+    assert L.sgs_layout(h, 0, C.byref(off), C.byref(J), C.byref(nv)) == sgs.OK and J.value == 12
+    L.sgs_destroy(h)
     assert L.sgs_strerror(sgs.ERR_WORKSPACE).decode().startswith("workspace")
 
 
@@ -95,8 +109,8 @@ def test_batch_api_on_host(L):
     assert L.sgs_setup(arr, 2, C.byref(h), C.byref(ws)) == sgs.OK
     e, c, t = C.c_int(), C.c_int(), C.c_int()
     assert L.sgs_get_sweep_shape(h, C.byref(e), C.byref(c), C.byref(t)) == sgs.OK
-    # every node of a cell has an owner thread; warps 0-3 exist for the Newton evaluations
-    assert 16 % e.value == 0 and c.value in (1, 2, 4, 8, 16) and 128 <= t.value <= 256 and t.value % 32 == 0
+    # every node of a cell has an owner thread; warps 0-4 exist for the Newton evaluations
+    assert 16 % e.value == 0 and c.value in (1, 2, 4, 8, 16) and 160 <= t.value <= 256 and t.value % 32 == 0
     assert e.value * c.value * t.value >= 16**3
     assert L.sgs_get_sweep_shape(h, None, C.byref(c), C.byref(t)) == sgs.ERR_ARG
     # nothing is enqueued before a workspace is bound
