@@ -57,9 +57,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-t2tol", action="store_true", help="skip the time-to-residual runs")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default scan shape")
     ap.add_argument("--t2tol-all", action="store_true", help="also time the plain FP64 SGS form to 1e-8")
     ap.add_argument("--t2tol-cap", type=float, default=150.0, help="seconds allowed per time-to-residual run")
-    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf"], default=None,
+    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d"], default=None,
                     help="run a small case of one kernel class (for profiler captures) and exit")
     return ap.parse_args()
 
@@ -204,6 +205,15 @@ def run_native(args, rank, world, local):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     visits_per_step = visits_per_iteration(wl)
 
+    # scan-shape autotuner (untimed, on a scratch copy of the state): keeps the fastest shape
+    tuning = None
+    if not args.no_autotune:
+        g, Qt, Pt = f0.clone(), s.field(), s.field()
+        s.collide(g, Qt, Pt)
+        tuning = s.autotune(g, Pt, reps=1)
+        del g, Qt, Pt
+        s.reset_stats()
+
     def step(i):
         if i % args.dc_every == 0:
             s.dc_step(f, Q, P, 0, res=res_hi)
@@ -259,7 +269,7 @@ def run_native(args, rank, world, local):
     t2tol = None
     if world == 1 and not args.no_t2tol:
         kinds = ["mixed_mg", "mixed_sgs", "fp64_mg"] + (["fp64_sgs"] if args.t2tol_all else [])
-        t2tol = {k: time_to_tol(wl, f0, dev, k, args.t2tol_cap) for k in kinds}
+        t2tol = {k: time_to_tol(wl, f0, dev, k, args.t2tol_cap, shape=s.sweep_shape()) for k in kinds}
 
     out = None
     if rank == 0:
@@ -285,6 +295,9 @@ def run_native(args, rank, world, local):
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "roofline_kernels": roofs,
+            "scan_shape": {"nodes_per_thread": s.sweep_shape()[0], "ctas_per_cluster": s.sweep_shape()[1],
+                           "threads_per_cta": s.sweep_shape()[2],
+                           "chosen_by": "autotuner" if tuning else "default", "tuning": tuning},
             "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
             "e2e": e2e,
             "clocks": clocks,
@@ -369,7 +382,7 @@ def roofline(cls, prof, wl, sm_mhz):
             "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs ({src})"}
 
 
-def time_to_tol(wl, f0, dev, kind, cap_s, tol=1e-8):
+def time_to_tol(wl, f0, dev, kind, cap_s, tol=1e-8, shape=None):
     """Seconds from the initial state until the FP64 residual falls below tol.
 
     kinds: mixed_sgs (defect correction every 10 SGS iterations), mixed_mg (defect
@@ -380,6 +393,8 @@ def time_to_tol(wl, f0, dev, kind, cap_s, tol=1e-8):
     from paper_2409_01910_gb300 import sgs
 
     s = make_solver(wl, sgs.FP32 if kind.startswith("mixed") else sgs.FP64)
+    if shape is not None and kind.startswith("mixed"):
+        s.set_sweep_shape(*shape)  # the bench handle's autotuned shape (same arithmetic)
     levels = 4 if is_shock(wl) else (3 if is_cavity(wl) else 2)  # shock 128/64/32/16; cavity 64^2/32^2/16^2
     f = f0.clone()
     Q, P = s.field(), s.field()
@@ -563,11 +578,23 @@ def run_reference(args, rank, world):
 
 def profile_case(which):
     """Small instance of one kernel class for ncu: the persistent scan on 4 cells, or the
-    spectral sum on 32 cells (one lane group), both on the 32^3 grid of the workload."""
+    spectral sum on 32 cells (one lane group), both on the 32^3 grid of the workload; or
+    one 2-D scan ordering of an 8 x 8 cavity on the 24^3 grid of the cavity workload."""
     import torch
 
     from paper_2409_01910_gb300 import inputs as I
     from paper_2409_01910_gb300 import sgs
+
+    if which == "sweep2d":
+        w = I.CavityWorkload("cavity2d_8x8_N24", nx=8, ny=8, N=24, L=6.0, eps=0.05)
+        s = make_solver(w, sgs.FP32)
+        f = torch.from_numpy(w.initial_state().reshape(-1)).cuda()
+        Q, P = s.field(), s.field()
+        s.collide(f, Q, P)
+        s.sweep_ordering(f, P, 0)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": which, "status": s.read_status()}))
+        return
 
     J = 4 if which == "sweep" else 32
     p = sgs.Problem(nx=J, nv=32, v_max=8.0, eps=0.01, bc_T=(1.0, 1.8), total_mass=1.0,
