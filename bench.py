@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default scan shape")
     ap.add_argument("--t2tol-all", action="store_true", help="also time the plain FP64 SGS form to 1e-8")
     ap.add_argument("--t2tol-cap", type=float, default=150.0, help="seconds allowed per time-to-residual run")
-    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d"], default=None,
+    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d", "dft"], default=None,
                     help="run a small case of one kernel class (for profiler captures) and exit")
     return ap.parse_args()
 
@@ -704,6 +704,17 @@ def profile_case(which):
     from paper_2409_01910_gb300 import inputs as I
     from paper_2409_01910_gb300 import sgs
 
+    if which == "dft":
+        # the transforms of the mixed solver's increment-form collision on the 64-cell workload
+        wl = I.heat_64cells_32v()
+        s = make_solver(wl, sgs.FP32)
+        f = torch.from_numpy(wl.initial_state().reshape(-1)).cuda()
+        Q, P = s.field(), s.field()
+        s.dc_step(f, Q, P, 0)
+        s.collide(f, Q, P)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": which, "status": s.read_status()}))
+        return
     if which == "sweep2d":
         w = I.CavityWorkload("cavity2d_8x8_N24", nx=8, ny=8, N=24, L=6.0, eps=0.05)
         s = make_solver(w, sgs.FP32)

@@ -84,6 +84,14 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ f, C
 }
 
 // Per-block factors E_d[i] of the discrete Maxwellian of cell c (E_1 carries exp(alpha)).
+__device__ inline void maxwell_factors(const double* theta, int c, int N, double dv, double* E /*[3][kMaxN]*/);
+
+// Separable factors of every cell's Maxwellian, once per collision step (one block per
+// cell), for the transform passes to read instead of re-evaluating 3N exponentials per block.
+__global__ void k_factors(const double* theta, int N, double dv, double* efac) {
+  maxwell_factors(theta, blockIdx.x, N, dv, efac + (long long)blockIdx.x * 3 * kMaxN);
+}
+
 __device__ inline void maxwell_factors(const double* theta, int c, int N, double dv, double* E /*[3][kMaxN]*/) {
   if (threadIdx.x < 3 * N) {
     int d = threadIdx.x / N, i = threadIdx.x % N;
@@ -100,35 +108,45 @@ __device__ inline void maxwell_factors(const double* theta, int c, int N, double
 // Pass 1 (index 3) forms a = f - M and b = f + M in FP64 and transforms them in T.
 // ---------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_dft_i3(const double* __restrict__ f, CellTables ct, const double* theta,
-                                                 SpecBufs<T> sb, int N, double dv, DftMode md) {
+__global__ void __launch_bounds__(256) k_dft_i3(const double* __restrict__ f, CellTables ct, const double* efac,
+                                                 const double* efac_ref, SpecBufs<T> sb, int N, double dv,
+                                                 DftMode md) {
   extern __shared__ __align__(16) unsigned char smraw[];
   int n = N - 1;
-  T* cs = (T*)smraw;             // [n][N] cos
-  T* sn = cs + n * N;            // [n][N] sin
+  T* cs = (T*)smraw;             // [N][n] cos, transposed: k3 fastest, so that the threads of
+  T* sn = cs + n * N;            // [N][n] sin  a warp (consecutive k3) read consecutive banks
   T* sa = sn + n * N;            // [N][N] a slab (i2, i3)
   T* sbb = sa + N * N;           // [N][N] b slab
-  __shared__ double E[3 * kMaxN];
-  __shared__ double Er[3 * kMaxN];
+  // M = E1[i1] E2[i2] E3[i3]: E12[i2] = E1[i1] E2[i2] for this block's i1, then one product
+  __shared__ double E12[kMaxN], E3[kMaxN], E12r[kMaxN], E3r[kMaxN];
   int c = blockIdx.x, i1 = blockIdx.y;
-  maxwell_factors(theta, c, N, dv, E);
-  if (md.mode != 0) maxwell_factors(md.theta_ref, c, N, dv, Er);
+  if (threadIdx.x < N) {
+    const double* e = efac + (long long)c * 3 * kMaxN;
+    E12[threadIdx.x] = e[i1] * e[kMaxN + threadIdx.x];
+    E3[threadIdx.x] = e[2 * kMaxN + threadIdx.x];
+    if (md.mode != 0) {
+      const double* er = efac_ref + (long long)c * 3 * kMaxN;
+      E12r[threadIdx.x] = er[i1] * er[kMaxN + threadIdx.x];
+      E3r[threadIdx.x] = er[2 * kMaxN + threadIdx.x];
+    }
+  }
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
-    cs[t] = (T)sb.tw_cos[t];
-    sn[t] = (T)sb.tw_sin[t];
+    int k3 = t / N, i3 = t % N;
+    cs[i3 * n + k3] = sb.twc[t];
+    sn[i3 * n + k3] = sb.tws[t];
   }
   __syncthreads();
   const long long off = ct.cell_off[c] + (long long)i1 * N * N;
   const double* fc = f + off;
   for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
     int i2 = t / N, i3 = t % N;
-    double M = E[i1] * E[kMaxN + i2] * E[2 * kMaxN + i3];
+    double M = E12[i2] * E3[i3];
     double x = fc[t];
     if (md.mode == 0) {  // a = f - M, b = f + M
       sa[t] = (T)(x - M);
       sbb[t] = (T)(x + M);
     } else {  // increments against the reference state f_ref, M_ref (exact in FP64, then rounded)
-      double Mr = Er[i1] * Er[kMaxN + i2] * Er[2 * kMaxN + i3];
+      double Mr = E12r[i2] * E3r[i3];
       double xr = md.f_ref[off + t];
       if (md.mode == 1) {  // a = (f - M) - (f_ref - M_ref), b = f + M
         sa[t] = (T)((x - xr) - (M - Mr));
@@ -147,7 +165,7 @@ __global__ void __launch_bounds__(256) k_dft_i3(const double* __restrict__ f, Ce
     int i2 = t / n, k3 = t % n;
     T ar = 0, ai = 0, br = 0, bi = 0;
     for (int i3 = 0; i3 < N; i3++) {
-      T co = cs[k3 * N + i3], si = sn[k3 * N + i3];
+      T co = cs[i3 * n + k3], si = sn[i3 * n + k3];
       T a = sa[i2 * N + i3], b = sbb[i2 * N + i3];
       ar += a * co;
       ai -= a * si;
@@ -171,8 +189,8 @@ __global__ void __launch_bounds__(256) k_dft_i2(SpecBufs<T> sb, int N) {
   CT* xb = xa + N * n;
   int c = blockIdx.x, i1 = blockIdx.y;
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
-    cs[t] = (T)sb.tw_cos[t];
-    sn[t] = (T)sb.tw_sin[t];
+    cs[t] = sb.twc[t];
+    sn[t] = sb.tws[t];
   }
   const CT* ia = sb.st1a + ((long long)c * N + i1) * N * n;
   const CT* ib = sb.st1b + ((long long)c * N + i1) * N * n;
@@ -211,8 +229,8 @@ __global__ void __launch_bounds__(256) k_dft_i1(SpecBufs<T> sb, int N) {
   CT* xb = xa + N * n;
   int c = blockIdx.x, k2 = blockIdx.y;
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
-    cs[t] = (T)sb.tw_cos[t];
-    sn[t] = (T)sb.tw_sin[t];
+    cs[t] = sb.twc[t];
+    sn[t] = sb.tws[t];
   }
   for (int t = threadIdx.x; t < N * n; t += blockDim.x) {
     int i1 = t / n, k3 = t % n;
@@ -590,8 +608,8 @@ __global__ void __launch_bounds__(256) k_idft_k1(SpecBufs<T> sb, int N) {
   int c = blockIdx.x, k2 = blockIdx.y;
   int g = c / kLanes, lane = c % kLanes;
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
-    cs[t] = (T)sb.tw_cos[t];
-    sn[t] = (T)sb.tw_sin[t];
+    cs[t] = sb.twc[t];
+    sn[t] = sb.tws[t];
   }
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     int k1 = t / n, k3 = t % n;
@@ -622,8 +640,8 @@ __global__ void __launch_bounds__(256) k_idft_k2(SpecBufs<T> sb, int N) {
   CT* x = (CT*)(sn + n * N);  // [k2][k3]
   int c = blockIdx.x, i1 = blockIdx.y;
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
-    cs[t] = (T)sb.tw_cos[t];
-    sn[t] = (T)sb.tw_sin[t];
+    cs[t] = sb.twc[t];
+    sn[t] = sb.tws[t];
   }
   const CT* src = sb.st2a + ((long long)c * N + i1) * n * n;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) x[t] = src[t];
@@ -645,7 +663,7 @@ __global__ void __launch_bounds__(256) k_idft_k2(SpecBufs<T> sb, int N) {
 // Last pass: real part along index 3, then Q and P = Q - nu (M - f) in FP64.
 template <typename T>
 __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* __restrict__ f, CellTables ct,
-                                                  const double* theta, const double* nu, double* Q, double* P,
+                                                  const double* efac, const double* nu, double* Q, double* P,
                                                   int N, double dv, const double* __restrict__ Qadd) {
   typedef typename CplxOf<T>::type CT;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -653,12 +671,16 @@ __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* _
   T* cs = (T*)smraw;
   T* sn = cs + n * N;
   CT* x = (CT*)(sn + n * N);  // [i2][k3]
-  __shared__ double E[3 * kMaxN];
+  __shared__ double E12[kMaxN], E3[kMaxN];
   int c = blockIdx.x, i1 = blockIdx.y;
-  maxwell_factors(theta, c, N, dv, E);
+  if (threadIdx.x < N) {
+    const double* e = efac + (long long)c * 3 * kMaxN;
+    E12[threadIdx.x] = e[i1] * e[kMaxN + threadIdx.x];
+    E3[threadIdx.x] = e[2 * kMaxN + threadIdx.x];
+  }
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
-    cs[t] = (T)sb.tw_cos[t];
-    sn[t] = (T)sb.tw_sin[t];
+    cs[t] = sb.twc[t];
+    sn[t] = sb.tws[t];
   }
   const CT* src = sb.st1a + ((long long)c * N + i1) * N * n;
   for (int t = threadIdx.x; t < N * n; t += blockDim.x) x[t] = src[t];
@@ -676,7 +698,7 @@ __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* _
     if (Qadd) q += Qadd[base + t];
     if (Q) Q[base + t] = q;
     if (P) {
-      double M = E[i1] * E[kMaxN + i2] * E[2 * kMaxN + i3];
+      double M = E12[i2] * E3[i3];
       P[base + t] = q - nuc * (M - f[base + t]);
     }
   }
@@ -829,10 +851,12 @@ template <typename T>
 cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, const DftMode& md, cudaStream_t st) {
   int N = x.N, n = N - 1, C = x.C;
   cudaError_t e;
+  k_factors<<<C, 3 * N, 0, st>>>(x.theta, N, x.dv, x.efac);
+  if (md.mode != 0) k_factors<<<C, 3 * N, 0, st>>>(md.theta_ref, N, x.dv, x.efac_ref);
   size_t sm1 = dft_smem<T>(N, 0, 2 * N * N);
   e = func_attr((const void*)k_dft_i3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
   if (e != cudaSuccess) return e;
-  k_dft_i3<T><<<dim3(C, N), 256, sm1, st>>>(f, x.ct, x.theta, x.sb, N, x.dv, md);
+  k_dft_i3<T><<<dim3(C, N), 256, sm1, st>>>(f, x.ct, x.efac, x.efac_ref, x.sb, N, x.dv, md);
   size_t sm2 = dft_smem<T>(N, 2 * N * n, 0);
   e = func_attr((const void*)k_dft_i2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   if (e != cudaSuccess) return e;
@@ -869,7 +893,8 @@ cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const Coll
   size_t sm4 = dft_smem<T>(N, N * n, 0);
   e = func_attr((const void*)k_idft_k3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
   if (e != cudaSuccess) return e;
-  k_idft_k3<T><<<dim3(C, N), 256, sm4, st>>>(x.sb, f, x.ct, x.theta, x.nu, Q, P, N, x.dv, Qadd);
+  // the factors of this collision step were written by launch_dft
+  k_idft_k3<T><<<dim3(C, N), 256, sm4, st>>>(x.sb, f, x.ct, x.efac, x.nu, Q, P, N, x.dv, Qadd);
   return cudaGetLastError();
 }
 

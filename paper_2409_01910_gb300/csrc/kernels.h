@@ -47,6 +47,8 @@ struct SpecBufs {
   typedef typename CplxOf<T>::type CT;
   const double* tw_cos;  // [n][N] cos(2 pi k j / N), k = row - h, j = i - N/2 + 1
   const double* tw_sin;  // [n][N] sin(2 pi k j / N)
+  const T* twc;          // the same tables in T (precomputed: no conversion in the kernels)
+  const T* tws;
   CT *st1a, *st1b;       // [C][N][N][n]
   CT *st2a, *st2b;       // [C][N][n][n]
   CT *ahat, *bhat;       // [G][n][n][n][32]
@@ -110,6 +112,8 @@ struct CollideCtx {
   CellTables ct;
   const double* theta;
   const double* nu;
+  double* efac;           // [C][3][kMaxN] separable factors of each cell's Maxwellian
+  double* efac_ref;       // the same for the reference state (increment modes)
   SpecBufs<T> sb;
   SumArgs<T> sum;
   RedArgs<T> red;

@@ -99,7 +99,7 @@ struct sgs_handle {
   struct {
     size_t inst, cell_off, cell_inst, cnt, theta, nu, scratch, tw_cos, tw_sin, G, Lo, units, step0, row_k, row_start,
         row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, partial2, f_ref, Q_ref, theta_ref,
-        ahat_ref, active, W32lo, end;
+        ahat_ref, active, W32lo, tw_cos32, tw_sin32, efac, efac_ref, end;
   } off;
   bool dc_ref = false;  // FP32 collisions use the increment form against the stored reference
   int dc_prec = SGS_DF64;  // arithmetic of the high-precision evaluation in sgs_dc_step
@@ -246,6 +246,10 @@ void layout(sgs_handle* h) {
   f.scratch = take(sizeof(double) * (2 * h->n_inst + 2 * C + 2 * (h->inst[0].nx + h->inst[0].ny) + 64));
   f.tw_cos = take(sizeof(double) * n * N);
   f.tw_sin = take(sizeof(double) * n * N);
+  f.tw_cos32 = take(sizeof(float) * n * N);
+  f.tw_sin32 = take(sizeof(float) * n * N);
+  f.efac = take(sizeof(double) * 3 * kMaxN * C);      // per-cell Maxwellian factors (finest level
+  f.efac_ref = take(sizeof(double) * 3 * kMaxN * C);  // is the largest) and those of the reference
   bool sp = h->spectral;
   size_t U = h->units.size();
   f.G = take(sp ? sizeof(double) * h->na * h->nb : 0);
@@ -470,6 +474,10 @@ CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0) {
   x.nu = h->at<double>(h->off.nu);
   x.sb.tw_cos = h->at<double>(h->off.tw_cos);
   x.sb.tw_sin = h->at<double>(h->off.tw_sin);
+  x.sb.twc = sizeof(T) == 8 ? h->at<T>(h->off.tw_cos) : h->at<T>(h->off.tw_cos32);
+  x.sb.tws = sizeof(T) == 8 ? h->at<T>(h->off.tw_sin) : h->at<T>(h->off.tw_sin32);
+  x.efac = h->at<double>(h->off.efac);
+  x.efac_ref = h->at<double>(h->off.efac_ref);
   x.sb.st1a = h->at<CT>(h->off.st1a);
   x.sb.st1b = h->at<CT>(h->off.st1b);
   x.sb.st2a = h->at<CT>(h->off.st2a);
@@ -517,7 +525,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
   auto run = [&](auto x) -> int {
     cudaError_t er;
     {
-      Scope sc(h, SGS_PROF_DFT, st, 3);
+      Scope sc(h, SGS_PROF_DFT, st, 4);
       er = launch_dft(f, x, DftMode{0, nullptr, nullptr}, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
@@ -540,7 +548,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     CT* part2 = h->at<CT>(h->off.partial2);
     cudaError_t er;
     {
-      Scope sc(h, SGS_PROF_DFT, st, 3);
+      Scope sc(h, SGS_PROF_DFT, st, 5);
       er = launch_dft(f, x, m1, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
@@ -550,7 +558,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     {
-      Scope sc(h, SGS_PROF_DFT, st, 3);
+      Scope sc(h, SGS_PROF_DFT, st, 5);
       er = launch_dft(f, x, m2, st);
       if (er == cudaSuccess)
         er = cudaMemcpyAsync(x.sb.ahat, h->at<CT>(Lv.rah),
@@ -570,7 +578,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     CollideCtx<double> x = collide_ctx<double>(h, l);
     cudaError_t er;
     {
-      Scope sc(h, SGS_PROF_DFT, st, 5);
+      Scope sc(h, SGS_PROF_DFT, st, 6);
       er = launch_dft(f, x, DftMode{0, nullptr, nullptr}, st);
       const long long cnt = (long long)h->lev[l].G * h->n * h->n * h->n * kLanes;
       if (er == cudaSuccess) er = launch_split_spec(x.sb.ahat, cnt, st);
@@ -920,6 +928,9 @@ int sgs_bind_workspace(sgs_handle* h, void* device_ptr, size_t bytes) {
   SGS_UP(cell_inst, h->cell_inst);
   SGS_UP(tw_cos, h->tw_cos);
   SGS_UP(tw_sin, h->tw_sin);
+  std::vector<float> twc32(h->tw_cos.begin(), h->tw_cos.end()), tws32(h->tw_sin.begin(), h->tw_sin.end());
+  SGS_UP(tw_cos32, twc32);
+  SGS_UP(tw_sin32, tws32);
   SGS_UP(G, h->Gtab);
   SGS_UP(Lo, h->Lo);
   SGS_UP(units, u4);
@@ -1039,7 +1050,7 @@ int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, int lo_iters, do
   if (e != cudaSuccess) return cuda_status(e);
   {
     CollideCtx<float> x = collide_ctx<float>(h);
-    Scope sc(h, SGS_PROF_DFT, st, 3);
+    Scope sc(h, SGS_PROF_DFT, st, 4);
     e = launch_dft(f, x, DftMode{0, nullptr, nullptr}, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h->ws + h->off.ahat_ref, x.sb.ahat,
