@@ -62,6 +62,7 @@ class _Problem(C.Structure):
         ("newton_tol", C.c_double),
         ("newton_max", C.c_int),
         ("inner_method", C.c_int),
+        ("conserve_proj", C.c_int),
     ]
 
 
@@ -102,6 +103,7 @@ class Problem:
     newton_tol: float = 1e-10
     newton_max: int = 50
     inner_method: int = PFP
+    conserve_proj: int = 0
 
     @property
     def dx(self) -> float:
@@ -110,7 +112,7 @@ class Problem:
     def c(self) -> _Problem:
         p = _Problem()
         for name in ("N", "L", "kernel", "b0", "J", "x_lo", "x_hi", "eps", "total_mass", "inner_tol",
-                     "inner_max", "inner_fixed", "newton_tol", "newton_max", "inner_method"):
+                     "inner_max", "inner_fixed", "newton_tol", "newton_max", "inner_method", "conserve_proj"):
             setattr(p, name, getattr(self, name))
         for s in range(2):
             p.bc_kind[s] = self.bc_kind[s]
@@ -189,6 +191,7 @@ def lib():
             "or_qhat_direct": (None, [C.c_int, C.c_double, C.c_int, C.c_double, d, d, d]),
             "or_qfsm": (None, [C.c_int, C.c_double, C.c_int, C.c_double, d, d]),
             "or_moments": (None, [C.c_int, C.c_double, d, d]),
+            "or_conserve_project": (C.c_int, [C.c_int, C.c_double, d]),
             "or_discrete_maxwellian": (C.c_int, [C.c_int, C.c_double, d, d, d, C.c_int, C.c_double, C.c_int]),
             "or_eval_maxwellian": (None, [C.c_int, C.c_double, d, d]),
             "or_collision_frequency": (C.c_double, [P, d]),
@@ -280,6 +283,14 @@ def moments(f, L):
     m = np.empty(5)
     lib().or_moments(f.shape[0], L, _p(_arr(f)), _p(m))
     return m
+
+
+def conserve_project(q, L):
+    """Conservation projection of one cell's q (N, N, N); returns a new array."""
+    out = _arr(q).copy()
+    if lib().or_conserve_project(q.shape[0], L, _p(out)) != 0:
+        raise ArithmeticError("singular Gram matrix")
+    return out
 
 
 def discrete_maxwellian(N, L, target, wk=None, theta0=None, tol=1e-10, maxit=50):

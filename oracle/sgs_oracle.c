@@ -544,10 +544,48 @@ double or_collision_frequency(const or_problem* p, const double* f) {
 }
 
 /* ------------------------------------------------------------------------------------
+ * Conservation projection (not in the paper, whose Fourier-spectral Q conserves mass to
+ * round-off but momentum and energy only to spectral accuracy). With C = [w phi_i(v_k)]
+ * (5 x K), the smallest Euclidean change of q that makes C q = 0 is
+ *   q_c = q - C^T (C C^T)^{-1} C q;
+ * the uniform weight w cancels, so lambda solves (sum_k phi phi^T) lambda = sum_k phi q
+ * and q_c = q - sum_i lambda_i phi_i. Written out over the nodes in plain loops.
+ * ---------------------------------------------------------------------------------- */
+int or_conserve_project(int N, double L, double* q) {
+  double* v = (double*)malloc(sizeof(double) * N);
+  or_velocity_nodes(N, L, v);
+  double A[25], s[5], lam[5];
+  memset(A, 0, sizeof(A));
+  memset(s, 0, sizeof(s));
+  long t = 0;
+  for (int i1 = 0; i1 < N; i1++)
+    for (int i2 = 0; i2 < N; i2++)
+      for (int i3 = 0; i3 < N; i3++, t++) {
+        double phi[5] = {1.0, v[i1], v[i2], v[i3], v[i1] * v[i1] + v[i2] * v[i2] + v[i3] * v[i3]};
+        for (int a = 0; a < 5; a++) {
+          s[a] += phi[a] * q[t];
+          for (int b = 0; b < 5; b++) A[a * 5 + b] += phi[a] * phi[b];
+        }
+      }
+  int ok = chol5(A, s, lam);
+  if (ok == 0) {
+    t = 0;
+    for (int i1 = 0; i1 < N; i1++)
+      for (int i2 = 0; i2 < N; i2++)
+        for (int i3 = 0; i3 < N; i3++, t++) {
+          double phi[5] = {1.0, v[i1], v[i2], v[i3], v[i1] * v[i1] + v[i2] * v[i2] + v[i3] * v[i3]};
+          for (int a = 0; a < 5; a++) q[t] -= lam[a] * phi[a];
+        }
+  }
+  free(v);
+  return ok;
+}
+
+/* ------------------------------------------------------------------------------------
  * Steady-state-preserving collision term (eq. (16)):
  *   Q = Q^FSM[f, f] - Q^FSM[M[f], M[f]]
  * and the BGK penalty split P = Q - nu (M - f) (eq. (28)). BGK mode: Q = nu (M - f),
- * P = 0 (eq. (12)).
+ * P = 0 (eq. (12)). With conserve_proj, Q is projected (above) before P is formed.
  * ---------------------------------------------------------------------------------- */
 void or_collide_cell(const or_problem* p, const double* f, double* Q, double* P, double* nu_out, double* theta_out) {
   int N = p->N;
@@ -569,6 +607,7 @@ void or_collide_cell(const or_problem* p, const double* f, double* Q, double* P,
     or_qfsm(N, p->L, p->kernel, p->b0, M, qm);
     for (long i = 0; i < K; i++) q[i] -= qm[i];
     free(qm);
+    if (p->conserve_proj) or_conserve_project(N, p->L, q);
   }
   if (Q) memcpy(Q, q, sizeof(double) * K);
   if (P) {

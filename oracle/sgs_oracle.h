@@ -40,6 +40,7 @@ typedef struct {
   double inner_tol; int inner_max, inner_fixed;
   double newton_tol; int newton_max;
   int inner_method;    /* OR_PFP or OR_FP */
+  int conserve_proj;   /* 1: project Q onto the zero-moment subspace (not in the paper) */
 } or_problem;
 
 typedef struct {
@@ -60,6 +61,9 @@ void or_idft(int N, const double* qhat, double* q);
 void or_qhat_direct(int N, double L, int kernel, double b0, const double* ahat, const double* bhat, double* qhat);
 /* Q^FSM[f, f] on the velocity nodes. */
 void or_qfsm(int N, double L, int kernel, double b0, const double* f, double* q);
+/* Orthogonal projection of q (in place) onto {q : sum_k phi_i(v_k) q_k = 0, i = 0..4},
+ * phi = (1, v1, v2, v3, |v|^2). Returns 0, or -1 if the 5x5 Gram matrix is singular. */
+int or_conserve_project(int N, double L, double* q);
 /* Moments (rho, rho*U, sum w|v|^2 f) with weights w. */
 void or_moments(int N, double L, const double* f, double* m5);
 /* Discrete Maxwellian exp(alpha + beta.v - gamma|v|^2) matching weighted moments.
