@@ -90,6 +90,12 @@ typedef struct {
   double newton_tol;  /* exponent-change tolerance of the Maxwellian Newton, e.g. 1e-10 */
   int newton_max;     /* e.g. 50 */
   int inner_method;   /* SGS_PFP (eqs. (24)-(25)) or SGS_FP (eq. (22)) */
+  int conserve_proj;  /* 0: the paper's Q (mass conserved to round-off, momentum and energy to
+                         spectral accuracy); 1: Q projected in FP64 onto the zero-moment
+                         subspace, Q_c = Q - C^T (C C^T)^-1 C Q with C = [w phi_i(v_k)],
+                         phi = (1, v, |v|^2), applied in every collision step (all levels
+                         and precisions) before P = Q_c - nu (M - f) is formed. Not in the
+                         paper; equal in every instance of a handle; ignored for BGK. */
 } sgs_problem;
 
 /* Counters accumulated on the device since setup or the last sgs_reset_stats(). */

@@ -664,7 +664,8 @@ __global__ void __launch_bounds__(256) k_idft_k2(SpecBufs<T> sb, int N) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* __restrict__ f, CellTables ct,
                                                   const double* efac, const double* nu, double* Q, double* P,
-                                                  int N, double dv, const double* __restrict__ Qadd) {
+                                                  int N, double dv, const double* __restrict__ Qadd,
+                                                  double* __restrict__ mom) {
   typedef typename CplxOf<T>::type CT;
   extern __shared__ __align__(16) unsigned char smraw[];
   int n = N - 1;
@@ -687,6 +688,8 @@ __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* _
   __syncthreads();
   long long base = ct.cell_off[c] + (long long)i1 * N * N;
   double nuc = nu[c];
+  // moments of this slab for the conservation projection: sum q, v2 q, v3 q, (v2^2 + v3^2) q
+  double m0 = 0.0, m2 = 0.0, m3 = 0.0, m4 = 0.0;
   for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
     int i2 = t / N, i3 = t % N;
     T re = 0;
@@ -701,6 +704,76 @@ __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* _
       double M = E12[i2] * E3[i3];
       P[base + t] = q - nuc * (M - f[base + t]);
     }
+    if (mom) {
+      double v2 = (i2 - N / 2 + 1) * dv, v3 = (i3 - N / 2 + 1) * dv;
+      m0 += q;
+      m2 += v2 * q;
+      m3 += v3 * q;
+      m4 += (v2 * v2 + v3 * v3) * q;
+    }
+  }
+  if (mom) {  // fixed-order block reduction (warp butterflies, then warps in order)
+    __shared__ double red[4][8];
+    for (int o = 16; o > 0; o >>= 1) {
+      m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+      m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+      m3 += __shfl_xor_sync(0xffffffffu, m3, o);
+      m4 += __shfl_xor_sync(0xffffffffu, m4, o);
+    }
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      red[0][w] = m0;
+      red[1][w] = m2;
+      red[2][w] = m3;
+      red[3][w] = m4;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int j = 0; j < 4; j++)
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s[j] += red[j][k];
+      double v1 = (i1 - N / 2 + 1) * dv;
+      double* o = mom + ((long long)c * N + i1) * 5;
+      o[0] = s[0];
+      o[1] = v1 * s[0];
+      o[2] = s[1];
+      o[3] = s[2];
+      o[4] = v1 * v1 * s[0] + s[3];
+    }
+  }
+}
+
+// Conservation projection (an option; not in the paper): Q_c = Q - sum_i lambda_i phi_i
+// with (sum_k phi phi^T) lambda = sum_k phi Q, phi = (1, v1, v2, v3, |v|^2), applied to Q and
+// to P = Q - nu (M - f) alike. The moments come from the slabs of k_idft_k3, summed here in
+// i1 order (every block of a cell forms the same lambda); Ainv is the inverse Gram matrix.
+__global__ void __launch_bounds__(256) k_conserve_apply(const double* __restrict__ mom,
+                                                        const double* __restrict__ Ainv, CellTables ct, double* Q,
+                                                        double* P, int N, double dv) {
+  __shared__ double sm[5], lam[5];
+  int c = blockIdx.x, i1 = blockIdx.y;
+  if (threadIdx.x < 5) {
+    double a = 0.0;
+    const double* m = mom + (long long)c * N * 5 + threadIdx.x;
+    for (int j = 0; j < N; j++) a += m[j * 5];
+    sm[threadIdx.x] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double a = 0.0;
+    for (int k = 0; k < 5; k++) a += Ainv[threadIdx.x * 5 + k] * sm[k];
+    lam[threadIdx.x] = a;
+  }
+  __syncthreads();
+  double v1 = (i1 - N / 2 + 1) * dv;
+  double c0 = lam[0] + lam[1] * v1 + lam[4] * v1 * v1;
+  long long base = ct.cell_off[c] + (long long)i1 * N * N;
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    int i2 = t / N, i3 = t % N;
+    double v2 = (i2 - N / 2 + 1) * dv, v3 = (i3 - N / 2 + 1) * dv;
+    double corr = c0 + lam[2] * v2 + lam[3] * v3 + lam[4] * (v2 * v2 + v3 * v3);
+    if (Q) Q[base + t] -= corr;
+    if (P) P[base + t] -= corr;
   }
 }
 
@@ -894,7 +967,10 @@ cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const Coll
   e = func_attr((const void*)k_idft_k3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
   if (e != cudaSuccess) return e;
   // the factors of this collision step were written by launch_dft
-  k_idft_k3<T><<<dim3(C, N), 256, sm4, st>>>(x.sb, f, x.ct, x.efac, x.nu, Q, P, N, x.dv, Qadd);
+  k_idft_k3<T><<<dim3(C, N), 256, sm4, st>>>(x.sb, f, x.ct, x.efac, x.nu, Q, P, N, x.dv, Qadd, x.mom);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !x.mom) return e;
+  k_conserve_apply<<<dim3(C, N), 256, 0, st>>>(x.mom, x.cproj, x.ct, Q, P, N, x.dv);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,8 @@ struct CollideCtx {
   const double* nu;
   double* efac;           // [C][3][kMaxN] separable factors of each cell's Maxwellian
   double* efac_ref;       // the same for the reference state (increment modes)
+  double* mom;            // [C][N][5] moments of Q per slab (conservation projection), or null
+  const double* cproj;    // [5][5] inverse Gram matrix of (1, v, |v|^2) (with mom)
   SpecBufs<T> sb;
   SumArgs<T> sum;
   RedArgs<T> red;

@@ -99,8 +99,9 @@ struct sgs_handle {
   struct {
     size_t inst, cell_off, cell_inst, cnt, theta, nu, scratch, tw_cos, tw_sin, G, Lo, units, step0, row_k, row_start,
         row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, partial2, f_ref, Q_ref, theta_ref,
-        ahat_ref, active, W32lo, tw_cos32, tw_sin32, efac, efac_ref, end;
+        ahat_ref, active, W32lo, tw_cos32, tw_sin32, efac, efac_ref, cproj_A, mom, end;
   } off;
+  bool cproj = false;  // conservation projection of Q after every spectral collision step
   bool dc_ref = false;  // FP32 collisions use the increment form against the stored reference
   int dc_prec = SGS_DF64;  // arithmetic of the high-precision evaluation in sgs_dc_step
   bool two_d = false;      // 2-D space: one instance, wavefront scans, four orderings
@@ -139,6 +140,41 @@ struct sgs_handle {
 };
 
 namespace {
+
+// Inverse of the Gram matrix A = sum_k phi(v_k) phi(v_k)^T, phi = (1, v1, v2, v3, |v|^2), over
+// the N^3 velocity nodes (conservation projection), by Gauss-Jordan elimination with
+// partial pivoting in FP64. False if A is singular.
+bool gram_inverse(int N, double dv, double* Ainv) {
+  double A[5][10];
+  memset(A, 0, sizeof(A));
+  for (int i1 = 0; i1 < N; i1++)
+    for (int i2 = 0; i2 < N; i2++)
+      for (int i3 = 0; i3 < N; i3++) {
+        double v1 = (i1 - N / 2 + 1) * dv, v2 = (i2 - N / 2 + 1) * dv, v3 = (i3 - N / 2 + 1) * dv;
+        double ph[5] = {1.0, v1, v2, v3, v1 * v1 + v2 * v2 + v3 * v3};
+        for (int a = 0; a < 5; a++)
+          for (int b = 0; b < 5; b++) A[a][b] += ph[a] * ph[b];
+      }
+  for (int a = 0; a < 5; a++) A[a][5 + a] = 1.0;
+  for (int col = 0; col < 5; col++) {
+    int piv = col;
+    for (int r = col + 1; r < 5; r++)
+      if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+    if (!(std::fabs(A[piv][col]) > 0.0)) return false;
+    if (piv != col)
+      for (int k = 0; k < 10; k++) std::swap(A[piv][k], A[col][k]);
+    double d = A[col][col];
+    for (int k = 0; k < 10; k++) A[col][k] /= d;
+    for (int r = 0; r < 5; r++) {
+      if (r == col) continue;
+      double m = A[r][col];
+      for (int k = 0; k < 10; k++) A[r][k] -= m * A[col][k];
+    }
+  }
+  for (int a = 0; a < 5; a++)
+    for (int b = 0; b < 5; b++) Ainv[a * 5 + b] = A[a][5 + b];
+  return true;
+}
 
 int plan(sgs_handle* h) {
   int N = h->N, n = N - 1, H = N / 2 - 1;
@@ -250,6 +286,8 @@ void layout(sgs_handle* h) {
   f.tw_sin32 = take(sizeof(float) * n * N);
   f.efac = take(sizeof(double) * 3 * kMaxN * C);      // per-cell Maxwellian factors (finest level
   f.efac_ref = take(sizeof(double) * 3 * kMaxN * C);  // is the largest) and those of the reference
+  f.cproj_A = take(h->cproj ? sizeof(double) * 25 : 0);       // inverse Gram matrix of (1, v, |v|^2)
+  f.mom = take(h->cproj ? sizeof(double) * 5 * (size_t)C * N : 0);  // moments of Q per (cell, i1) slab
   bool sp = h->spectral;
   size_t U = h->units.size();
   f.G = take(sp ? sizeof(double) * h->na * h->nb : 0);
@@ -332,6 +370,7 @@ int check_problem(const sgs_problem& p) {
   if (p.precision != SGS_FP64 && p.precision != SGS_FP32) return SGS_ERR_ARG;
   if (p.inner_method != SGS_PFP && p.inner_method != SGS_FP) return SGS_ERR_ARG;
   if (p.inner_max < 0 || p.inner_fixed < 0 || p.newton_max < 1) return SGS_ERR_ARG;
+  if (p.conserve_proj != 0 && p.conserve_proj != 1) return SGS_ERR_ARG;
   for (int s = 0; s < 2; s++) {
     if (p.bc[s].kind != SGS_DIFFUSE && p.bc[s].kind != SGS_INFLOW) return SGS_ERR_ARG;
     if (!(p.bc[s].T > 0.0)) return SGS_ERR_ARG;
@@ -478,6 +517,8 @@ CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0) {
   x.sb.tws = sizeof(T) == 8 ? h->at<T>(h->off.tw_sin) : h->at<T>(h->off.tw_sin32);
   x.efac = h->at<double>(h->off.efac);
   x.efac_ref = h->at<double>(h->off.efac_ref);
+  x.mom = h->cproj ? h->at<double>(h->off.mom) : nullptr;
+  x.cproj = h->cproj ? h->at<double>(h->off.cproj_A) : nullptr;
   x.sb.st1a = h->at<CT>(h->off.st1a);
   x.sb.st1b = h->at<CT>(h->off.st1b);
   x.sb.st2a = h->at<CT>(h->off.st2a);
@@ -534,7 +575,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
       er = launch_spectral_sum(x, nullptr, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
-    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 4);
+    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, h->cproj ? 5 : 4);
     return cuda_status(launch_reduce_idft(f, Q, P, x, nullptr, nullptr, st));
   };
   // Increment form against the reference f_ref (defect correction): with a = f - M, b = f + M,
@@ -570,7 +611,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
       er = launch_spectral_sum(x, part2, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
-    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 4);
+    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, h->cproj ? 5 : 4);
     return cuda_status(launch_reduce_idft(f, Q, P, x, part2, h->at<double>(Lv.rQ), st));
   };
   if (precision == SGS_DF64) {
@@ -601,7 +642,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
       er = launch_sum_df(d, h->H, x.n_units, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
-    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 4);
+    Scope sc(h, SGS_PROF_REDUCE_IDFT, st, h->cproj ? 5 : 4);
     return cuda_status(launch_reduce_idft(f, Q, P, x, nullptr, nullptr, st));
   }
   if (precision == SGS_FP32) {
@@ -821,7 +862,8 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
     if (problems[q].nv != problems[0].nv || problems[q].v_max != problems[0].v_max ||
         problems[q].precision != problems[0].precision || problems[q].b0 != problems[0].b0 ||
         (problems[q].collision == SGS_BGK) != (problems[0].collision == SGS_BGK) ||
-        (problems[q].collision != SGS_BGK && problems[q].collision != problems[0].collision))
+        (problems[q].collision != SGS_BGK && problems[q].collision != problems[0].collision) ||
+        problems[q].conserve_proj != problems[0].conserve_proj)
       return SGS_ERR_UNSUPPORTED;
   }
   if (problems[0].space_dim == 2 && n_inst != 1) return SGS_ERR_UNSUPPORTED;  // one 2-D instance per handle
@@ -834,6 +876,7 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
   h->dv = 2.0 * h->L / h->N;
   h->precision = problems[0].precision;
   h->spectral = problems[0].collision != SGS_BGK;
+  h->cproj = h->spectral && problems[0].conserve_proj == 1;
   h->two_d = problems[0].space_dim == 2;
   long long K = (long long)h->N * h->N * h->N;
   h->inst.resize(n_inst);
@@ -944,6 +987,11 @@ int sgs_bind_workspace(sgs_handle* h, void* device_ptr, size_t bytes) {
     e = up(L.inst, L.hinst.data(), sizeof(InstDev) * L.hinst.size());
     if (e == cudaSuccess) e = up(L.cell_off, L.hcell_off.data(), sizeof(long long) * L.hcell_off.size());
     if (e == cudaSuccess) e = up(L.cell_inst, L.hcell_inst.data(), sizeof(int) * L.hcell_inst.size());
+  }
+  if (e == cudaSuccess && h->cproj) {
+    double Ainv[25];
+    if (!gram_inverse(h->N, h->dv, Ainv)) return SGS_ERR_ARG;
+    e = up(h->off.cproj_A, Ainv, sizeof(Ainv));
   }
   if (e == cudaSuccess) e = cudaMemset(h->ws + h->off.cnt, 0, sizeof(Counters) * h->n_inst);
   if (e == cudaSuccess) {

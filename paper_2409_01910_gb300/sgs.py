@@ -54,6 +54,7 @@ class _Problem(C.Structure):
         ("newton_tol", C.c_double),
         ("newton_max", C.c_int),
         ("inner_method", C.c_int),
+        ("conserve_proj", C.c_int),
     ]
 
 
@@ -105,6 +106,7 @@ class Problem:
     newton_tol: float = 1e-10
     newton_max: int = 50
     inner_method: int = PFP
+    conserve_proj: int = 0  # 1: FP64 projection of Q onto the zero-moment subspace (not in the paper)
     space_dim: int = 1
     ny: int = 1
     y_lo: float = 0.0
@@ -123,7 +125,7 @@ class Problem:
         p = _Problem()
         for name in ("space_dim", "nx", "x_lo", "x_hi", "ny", "y_lo", "y_hi", "nv", "v_max", "collision", "b0",
                      "eps", "total_mass", "precision", "inner_tol", "inner_max", "inner_fixed", "newton_tol",
-                     "newton_max", "inner_method"):
+                     "newton_max", "inner_method", "conserve_proj"):
             setattr(p, name, getattr(self, name))
         kinds = list(self.bc_kind) + list(self.bc_kind_y)
         rhos = list(self.bc_rho) + list(self.bc_rho_y)

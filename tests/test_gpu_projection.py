@@ -1,0 +1,189 @@
+"""GPU parity of the conservation projection of Q (an option, not in the paper) against the
+oracle's projection: the collision step in FP64 (1e-12), double-float (1e-11) and FP32
+(1e-5); SGS iterations and a V-cycle on the normal-shock configuration (1e-12); defect
+correction with FP32 increments tracking the FP64 iteration; and the five moments
+(1, v, |v|^2) of the projected Q at round-off in every precision."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2409_01910_gb300 import inputs as I
+from paper_2409_01910_gb300 import sgs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sgs.lib()
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x).reshape(-1)).cuda()
+
+
+def basis(N, L):
+    v = (np.arange(N) - N // 2 + 1) * (2 * L / N)
+    V = np.stack(np.meshgrid(v, v, v, indexing="ij"), -1).reshape(-1, 3)
+    return np.column_stack([np.ones(len(V)), V, (V**2).sum(-1)])
+
+
+def assert_zero_moments(Q, N, L, tol=1e-13):
+    Phi = basis(N, L)
+    for q in Q.reshape(Q.shape[0], -1):
+        scale = (np.abs(Phi) * np.abs(q)[:, None]).sum(0)
+        assert np.all(np.abs(Phi.T @ q) <= tol * scale)
+
+
+def varied_state(J, N, L, seed=0):
+    rng = np.random.default_rng(seed)
+    f = np.empty((J, N, N, N))
+    for j in range(J):
+        u = rng.uniform(-0.6, 0.6, 3)
+        f[j] = I.sampled_maxwellian(N, L, rng.uniform(0.5, 1.5), u, rng.uniform(0.6, 1.6))
+        f[j] += I.sampled_maxwellian(N, L, rng.uniform(0.2, 0.6), -u, rng.uniform(0.4, 1.0))
+        f[j] *= 1 + 0.02 * rng.uniform(-1, 1, (N, N, N))
+    return f
+
+
+def pair(oracle, J, N, L, kernel, precision=sgs.FP64, **kw):
+    g = sgs.Problem(nx=J, nv=N, v_max=L, collision=kernel, precision=precision, conserve_proj=1, **kw)
+    o = oracle.Problem(N=N, L=L, J=J, kernel=kernel, conserve_proj=1, **kw)
+    return g, o
+
+
+@pytest.mark.parametrize("N,J,L,kernel", [(8, 40, 6.0, 0), (16, 16, 6.0, 1), (12, 3, 8.0, 1)])
+def test_projected_collide_fp64_parity(oracle, N, J, L, kernel):
+    f = varied_state(J, N, L, seed=N + J)
+    g, o = pair(oracle, J, N, L, kernel)
+    s = sgs.Solver(g)
+    Q, P = s.field(), s.field()
+    s.collide(to_dev(f), Q, P)
+    Qo, Po, nuo = oracle.collide(o, f)
+    Qg = Q.cpu().numpy().reshape(f.shape)
+    assert rel(Qg, Qo) <= 1e-12
+    assert rel(P.cpu().numpy().reshape(f.shape), Po) <= 1e-12
+    assert_zero_moments(Qg, N, L)
+    # the projection did change Q: the plain operator's moments are not at round-off
+    Qp, _, _ = oracle.collide(oracle.Problem(N=N, L=L, J=J, kernel=kernel), f)
+    assert rel(Qg, Qp) > 1e-12
+    assert s.read_status()["status"] == 0
+
+
+def test_projected_collide_reduced_precision(oracle):
+    N, J, L = 16, 16, 6.0
+    f = varied_state(J, N, L, seed=7)
+    g, o = pair(oracle, J, N, L, 1, precision=sgs.FP32)
+    s = sgs.Solver(g)
+    Qo, Po, nuo = oracle.collide(o, f)
+    for prec, tol in ((None, 1e-5), (sgs.DF64, 1e-11)):
+        Q, P = s.field(), s.field()
+        s.collide(to_dev(f), Q, P, precision=prec)
+        Qg = Q.cpu().numpy().reshape(f.shape)
+        assert rel(Qg, Qo) <= tol, prec
+        assert rel(P.cpu().numpy().reshape(f.shape), Po) <= tol, prec
+        assert_zero_moments(Qg, N, L)
+    assert s.read_status()["status"] == 0
+
+
+SHOCK = dict(J=8, N=8, L=8.0, eps=0.5)
+
+
+def shock_gpu(inner_fixed=4, precision=sgs.FP64, inner_tol=1e-8):
+    up, down = I.rankine_hugoniot(2.0)
+    return sgs.Problem(nx=SHOCK["J"], x_lo=-4.0, x_hi=4.0, nv=SHOCK["N"], v_max=SHOCK["L"], eps=SHOCK["eps"],
+                       collision=sgs.HARD_SPHERE, bc_kind=(sgs.INFLOW, sgs.INFLOW), bc_rho=(up[0], down[0]),
+                       bc_u=((up[1], 0.0, 0.0), (down[1], 0.0, 0.0)), bc_T=(up[2], down[2]), total_mass=0.0,
+                       precision=precision, inner_tol=inner_tol, inner_fixed=inner_fixed, conserve_proj=1)
+
+
+def shock_oracle(oracle, inner_fixed=4):
+    up, down = I.rankine_hugoniot(2.0)
+    return oracle.Problem(N=SHOCK["N"], L=SHOCK["L"], J=SHOCK["J"], x_lo=-4.0, x_hi=4.0, eps=SHOCK["eps"],
+                          kernel=oracle.HARD_SPHERE, bc_kind=(oracle.INFLOW, oracle.INFLOW),
+                          bc_rho=(up[0], down[0]), bc_u=((up[1], 0.0, 0.0), (down[1], 0.0, 0.0)),
+                          bc_T=(up[2], down[2]), total_mass=0.0, inner_tol=1e-8, inner_fixed=inner_fixed,
+                          conserve_proj=1)
+
+
+def shock_state():
+    up, down = I.rankine_hugoniot(2.0)
+    return I.ShockWorkload("t", J=SHOCK["J"], N=SHOCK["N"], L=SHOCK["L"], eps=SHOCK["eps"], up=up, down=down,
+                           x_lo=-4.0, x_hi=4.0).initial_state()
+
+
+def test_projected_shock_iterations_parity(oracle):
+    g, o, f0 = shock_gpu(), shock_oracle(oracle), shock_state()
+    fo = f0.copy()
+    for _ in range(2):
+        oracle.sgs_iteration(o, fo)
+    s = sgs.Solver(g)
+    f = to_dev(f0)
+    Q, P = s.field(), s.field()
+    for it in range(2):
+        s.iterate(f, Q, P, flags=sgs.IT_EVAL | (sgs.IT_P_VALID if it else 0))
+    assert s.read_status()["status"] == 0
+    assert rel(f.cpu().numpy().reshape(f0.shape), fo) <= 1e-12
+
+
+def test_projected_shock_vcycle_parity(oracle):
+    g, o, f0 = shock_gpu(), shock_oracle(oracle), shock_state()
+    fo = f0.copy()
+    oracle.vcycle(o, fo, 3, 1, 1, 2)
+    s = sgs.Solver(g)
+    f = to_dev(f0)
+    s.vcycle(f, 3, 1, 1, 2)
+    assert s.read_status()["status"] == 0
+    assert rel(f.cpu().numpy().reshape(f0.shape), fo) <= 1e-12
+
+
+def dc_vs_fp64(g64, g32, f0, cycles, lo):
+    s64 = sgs.Solver(g64)
+    f64 = to_dev(f0)
+    Q, P = s64.field(), s64.field()
+    for it in range(cycles * lo):
+        s64.iterate(f64, Q, P, flags=sgs.IT_EVAL | (sgs.IT_P_VALID if it else 0))
+    s32 = sgs.Solver(g32)
+    fdc = to_dev(f0)
+    Q2, P2 = s32.field(), s32.field()
+    for k in range(cycles):
+        s32.dc_step(fdc, Q2, P2, lo)
+    s32.dc_step(fdc, Q2, P2, 0)
+    assert s64.read_status()["status"] == 0 and s32.read_status()["status"] == 0
+    return rel(fdc.cpu().numpy(), f64.cpu().numpy()), Q2.cpu().numpy().reshape(f0.shape)
+
+
+def test_projected_defect_correction_adds_no_error():
+    """Heat transfer (16 cells, 16^3, eps = 0.1): FP32 increments + double-float evaluation
+    against the FP64 iteration after the same 48 SGS iterations, with and without the
+    projection. The projection is linear and orthogonal, so it adds no error of its own."""
+    wl = I.heat_16cells_16v()
+    f0 = wl.initial_state()
+    errs = {}
+    for cp in (0, 1):
+        g = dict(nx=wl.J, nv=wl.N, v_max=wl.L, eps=0.1, bc_T=(wl.T_left, wl.T_right), total_mass=wl.total_mass,
+                 inner_tol=1e-11, conserve_proj=cp)
+        errs[cp], Q = dc_vs_fp64(sgs.Problem(precision=sgs.FP64, **g), sgs.Problem(precision=sgs.FP32, **g), f0, 6, 8)
+    print("dc vs fp64 (heat): plain", errs[0], "projected", errs[1])
+    assert errs[0] <= 2e-8 and errs[1] <= 2.0 * errs[0] + 1e-9
+    assert_zero_moments(Q, wl.N, wl.L)
+
+
+def test_projected_defect_correction_on_shock():
+    """The same on the 8-cell shock (hard spheres, 8^3 velocities, 24 SGS iterations); on so
+    coarse a velocity grid the plain spectral operator is not usable here (its iterates lose
+    positivity), the projected one is."""
+    f0 = shock_state()
+    err, Q = dc_vs_fp64(shock_gpu(inner_fixed=0, inner_tol=1e-11),
+                        shock_gpu(inner_fixed=0, inner_tol=1e-11, precision=sgs.FP32), f0, 3, 8)
+    print("dc vs fp64 (shock, projected)", err)
+    assert err <= 1e-7
+    assert_zero_moments(Q, SHOCK["N"], SHOCK["L"])
