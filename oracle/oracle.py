@@ -192,6 +192,7 @@ def lib():
             "or_qfsm": (None, [C.c_int, C.c_double, C.c_int, C.c_double, d, d]),
             "or_moments": (None, [C.c_int, C.c_double, d, d]),
             "or_conserve_project": (C.c_int, [C.c_int, C.c_double, d]),
+            "or_conserve_project_w": (C.c_int, [C.c_int, C.c_double, d, d]),
             "or_discrete_maxwellian": (C.c_int, [C.c_int, C.c_double, d, d, d, C.c_int, C.c_double, C.c_int]),
             "or_eval_maxwellian": (None, [C.c_int, C.c_double, d, d]),
             "or_collision_frequency": (C.c_double, [P, d]),
@@ -289,6 +290,14 @@ def conserve_project(q, L):
     """Conservation projection of one cell's q (N, N, N); returns a new array."""
     out = _arr(q).copy()
     if lib().or_conserve_project(q.shape[0], L, _p(out)) != 0:
+        raise ArithmeticError("singular Gram matrix")
+    return out
+
+
+def conserve_project_w(q, L, M):
+    """Maxwellian-weighted conservation projection of one cell's q; returns a new array."""
+    out = _arr(q).copy()
+    if lib().or_conserve_project_w(q.shape[0], L, _p(_arr(M)), _p(out)) != 0:
         raise ArithmeticError("singular Gram matrix")
     return out
 

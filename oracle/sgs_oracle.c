@@ -581,6 +581,41 @@ int or_conserve_project(int N, double L, double* q) {
   return ok;
 }
 
+/* Weighted variant: minimising sum_k (q_c - q)^2 / M_k under the same five constraints
+ * gives q_c = q - M sum_i lambda_i phi_i with (sum_k M phi phi^T) lambda = sum_k phi q, so the
+ * correction lives where the local Maxwellian M does and leaves the far tails untouched. */
+int or_conserve_project_w(int N, double L, const double* M, double* q) {
+  double* v = (double*)malloc(sizeof(double) * N);
+  or_velocity_nodes(N, L, v);
+  double A[25], s[5], lam[5];
+  memset(A, 0, sizeof(A));
+  memset(s, 0, sizeof(s));
+  long t = 0;
+  for (int i1 = 0; i1 < N; i1++)
+    for (int i2 = 0; i2 < N; i2++)
+      for (int i3 = 0; i3 < N; i3++, t++) {
+        double phi[5] = {1.0, v[i1], v[i2], v[i3], v[i1] * v[i1] + v[i2] * v[i2] + v[i3] * v[i3]};
+        for (int a = 0; a < 5; a++) {
+          s[a] += phi[a] * q[t];
+          for (int b = 0; b < 5; b++) A[a * 5 + b] += M[t] * phi[a] * phi[b];
+        }
+      }
+  int ok = chol5(A, s, lam);
+  if (ok == 0) {
+    t = 0;
+    for (int i1 = 0; i1 < N; i1++)
+      for (int i2 = 0; i2 < N; i2++)
+        for (int i3 = 0; i3 < N; i3++, t++) {
+          double phi[5] = {1.0, v[i1], v[i2], v[i3], v[i1] * v[i1] + v[i2] * v[i2] + v[i3] * v[i3]};
+          double c = 0.0;
+          for (int a = 0; a < 5; a++) c += lam[a] * phi[a];
+          q[t] -= M[t] * c;
+        }
+  }
+  free(v);
+  return ok;
+}
+
 /* ------------------------------------------------------------------------------------
  * Steady-state-preserving collision term (eq. (16)):
  *   Q = Q^FSM[f, f] - Q^FSM[M[f], M[f]]
@@ -607,7 +642,8 @@ void or_collide_cell(const or_problem* p, const double* f, double* Q, double* P,
     or_qfsm(N, p->L, p->kernel, p->b0, M, qm);
     for (long i = 0; i < K; i++) q[i] -= qm[i];
     free(qm);
-    if (p->conserve_proj) or_conserve_project(N, p->L, q);
+    if (p->conserve_proj == 1) or_conserve_project(N, p->L, q);
+    if (p->conserve_proj == 2) or_conserve_project_w(N, p->L, M, q);
   }
   if (Q) memcpy(Q, q, sizeof(double) * K);
   if (P) {

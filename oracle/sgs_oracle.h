@@ -40,7 +40,8 @@ typedef struct {
   double inner_tol; int inner_max, inner_fixed;
   double newton_tol; int newton_max;
   int inner_method;    /* OR_PFP or OR_FP */
-  int conserve_proj;   /* 1: project Q onto the zero-moment subspace (not in the paper) */
+  int conserve_proj;   /* 1: project Q onto the zero-moment subspace (not in the paper);
+                          2: the same with the correction weighted by the local Maxwellian */
 } or_problem;
 
 typedef struct {
@@ -64,6 +65,9 @@ void or_qfsm(int N, double L, int kernel, double b0, const double* f, double* q)
 /* Orthogonal projection of q (in place) onto {q : sum_k phi_i(v_k) q_k = 0, i = 0..4},
  * phi = (1, v1, v2, v3, |v|^2). Returns 0, or -1 if the 5x5 Gram matrix is singular. */
 int or_conserve_project(int N, double L, double* q);
+/* Maxwellian-weighted variant: q_c = q - M (lambda . phi) with (sum_k M phi phi^T) lambda =
+ * sum_k phi q, the smallest change of q in the norm sum (.)^2 / M that zeroes the moments. */
+int or_conserve_project_w(int N, double L, const double* M, double* q);
 /* Moments (rho, rho*U, sum w|v|^2 f) with weights w. */
 void or_moments(int N, double L, const double* f, double* m5);
 /* Discrete Maxwellian exp(alpha + beta.v - gamma|v|^2) matching weighted moments.

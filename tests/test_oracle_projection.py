@@ -77,3 +77,43 @@ def test_projected_collision_of_maxwellian_vanishes(oracle):
     Q, P, nu, _ = oracle.collide_cell(oracle.Problem(N=N, L=L, conserve_proj=1), M)
     assert np.abs(Q).max() <= 1e-13 * nu * M.max()
     assert np.abs(P).max() <= 1e-13 * nu * M.max()
+
+
+# Maxwellian-weighted variant (conserve_proj = 2): q_c = q - M (lambda . phi). It is fixed by
+# (i) zero moments and (ii) q - q_c = M (phi . c) for some c, checked with numpy least squares.
+def check_weighted(q, qc, M, Phi, tol=1e-13):
+    scale = (np.abs(Phi) * np.abs(q.reshape(-1, 1))).sum(0)
+    assert np.all(np.abs(Phi.T @ qc.reshape(-1)) <= tol * scale)
+    d = (q - qc).reshape(-1)
+    MPhi = M.reshape(-1, 1) * Phi
+    coef, *_ = np.linalg.lstsq(MPhi, d, rcond=None)
+    assert np.abs(MPhi @ coef - d).max() <= 1e-13 * np.abs(q).max()
+
+
+@pytest.mark.parametrize("N,L,seed", [(8, 6.0, 0), (16, 10.0, 3)])
+def test_weighted_projection_of_random_vectors(oracle, N, L, seed):
+    rng = np.random.default_rng(seed)
+    v = (np.arange(N) - N // 2 + 1) * (2 * L / N)
+    V = np.stack(np.meshgrid(v, v, v, indexing="ij"), -1)
+    M = 1.3 / (2 * np.pi * 1.7) ** 1.5 * np.exp(-((V - [0.8, 0.2, -0.3]) ** 2).sum(-1) / (2 * 1.7))
+    q = rng.standard_normal((N, N, N)) * M
+    qc = oracle.conserve_project_w(q, L, M)
+    check_weighted(q, qc, M, basis(N, L))
+    assert np.abs(oracle.conserve_project_w(qc, L, M) - qc).max() <= 1e-13 * np.abs(q).max()
+    # far from the Maxwellian the correction vanishes with it (the tails are left alone)
+    far = M < 1e-12 * M.max()
+    assert np.abs((qc - q)[far]).max() <= 1e-10 * np.abs(q).max()
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_weighted_projected_collision_conserves(oracle, kernel):
+    N, L = 16, 8.0
+    f = bimodal(N, L)
+    Q0, P0, nu0, th = oracle.collide_cell(oracle.Problem(N=N, L=L, kernel=kernel), f)
+    Q2, P2, nu2, th2 = oracle.collide_cell(oracle.Problem(N=N, L=L, kernel=kernel, conserve_proj=2), f)
+    M = oracle.eval_maxwellian(N, L, th)
+    check_weighted(Q0, Q2, M, basis(N, L))
+    assert np.abs((P2 - P0) - (Q2 - Q0)).max() <= 1e-14 * np.abs(Q0).max()
+    # the weighted and the plain projection both zero the moments, with different corrections
+    Q1, _, _, _ = oracle.collide_cell(oracle.Problem(N=N, L=L, kernel=kernel, conserve_proj=1), f)
+    assert np.abs(Q1 - Q2).max() > 1e-6 * np.abs(Q1 - Q0).max()
