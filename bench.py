@@ -19,6 +19,9 @@ four orderings per SGS iteration, V-cycles on 64^2/32^2/16^2 cells).
 [-20, 20], 32^3 velocities on [-10, 10]^3, hard spheres, eps = 0.1, Rankine-Hugoniot inflow
 data, V-cycles on 128/64/32/16 cells) and records the shock position.
 
+--conserve-proj 1|2 adds the FP64 conservation projection of Q (plain or Maxwellian-weighted;
+not in the paper); --pin-mass holds the shock's total mass at its initial value (eq. (32)).
+
 N > 1 runs independent replicas (one per GPU, launched by torchrun): the method is a
 sequential scan per problem, so work is replicated, not sharded ("scaling": "weak").
 """
@@ -63,6 +66,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default scan shape")
     ap.add_argument("--t2tol-all", action="store_true", help="also time the plain FP64 SGS form to 1e-8")
     ap.add_argument("--t2tol-cap", type=float, default=150.0, help="seconds allowed per time-to-residual run")
+    ap.add_argument("--conserve-proj", type=int, choices=[0, 1, 2], default=0,
+                    help="conservation projection of Q: 0 the paper's operator, 1 plain, 2 Maxwellian-weighted")
+    ap.add_argument("--pin-mass", action="store_true",
+                    help="shock: hold the total mass at the initial state's (eq. (32) rescale), pinning the shock")
     ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d", "dft"], default=None,
                     help="run a small case of one kernel class (for profiler captures) and exit")
     return ap.parse_args()
@@ -130,6 +137,8 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------- native
 WORKLOAD = "heat"
+CONSERVE_PROJ = 0   # --conserve-proj
+PIN_MASS = False    # --pin-mass (shock)
 
 
 def workload():
@@ -157,6 +166,12 @@ def visits_per_iteration(wl):
     return (4 if is_cavity(wl) else 2) * wl.J
 
 
+def shock_mass(wl):
+    """Total mass of the shock's initial state, sum_j dx sum_k w f0 (the --pin-mass constant)."""
+    dx = (wl.x_hi - wl.x_lo) / wl.J
+    return float(wl.initial_state().sum()) * (2 * wl.L / wl.N) ** 3 * dx
+
+
 def make_solver(wl, precision):
     from paper_2409_01910_gb300 import sgs
 
@@ -168,14 +183,25 @@ def make_solver(wl, precision):
         (r1, u1, T1), (r2, u2, T2) = wl.up, wl.down
         p = sgs.Problem(nx=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, nv=wl.N, v_max=wl.L, collision=sgs.HARD_SPHERE,
                         eps=wl.eps, bc_kind=(sgs.INFLOW, sgs.INFLOW), bc_rho=(r1, r2),
-                        bc_u=((u1, 0.0, 0.0), (u2, 0.0, 0.0)), bc_T=(T1, T2), total_mass=0.0, precision=precision)
+                        bc_u=((u1, 0.0, 0.0), (u2, 0.0, 0.0)), bc_T=(T1, T2),
+                        total_mass=shock_mass(wl) if PIN_MASS else 0.0, precision=precision)
     else:
         p = sgs.Problem(nx=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, nv=wl.N, v_max=wl.L, eps=wl.eps,
                         bc_T=(wl.T_left, wl.T_right), total_mass=wl.total_mass, precision=precision)
+    p.conserve_proj = CONSERVE_PROJ
     return sgs.Solver(p)
 
 
 def config_of(wl):
+    c = _config_of(wl)
+    if CONSERVE_PROJ:
+        c["conserve_proj"] = ["plain", "maxwellian_weighted"][CONSERVE_PROJ - 1]
+    if PIN_MASS and is_shock(wl):
+        c["total_mass_pinned"] = True
+    return c
+
+
+def _config_of(wl):
     if is_cavity(wl):
         return {"workload": wl.name, "cells": [wl.nx, wl.ny], "domain": [[0.0, 1.0], [0.0, 1.0]], "nv": wl.N,
                 "v_max": wl.L, "eps": wl.eps, "collision": "maxwell", "lid_speed": wl.lid, "T_walls": wl.T_wall,
@@ -746,9 +772,11 @@ def profile_case(which):
 
 
 def main():
-    global WORKLOAD
+    global WORKLOAD, CONSERVE_PROJ, PIN_MASS
     args = parse()
     WORKLOAD = args.workload
+    CONSERVE_PROJ = args.conserve_proj
+    PIN_MASS = args.pin_mass
     if args.case:
         profile_case(args.case)
         return

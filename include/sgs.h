@@ -93,9 +93,12 @@ typedef struct {
   int conserve_proj;  /* 0: the paper's Q (mass conserved to round-off, momentum and energy to
                          spectral accuracy); 1: Q projected in FP64 onto the zero-moment
                          subspace, Q_c = Q - C^T (C C^T)^-1 C Q with C = [w phi_i(v_k)],
-                         phi = (1, v, |v|^2), applied in every collision step (all levels
-                         and precisions) before P = Q_c - nu (M - f) is formed. Not in the
-                         paper; equal in every instance of a handle; ignored for BGK. */
+                         phi = (1, v, |v|^2); 2: the Maxwellian-weighted projection
+                         Q_c = Q - M (lambda . phi), (sum_k M phi phi^T) lambda = sum_k phi Q,
+                         M the cell's discrete Maxwellian (the correction stays out of the
+                         far velocity tails). Applied in FP64 in every collision step (all
+                         levels and precisions) before P = Q_c - nu (M - f) is formed. Not in
+                         the paper; equal in every instance of a handle; ignored for BGK. */
 } sgs_problem;
 
 /* Counters accumulated on the device since setup or the last sgs_reset_stats(). */

@@ -743,35 +743,98 @@ __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* _
   }
 }
 
-// Conservation projection (an option; not in the paper): Q_c = Q - sum_i lambda_i phi_i
-// with (sum_k phi phi^T) lambda = sum_k phi Q, phi = (1, v1, v2, v3, |v|^2), applied to Q and
-// to P = Q - nu (M - f) alike. The moments come from the slabs of k_idft_k3, summed here in
-// i1 order (every block of a cell forms the same lambda); Ainv is the inverse Gram matrix.
+// Conservation projection (an option; not in the paper), applied to Q and to
+// P = Q - nu (M - f) alike, with phi = (1, v1, v2, v3, |v|^2) and the moments sum_k phi Q from
+// the slabs of k_idft_k3, summed here in i1 order (every block of a cell forms the same lambda):
+//   mode 1: Q_c = Q - sum_i lambda_i phi_i,      (sum_k phi phi^T) lambda = sum_k phi Q,
+//           with the inverse Gram matrix Ainv of the grid;
+//   mode 2: Q_c = Q - M sum_i lambda_i phi_i,    (sum_k M phi phi^T) lambda = sum_k phi Q,
+//           with the cell's Maxwellian M = E1(v1) E2(v2) E3(v3) (factors efac): its Gram
+//           matrix is a sum of products of the 1-D sums S_d^p = sum_i E_d(v_i) v_i^p.
+__device__ bool chol5_solve(double A[5][5], const double* b, double* x) {
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j <= i; j++) {
+      double t = A[i][j];
+      for (int k = 0; k < j; k++) t -= A[i][k] * A[j][k];
+      if (i == j) {
+        if (!(t > 0.0)) return false;
+        A[i][i] = sqrt(t);
+      } else {
+        A[i][j] = t / A[j][j];
+      }
+    }
+  double z[5];
+  for (int i = 0; i < 5; i++) {
+    double t = b[i];
+    for (int k = 0; k < i; k++) t -= A[i][k] * z[k];
+    z[i] = t / A[i][i];
+  }
+  for (int i = 4; i >= 0; i--) {
+    double t = z[i];
+    for (int k = i + 1; k < 5; k++) t -= A[k][i] * x[k];
+    x[i] = t / A[i][i];
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(256) k_conserve_apply(const double* __restrict__ mom,
-                                                        const double* __restrict__ Ainv, CellTables ct, double* Q,
-                                                        double* P, int N, double dv) {
-  __shared__ double sm[5], lam[5];
+                                                        const double* __restrict__ Ainv,
+                                                        const double* __restrict__ efac, int mode, CellTables ct,
+                                                        double* Q, double* P, double* Qraw, int N, double dv) {
+  __shared__ double sm[5], lam[5], S[3][5];
   int c = blockIdx.x, i1 = blockIdx.y;
+  const double* e = efac + (long long)c * 3 * kMaxN;
   if (threadIdx.x < 5) {
     double a = 0.0;
     const double* m = mom + (long long)c * N * 5 + threadIdx.x;
     for (int j = 0; j < N; j++) a += m[j * 5];
     sm[threadIdx.x] = a;
+  } else if (mode == 2 && threadIdx.x < 20) {
+    int d = (threadIdx.x - 5) / 5, p = (threadIdx.x - 5) % 5;
+    double a = 0.0;
+    for (int i = 0; i < N; i++) {
+      double v = (i - N / 2 + 1) * dv, vp = 1.0;
+      for (int k = 0; k < p; k++) vp *= v;
+      a += e[d * kMaxN + i] * vp;
+    }
+    S[d][p] = a;
   }
   __syncthreads();
-  if (threadIdx.x < 5) {
+  if (mode == 1 && threadIdx.x < 5) {
     double a = 0.0;
     for (int k = 0; k < 5; k++) a += Ainv[threadIdx.x * 5 + k] * sm[k];
     lam[threadIdx.x] = a;
+  } else if (mode == 2 && threadIdx.x == 0) {
+    // phi as monomials v1^a v2^b v3^c: 1, v1, v2, v3 and |v|^2 = v1^2 + v2^2 + v3^2
+    const int nm[5] = {1, 1, 1, 1, 3};
+    const int mono[5][3][3] = {{{0, 0, 0}}, {{1, 0, 0}}, {{0, 1, 0}}, {{0, 0, 1}},
+                               {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}}};
+    double A[5][5];
+    for (int a = 0; a < 5; a++)
+      for (int b = 0; b < 5; b++) {
+        double t = 0.0;
+        for (int x = 0; x < nm[a]; x++)
+          for (int y = 0; y < nm[b]; y++)
+            t += S[0][mono[a][x][0] + mono[b][y][0]] * S[1][mono[a][x][1] + mono[b][y][1]] *
+                 S[2][mono[a][x][2] + mono[b][y][2]];
+        A[a][b] = t;
+      }
+    double x[5];
+    if (!chol5_solve(A, sm, x))
+      for (int k = 0; k < 5; k++) x[k] = 0.0;
+    for (int k = 0; k < 5; k++) lam[k] = x[k];
   }
   __syncthreads();
   double v1 = (i1 - N / 2 + 1) * dv;
   double c0 = lam[0] + lam[1] * v1 + lam[4] * v1 * v1;
+  double e1 = mode == 2 ? e[i1] : 1.0;
   long long base = ct.cell_off[c] + (long long)i1 * N * N;
   for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
     int i2 = t / N, i3 = t % N;
     double v2 = (i2 - N / 2 + 1) * dv, v3 = (i3 - N / 2 + 1) * dv;
     double corr = c0 + lam[2] * v2 + lam[3] * v3 + lam[4] * (v2 * v2 + v3 * v3);
+    if (mode == 2) corr *= e1 * e[kMaxN + i2] * e[2 * kMaxN + i3];
+    if (Qraw) Qraw[base + t] = Q[base + t];  // the unprojected operator (increment-form reference)
     if (Q) Q[base + t] -= corr;
     if (P) P[base + t] -= corr;
   }
@@ -950,7 +1013,8 @@ cudaError_t launch_spectral_sum(const CollideCtx<T>& x, typename CplxOf<T>::type
 
 template <typename T>
 cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const CollideCtx<T>& x,
-                               const typename CplxOf<T>::type* partial2, const double* Qadd, cudaStream_t st) {
+                               const typename CplxOf<T>::type* partial2, const double* Qadd, cudaStream_t st,
+                               double* Qraw) {
   int N = x.N, n = N - 1, C = x.C;
   cudaError_t e;
   RedArgs<T> ra = x.red;
@@ -970,7 +1034,8 @@ cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const Coll
   k_idft_k3<T><<<dim3(C, N), 256, sm4, st>>>(x.sb, f, x.ct, x.efac, x.nu, Q, P, N, x.dv, Qadd, x.mom);
   e = cudaGetLastError();
   if (e != cudaSuccess || !x.mom) return e;
-  k_conserve_apply<<<dim3(C, N), 256, 0, st>>>(x.mom, x.cproj, x.ct, Q, P, N, x.dv);
+  if (Qraw && !Q) return cudaErrorInvalidValue;
+  k_conserve_apply<<<dim3(C, N), 256, 0, st>>>(x.mom, x.cproj, x.efac, x.cproj_mode, x.ct, Q, P, Qraw, N, x.dv);
   return cudaGetLastError();
 }
 
@@ -1004,9 +1069,9 @@ template cudaError_t launch_dft<float>(const double*, const CollideCtx<float>&, 
 template cudaError_t launch_spectral_sum<double>(const CollideCtx<double>&, double2*, cudaStream_t);
 template cudaError_t launch_spectral_sum<float>(const CollideCtx<float>&, float2*, cudaStream_t);
 template cudaError_t launch_reduce_idft<double>(const double*, double*, double*, const CollideCtx<double>&,
-                                                const double2*, const double*, cudaStream_t);
+                                                const double2*, const double*, cudaStream_t, double*);
 template cudaError_t launch_reduce_idft<float>(const double*, double*, double*, const CollideCtx<float>&,
-                                               const float2*, const double*, cudaStream_t);
+                                               const float2*, const double*, cudaStream_t, double*);
 template cudaError_t launch_build_weights<double>(const int4*, const long long*, int, int, int, const double*,
                                                   long long, const double*, double*, cudaStream_t);
 template cudaError_t launch_build_weights<float>(const int4*, const long long*, int, int, int, const double*,

@@ -115,7 +115,8 @@ struct CollideCtx {
   double* efac;           // [C][3][kMaxN] separable factors of each cell's Maxwellian
   double* efac_ref;       // the same for the reference state (increment modes)
   double* mom;            // [C][N][5] moments of Q per slab (conservation projection), or null
-  const double* cproj;    // [5][5] inverse Gram matrix of (1, v, |v|^2) (with mom)
+  const double* cproj;    // [5][5] inverse Gram matrix of (1, v, |v|^2) (projection mode 1)
+  int cproj_mode;         // 0 none, 1 plain, 2 Maxwellian-weighted conservation projection
   SpecBufs<T> sb;
   SumArgs<T> sum;
   RedArgs<T> red;
@@ -163,8 +164,10 @@ cudaError_t launch_dft(const double* f, const CollideCtx<T>& x, const DftMode& m
 template <typename T>
 cudaError_t launch_spectral_sum(const CollideCtx<T>& x, typename CplxOf<T>::type* partial, cudaStream_t st);
 template <typename T>
+// Qraw (with the conservation projection; needs Q): also receives the unprojected operator.
 cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const CollideCtx<T>& x,
-                               const typename CplxOf<T>::type* partial2, const double* Qadd, cudaStream_t st);
+                               const typename CplxOf<T>::type* partial2, const double* Qadd, cudaStream_t st,
+                               double* Qraw = nullptr);
 cudaError_t launch_sum_df(const SumDfArgs& a, int H, int n_units, cudaStream_t st);
 cudaError_t launch_split_spec(double2* x, long long count, cudaStream_t st);
 cudaError_t launch_build_weights_lo(const int4* units, const long long* unit_step0, int n_units, int H, int PW,

@@ -101,7 +101,7 @@ struct sgs_handle {
         row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, partial2, f_ref, Q_ref, theta_ref,
         ahat_ref, active, W32lo, tw_cos32, tw_sin32, efac, efac_ref, cproj_A, mom, end;
   } off;
-  bool cproj = false;  // conservation projection of Q after every spectral collision step
+  int cproj = 0;  // conservation projection of Q after every spectral collision step (mode 1 or 2)
   bool dc_ref = false;  // FP32 collisions use the increment form against the stored reference
   int dc_prec = SGS_DF64;  // arithmetic of the high-precision evaluation in sgs_dc_step
   bool two_d = false;      // 2-D space: one instance, wavefront scans, four orderings
@@ -286,7 +286,7 @@ void layout(sgs_handle* h) {
   f.tw_sin32 = take(sizeof(float) * n * N);
   f.efac = take(sizeof(double) * 3 * kMaxN * C);      // per-cell Maxwellian factors (finest level
   f.efac_ref = take(sizeof(double) * 3 * kMaxN * C);  // is the largest) and those of the reference
-  f.cproj_A = take(h->cproj ? sizeof(double) * 25 : 0);       // inverse Gram matrix of (1, v, |v|^2)
+  f.cproj_A = take(h->cproj == 1 ? sizeof(double) * 25 : 0);  // inverse Gram matrix of (1, v, |v|^2)
   f.mom = take(h->cproj ? sizeof(double) * 5 * (size_t)C * N : 0);  // moments of Q per (cell, i1) slab
   bool sp = h->spectral;
   size_t U = h->units.size();
@@ -370,7 +370,7 @@ int check_problem(const sgs_problem& p) {
   if (p.precision != SGS_FP64 && p.precision != SGS_FP32) return SGS_ERR_ARG;
   if (p.inner_method != SGS_PFP && p.inner_method != SGS_FP) return SGS_ERR_ARG;
   if (p.inner_max < 0 || p.inner_fixed < 0 || p.newton_max < 1) return SGS_ERR_ARG;
-  if (p.conserve_proj != 0 && p.conserve_proj != 1) return SGS_ERR_ARG;
+  if (p.conserve_proj < 0 || p.conserve_proj > 2) return SGS_ERR_ARG;
   for (int s = 0; s < 2; s++) {
     if (p.bc[s].kind != SGS_DIFFUSE && p.bc[s].kind != SGS_INFLOW) return SGS_ERR_ARG;
     if (!(p.bc[s].T > 0.0)) return SGS_ERR_ARG;
@@ -518,7 +518,8 @@ CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0) {
   x.efac = h->at<double>(h->off.efac);
   x.efac_ref = h->at<double>(h->off.efac_ref);
   x.mom = h->cproj ? h->at<double>(h->off.mom) : nullptr;
-  x.cproj = h->cproj ? h->at<double>(h->off.cproj_A) : nullptr;
+  x.cproj = h->cproj == 1 ? h->at<double>(h->off.cproj_A) : nullptr;
+  x.cproj_mode = h->cproj;
   x.sb.st1a = h->at<CT>(h->off.st1a);
   x.sb.st1b = h->at<CT>(h->off.st1b);
   x.sb.st2a = h->at<CT>(h->off.st2a);
@@ -546,7 +547,11 @@ CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0) {
   return x;
 }
 
-int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int precision, cudaStream_t st, int l = 0) {
+// Qraw (non-null only with the conservation projection): receives the unprojected operator,
+// the reference of the increment form. The projection of mode 2 depends on f through M, so
+// the increment form adds increments to the unprojected reference and projects the sum.
+int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int precision, cudaStream_t st, int l = 0,
+                 double* Qraw = nullptr) {
   CellTables ct = cell_tables(h, l);
   const int C = h->lev[l].C;
   double* theta = h->at<double>(h->off.theta);
@@ -576,7 +581,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     Scope sc(h, SGS_PROF_REDUCE_IDFT, st, h->cproj ? 5 : 4);
-    return cuda_status(launch_reduce_idft(f, Q, P, x, nullptr, nullptr, st));
+    return cuda_status(launch_reduce_idft(f, Q, P, x, nullptr, nullptr, st, Qraw));
   };
   // Increment form against the reference f_ref (defect correction): with a = f - M, b = f + M,
   //   Q(f) = Q_ref + Q_s(a - a_ref, b) + Q_s(a_ref, b - b_ref)   (exact: Q_s is bilinear),
@@ -612,7 +617,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     Scope sc(h, SGS_PROF_REDUCE_IDFT, st, h->cproj ? 5 : 4);
-    return cuda_status(launch_reduce_idft(f, Q, P, x, part2, h->at<double>(Lv.rQ), st));
+    return cuda_status(launch_reduce_idft(f, Q, P, x, part2, h->at<double>(Lv.rQ), st, Qraw));
   };
   if (precision == SGS_DF64) {
     if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
@@ -643,7 +648,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     Scope sc(h, SGS_PROF_REDUCE_IDFT, st, h->cproj ? 5 : 4);
-    return cuda_status(launch_reduce_idft(f, Q, P, x, nullptr, nullptr, st));
+    return cuda_status(launch_reduce_idft(f, Q, P, x, nullptr, nullptr, st, Qraw));
   }
   if (precision == SGS_FP32) {
     if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
@@ -772,13 +777,17 @@ int vcycle_impl(sgs_handle* h, int l, int levels, double* f, const double* b, in
   }
   // b_H = R_H(I f) - I(R_h), with R_H(I f) the coarse residual field of the restricted iterate
   H.ref = false;
-  if ((r = collide_impl(h, fH0, QH, nullptr, h->precision, st, l + 1))) return r;
-  if (h->precision == SGS_FP32 && h->spectral) {
+  const bool coarse_ref = h->precision == SGS_FP32 && h->spectral;
+  if ((r = collide_impl(h, fH0, QH, nullptr, h->precision, st, l + 1,
+                        coarse_ref && h->cproj ? h->at<double>(H.rQ) : nullptr)))
+    return r;
+  if (coarse_ref) {
     // Coarse FP32 collisions in increment form against I f: the coarse operator then
     // reproduces R_H(I f) exactly at f_H = I f, so FP32 rounding of Q_H(I f) cancels in the
     // coarse correction f_H - I f instead of entering it as noise.
     CollideCtx<float> x = collide_ctx<float>(h, l + 1);
-    cudaError_t e = cudaMemcpyAsync(h->ws + H.rQ, QH, sizeof(double) * K * H.C, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = h->cproj ? cudaSuccess  // the unprojected operator is already in rQ
+                             : cudaMemcpyAsync(h->ws + H.rQ, QH, sizeof(double) * K * H.C, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h->ws + H.rth, h->ws + h->off.theta, sizeof(double) * 5 * H.C, cudaMemcpyDeviceToDevice,
                           st);
@@ -876,7 +885,7 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
   h->dv = 2.0 * h->L / h->N;
   h->precision = problems[0].precision;
   h->spectral = problems[0].collision != SGS_BGK;
-  h->cproj = h->spectral && problems[0].conserve_proj == 1;
+  h->cproj = h->spectral ? problems[0].conserve_proj : 0;
   h->two_d = problems[0].space_dim == 2;
   long long K = (long long)h->N * h->N * h->N;
   h->inst.resize(n_inst);
@@ -988,7 +997,7 @@ int sgs_bind_workspace(sgs_handle* h, void* device_ptr, size_t bytes) {
     if (e == cudaSuccess) e = up(L.cell_off, L.hcell_off.data(), sizeof(long long) * L.hcell_off.size());
     if (e == cudaSuccess) e = up(L.cell_inst, L.hcell_inst.data(), sizeof(int) * L.hcell_inst.size());
   }
-  if (e == cudaSuccess && h->cproj) {
+  if (e == cudaSuccess && h->cproj == 1) {
     double Ainv[25];
     if (!gram_inverse(h->N, h->dv, Ainv)) return SGS_ERR_ARG;
     e = up(h->off.cproj_A, Ainv, sizeof(Ainv));
@@ -1086,11 +1095,12 @@ int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, int lo_iters, do
   int r;
   // FP64 collision and residual of the current iterate f_k: the convergence test
   h->dc_ref = false;
-  if ((r = collide_impl(h, f, Q, P, h->dc_prec, st))) return r;
+  // with the conservation projection the unprojected operator goes straight to Q_ref
+  if ((r = collide_impl(h, f, Q, P, h->dc_prec, st, 0, h->cproj ? h->at<double>(h->off.Q_ref) : nullptr))) return r;
   if (res && (r = residual_impl(h, f, Q, nullptr, res, st))) return r;
   // new reference: f_ref = f_k, theta_ref = theta(f_k), Q_ref = Q_FP64(f_k), ahat_ref = FP32 DFT of f_k - M_k
   cudaError_t e = cudaMemcpyAsync(h->ws + h->off.f_ref, f, sizeof(double) * h->field, cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && !h->cproj)
     e = cudaMemcpyAsync(h->ws + h->off.Q_ref, Q, sizeof(double) * h->field, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->ws + h->off.theta_ref, h->ws + h->off.theta, sizeof(double) * 5 * h->C,
