@@ -39,6 +39,7 @@ struct SweepSmem {
   E S[3][5];           // 1-D sums of the last evaluation (unweighted)
   E S1w[5];            // dimension-1 sums with the step-1 weights |v1|/dx, same evaluation
   E S2w[5];            // dimension-2 sums with the weights |v2|/dy (2-D), same evaluation
+  E Sb[2][5][5];       // Newton evaluations, double-buffered: row r = sums of evaluating warp r
   E svE[5];            // step-1 target s
   E W3[4][kMaxN];      // third factor of each wall's unit Maxwellian
   E red_warp[32][kRedMax];
@@ -53,6 +54,7 @@ struct SweepSmem {
   int flag;
   int ctl;             // broadcast decisions of thread 0
   int wdims;           // space dimensions of the step-1 weights (1: |v1|/dx; 2: + |v2|/dy)
+  int nret;            // Newton result, for the warps that do not evaluate
 };
 
 // ---------------------------------------------------------------------------------------
@@ -199,89 +201,179 @@ __device__ inline void combine(const SweepSmem<E>& sm, E w, int wmode, const E* 
   for (int i = 0; i < 15; i++) A[i] = cf * Aa[i];
 }
 
+// One evaluation by evaluating warp wid (warps 0-2: dimension wid, unweighted; warp 3:
+// dimension 1 weighted by |v1|/dx; warp 4: dimension 2 weighted by |v2|/dy) at the trial
+// theta thE: factors of warps 0-2 to sm.ef, the five 1-D sums to row wid of sm.Sb[buf].
+// The same arithmetic as eval_cta.
+template <typename E>
+__device__ inline void eval_warp(SweepSmem<E>& sm, int N, const E (&thE)[5], int wid, int buf) {
+  const int lane = threadIdx.x & 31;
+  const int d = wid == 3 ? 0 : (wid == 4 ? 1 : wid);
+  E e = cvt<E>(0.0);
+  if (lane < N) {
+    E x = thE[1 + d] * sm.vv[lane] - thE[4] * sm.vq[lane];
+    if (d == 0) x += thE[0];
+    e = exp_in(x);
+  }
+  if (wid < 3) sm.ef[d][lane] = e;
+  if (wid == 3) e = e * sm.c1e[lane];
+  if (wid == 4) e = e * sm.c2e[lane];
+  E s[5];
+  s[0] = e;
+  s[1] = e * sm.vv[lane];
+  s[2] = e * sm.vq[lane];
+  s[3] = s[2] * sm.vv[lane];
+  s[4] = s[2] * sm.vq[lane];
+  warp_allsum<5, E>(s);
+  if (lane < 5) {
+    E t = s[0];
+#pragma unroll
+    for (int q = 1; q < 5; q++)
+      if (lane == q) t = s[q];
+    sm.Sb[buf][wid][lane] = t;
+  }
+}
+
+// combine on the sums of one buffer (rows as in eval_warp).
+template <typename E>
+__device__ inline void combine_rows(const E (*R)[5], E w, int wmode, const E* target, E (&F)[5], float (&A)[15],
+                                    float& fn) {
+  E mom[5];
+  float Aa[15];
+  moments_from_sums<E>(wmode ? R[3] : R[0], R[1], R[2], mom, Aa);
+  if (wmode == 2) {
+    E m2[5];
+    float A2[15];
+    moments_from_sums<E>(R[0], R[4], R[2], m2, A2);
+#pragma unroll
+    for (int i = 0; i < 5; i++) mom[i] += m2[i];
+#pragma unroll
+    for (int i = 0; i < 15; i++) Aa[i] += A2[i];
+  }
+  float amax = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    F[i] = w * mom[i] - target[i];
+    amax = fmaxf(amax, fabsf(tof(F[i])));
+  }
+  fn = amax / fabsf(tof(target[0]));
+  float cf = tof(w);
+#pragma unroll
+  for (int i = 0; i < 15; i++) A[i] = cf * Aa[i];
+}
+
+// Barrier among the evaluating warps only (hardware barrier 1; __syncthreads uses 0).
+__device__ __forceinline__ void eval_bar(int nwarps) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nwarps * 32) : "memory");
+}
+
 // Newton from the theta in th (shared memory). With have_eval the last evaluation (sm.S,
-// sm.S1w, sm.ef) is already at th and is reused. On success th holds the root, the last
-// evaluation is at th, and the return value is the iteration count; -1 on failure. Scalar
-// FP64 decisions are taken by thread 0 and broadcast (FP64 is scarce on this GPU).
+// sm.S1w, sm.S2w, sm.ef) is already at th and is reused. On success th holds the root, the
+// last evaluation is at th, and the return value is the iteration count; -1 on failure.
+//
+// Only the evaluating warps (3 + wdims) take part, and each of them runs the whole iteration
+// itself: it evaluates its dimension into a double-buffered row of sm.Sb, meets the others
+// at one barrier, and then combines the rows, factorises the Jacobian (FP32: inexact Newton)
+// and takes the line-search decisions in registers. All of them read the same rows and the
+// same inputs through the same instructions, so their decisions agree and they pass every
+// barrier the same number of times; one barrier per evaluation replaces the CTA barriers
+// and thread-0 broadcasts of a split design. The FP64 trial theta is formed on lane 0 of
+// each warp and shuffled to its lanes (FP64 is scarce on this GPU).
 template <typename E>
 __device__ __noinline__ int newton_cta(SweepSmem<E>& sm, int N, E w, int wmode, const E* target, double* th,
                                        double L, double tol, int maxit, bool have_eval) {
-  const int wid = threadIdx.x >> 5, tid = threadIdx.x;
-  if (!have_eval) {
-    if (tid < 5) sm.thE[tid] = cvt<E>(th[tid]);
-    __syncthreads();
-    eval_cta<E>(sm, N);
-  }
-  E F[5];
-  float A[15], fnv = 0.0f;
-  if (wid == 0) {
-    combine<E>(sm, w, wmode, target, F, A, fnv);
-    if (tid == 0) sm.fn = fnv;
-  }
-  __syncthreads();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nev = 3 + sm.wdims;
   // Converged as well once the scaled moment residual |F|/rho is at the arithmetic's
   // resolution (double-float and FP64 evaluate F to about 1e-14; 1e-13 bounds the relative
   // error of the Maxwellian near 1e-12 or below): with the residual already
   // there, a further step could only confirm it.
   constexpr float ftol = sizeof(E) == 4 ? 0.0f : 1e-13f;
-  float fn_cur = sm.fn;
-  if (fn_cur <= ftol) return 0;
-  for (int it = 0; it < maxit; it++) {
-    if (wid == 0) {
-      float y[5], Ff[5];
+  if (wid < nev) {
+    double thc[5];
 #pragma unroll
-      for (int i = 0; i < 5; i++) Ff[i] = tof(F[i]);
-      bool ok = chol5_solve(A, Ff, y);
-      if (tid == 0) {
-        sm.flag = ok;
+    for (int k = 0; k < 5; k++) thc[k] = th[k];
+    E F[5];
+    float A[15], fn = 0.0f;
+    int buf = 0, last = -1;  // last: buffer of the latest evaluation (-1: the canonical sums)
+    if (have_eval) {
+      combine<E>(sm, w, wmode, target, F, A, fn);
+    } else {
+      E thE[5];
+#pragma unroll
+      for (int k = 0; k < 5; k++) thE[k] = cvt<E>(thc[k]);
+      eval_warp<E>(sm, N, thE, wid, buf);
+      eval_bar(nev);
+      combine_rows<E>(sm.Sb[buf], w, wmode, target, F, A, fn);
+      last = buf;
+      buf ^= 1;
+    }
+    int ret = 0;
+    if (!(fn <= ftol)) {
+      ret = -1;
+      float fn_cur = fn;
+      for (int it = 0; it < maxit; it++) {
+        float y[5], Ff[5];
+#pragma unroll
+        for (int i = 0; i < 5; i++) Ff[i] = tof(F[i]);
+        if (!chol5_solve(A, Ff, y)) break;
         // exponent change of a full step, |d alpha| + L sum |d beta| + L^2 |d gamma|
         const float Lf = (float)L;
-        sm.stepf = fabsf(y[0]) + Lf * (fabsf(y[1]) + fabsf(y[2]) + fabsf(y[3])) + Lf * Lf * fabsf(y[4]);
-        sm.dir[0] = -(double)y[0];
-        sm.dir[1] = -(double)y[1];
-        sm.dir[2] = -(double)y[2];
-        sm.dir[3] = -(double)y[3];
-        sm.dir[4] = (double)y[4];  // -D A^{-1} F, D = diag(1,1,1,1,-1)
-      }
-    }
-    __syncthreads();
-    if (!sm.flag) return -1;
-    float lam = 1.0f;
-    for (int hv = 0; hv < 40; hv++) {
-      if (tid == 0) {
+        const float stepf = fabsf(y[0]) + Lf * (fabsf(y[1]) + fabsf(y[2]) + fabsf(y[3])) + Lf * Lf * fabsf(y[4]);
+        // -D A^{-1} F, D = diag(1,1,1,1,-1)
+        const double dir[5] = {-(double)y[0], -(double)y[1], -(double)y[2], -(double)y[3], (double)y[4]};
+        float lam = 1.0f;
+        double tt[5];
+        for (int hv = 0; hv < 40; hv++) {
+          E thE[5];
 #pragma unroll
-        for (int k = 0; k < 5; k++) {
-          double t = th[k] + (double)lam * sm.dir[k];
-          sm.th_try[k] = t;
-          sm.thE[k] = cvt<E>(t);
+          for (int k = 0; k < 5; k++) {
+            double t = 0.0;
+            if (lane == 0) t = thc[k] + (double)lam * dir[k];
+            t = __shfl_sync(0xffffffffu, t, 0);
+            tt[k] = t;
+            thE[k] = cvt<E>(t);
+          }
+          eval_warp<E>(sm, N, thE, wid, buf);
+          eval_bar(nev);
+          combine_rows<E>(sm.Sb[buf], w, wmode, target, F, A, fn);
+          last = buf;
+          buf ^= 1;
+          if (fn == fn && (fn <= fn_cur || fn <= 1e-10f)) {
+            fn_cur = fn;
+            break;
+          }
+          lam *= 0.5f;
+        }
+        const float step = lam * stepf;
+#pragma unroll
+        for (int k = 0; k < 5; k++) thc[k] = tt[k];
+        if (!(step == step)) break;
+        if (step <= (float)tol || fn_cur <= ftol) {
+          ret = it + 1;
+          break;
         }
       }
-      __syncthreads();
-      eval_cta<E>(sm, N);
-      if (wid == 0) {
-        combine<E>(sm, w, wmode, target, F, A, fnv);
-        if (tid == 0) sm.fn = fnv;
-      }
-      __syncthreads();
-      float fnt = sm.fn;
-      if (fnt == fnt && (fnt <= fn_cur || fnt <= 1e-10f)) {
-        fn_cur = fnt;
-        break;
-      }
-      lam *= 0.5f;
     }
-    if (tid == 0) {
-      const float step = lam * sm.stepf;
-#pragma unroll
-      for (int k = 0; k < 5; k++) th[k] = sm.th_try[k];
-      sm.ctl = !(step == step) ? -1 : ((step <= (float)tol || fn_cur <= ftol) ? 1 : 0);
+    // publish the result: theta, and the latest evaluation's sums as the canonical ones (its
+    // factors are in sm.ef already)
+    if (wid == 0 && lane < 5) {
+      th[lane] = thc[lane];
+      sm.thE[lane] = cvt<E>(thc[lane]);
     }
-    __syncthreads();
-    int c = sm.ctl;
-    if (c < 0) return -1;
-    if (c > 0) return it + 1;
+    if (last >= 0 && lane < 5) {
+      const E t = sm.Sb[last][wid][lane];
+      if (wid < 3)
+        sm.S[wid][lane] = t;
+      else if (wid == 3)
+        sm.S1w[lane] = t;
+      else
+        sm.S2w[lane] = t;
+    }
+    if (wid == 0 && lane == 0) sm.nret = ret;
   }
-  return -1;
+  __syncthreads();
+  return sm.nret;
 }
 
 template <typename E>
