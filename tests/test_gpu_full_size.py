@@ -1,0 +1,143 @@
+"""GPU parity at the full sizes of the measured workloads, in the launch configuration the
+benchmark times.
+
+- Heat transfer, 64 cells, 32^3 velocities on [-8, 8]^3, eps = 0.01: one forward and one
+  backward scan of the mixed solver (double-float scan, 8 nodes per thread x 16 CTAs x 256
+  threads, the shape the benchmark's autotuner picks) and of the FP64 solver against the
+  oracle's scans from the same state with the oracle's P, fixed inner count; 1e-11
+  (double-float) and 1e-12 (FP64).
+- Converged solutions (heat: defect correction + 2-level V-cycles; lid-driven cavity,
+  64 x 64 cells, 24^3: defect correction + 3-level V-cycles) reach an FP64 residual of
+  1e-8 on the GPU; the oracle then recomputes, one sampled cell at a time, its own
+  collision operator and the cell's share of the residual sqrt(dx dy sum_k w R^2) of the
+  GPU's final state, which must stay below the same 1e-8.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2409_01910_gb300 import inputs as I
+from paper_2409_01910_gb300 import sgs
+
+pytestmark = pytest.mark.gpu
+BENCH_SHAPE = (8, 16, 256)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sgs.lib()
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x).reshape(-1)).cuda()
+
+
+def heat(oracle, precision, inner_fixed=6):
+    wl = I.heat_64cells_32v(seed=0)
+    common = dict(eps=wl.eps, bc_T=(wl.T_left, wl.T_right), total_mass=wl.total_mass, inner_fixed=inner_fixed)
+    g = sgs.Problem(nx=wl.J, nv=wl.N, v_max=wl.L, precision=precision, **common)
+    o = oracle.Problem(N=wl.N, L=wl.L, J=wl.J, **common)
+    return wl, g, o
+
+
+@pytest.fixture(scope="module")
+def heat_initial(oracle):
+    """The initial state and the oracle's collision step of all 64 cells (shared)."""
+    wl, _, o = heat(oracle, sgs.FP64)
+    f0 = wl.initial_state()
+    Qo, Po, nuo = oracle.collide(o, f0)
+    return f0, Po, nuo
+
+
+@pytest.mark.parametrize("direction", [1, -1])
+@pytest.mark.parametrize("precision,shape,tol", [(sgs.FP32, BENCH_SHAPE, 1e-11), (sgs.FP64, None, 1e-12)])
+def test_heat_full_size_scan_parity(oracle, heat_initial, precision, shape, tol, direction):
+    f0, Po, nuo = heat_initial
+    wl, g, o = heat(oracle, precision)
+    fo = f0.copy()
+    oracle.sweep(o, fo, Po, nuo, direction)
+    s = sgs.Solver(g)
+    if shape is not None:
+        s.set_sweep_shape(*shape)
+        assert s.sweep_shape() == shape
+    f = dev(f0)
+    Q, P = s.field(), s.field()
+    s.collide(f, Q, P)  # the scan reads the collision frequencies of f0 from this step
+    if direction > 0:
+        s.sweep_forward(f, dev(Po))
+    else:
+        s.sweep_backward(f, dev(Po))
+    st = s.read_status()
+    assert st["status"] == 0 and st["visits"] == wl.J and st["inner_iters"] == 6 * wl.J
+    assert rel(f.cpu().numpy().reshape(f0.shape), fo) <= tol
+
+
+def sampled_cell_residuals(oracle, residual_fn, o, f, cells, dxdy):
+    """The oracle's collision operator at the sampled cells only (zeros elsewhere: the
+    residual of a cell uses its own Q) and each sampled cell's share of the residual."""
+    Q = np.zeros_like(f)
+    for c in cells:
+        Q[c] = oracle.collide_cell(o if not hasattr(o, "base") else o.base, f[c])[0]
+    _, R = residual_fn(o, f, Q, return_field=True)
+    N = f.shape[1]
+    w = (2 * o_L(o) / N) ** 3
+    return {c: float(np.sqrt(dxdy * w * (R[c] ** 2).sum())) for c in cells}
+
+
+def o_L(o):
+    return o.base.L if hasattr(o, "base") else o.L
+
+
+def test_heat_full_size_converged_residual_sampled(oracle):
+    wl, g, o = heat(oracle, sgs.FP32, inner_fixed=0)
+    s = sgs.Solver(g)
+    s.set_sweep_shape(*BENCH_SHAPE)
+    f = dev(wl.initial_state())
+    Q, P = s.field(), s.field()
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for cycle in range(40):
+        s.dc_step(f, Q, P, 0, res=res)
+        if res.item() < 1e-8:
+            break
+        for _ in range(2):
+            s.vcycle(f, 2, 1, 1, 4)
+    assert res.item() < 1e-8 and s.read_status()["status"] == 0
+    fh = f.cpu().numpy().reshape(wl.J, wl.N, wl.N, wl.N)
+    cells = [0, 1, 21, 42, wl.J - 2, wl.J - 1]
+    r = sampled_cell_residuals(oracle, oracle.residual, o, fh, cells, 1.0 / wl.J)
+    print("heat: GPU residual", res.item(), "oracle per-cell residuals", r)
+    assert max(r.values()) < 1e-8
+
+
+def test_cavity_full_size_converged_residual_sampled(oracle):
+    wl = I.cavity_64x64_24v()
+    lid = ((0.0, 0.0, 0.0), (wl.lid, 0.0, 0.0))
+    g = sgs.Problem(space_dim=2, nx=wl.nx, ny=wl.ny, nv=wl.N, v_max=wl.L, eps=wl.eps, bc_T=(wl.T_wall, wl.T_wall),
+                    bc_T_y=(wl.T_wall, wl.T_wall), bc_u_y=lid, total_mass=wl.total_mass, precision=sgs.FP32)
+    base = oracle.Problem(N=wl.N, L=wl.L, J=wl.nx, eps=wl.eps, bc_T=(wl.T_wall, wl.T_wall), total_mass=wl.total_mass)
+    o = oracle.Problem2D(base=base, ny=wl.ny, bc_T_y=(wl.T_wall, wl.T_wall), bc_u_y=lid)
+    s = sgs.Solver(g)
+    f = dev(wl.initial_state())
+    Q, P = s.field(), s.field()
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for cycle in range(30):
+        s.dc_step(f, Q, P, 0, res=res)
+        if res.item() < 1e-8:
+            break
+        for _ in range(2):
+            s.vcycle(f, 3, 1, 1, 4)
+    assert res.item() < 1e-8 and s.read_status()["status"] == 0
+    fh = f.cpu().numpy().reshape(wl.J, wl.N, wl.N, wl.N)
+    nx = wl.nx
+    cells = [0, nx - 1, (wl.ny - 1) * nx, wl.J - 1, (wl.ny // 2) * nx + nx // 2, (wl.ny - 2) * nx + 7]
+    r = sampled_cell_residuals(oracle, oracle.residual2d, o, fh, cells, 1.0 / wl.J)
+    print("cavity: GPU residual", res.item(), "oracle per-cell residuals", r)
+    assert max(r.values()) < 1e-8
