@@ -40,6 +40,7 @@ struct SweepSmem {
   E S1w[5];            // dimension-1 sums with the step-1 weights |v1|/dx, same evaluation
   E S2w[5];            // dimension-2 sums with the weights |v2|/dy (2-D), same evaluation
   E Sb[2][5][5];       // Newton evaluations, double-buffered: row r = sums of evaluating warp r
+  E Gs[3][6];          // per-dimension sums for the norm of M+ - M[g] (derived residual)
   E svE[5];            // step-1 target s
   E W3[4][kMaxN];      // third factor of each wall's unit Maxwellian
   E red_warp[32][kRedMax];
@@ -431,6 +432,45 @@ __device__ __noinline__ int solve_mg(SweepSmem<E>& sm, int N, E w, const E* mom,
   return it;
 }
 
+// After a step-2 update the cell equation holds up to the Maxwellians:
+//   (|v1|/dx + A) g + r = A M+   =>   R(g) = A (M+ - M[g]),   A = nu/eps,
+// where M+ is the Maxwellian step 2 used (step 1's, else M[g_old]). The norm of R then comes
+// from per-dimension sums of the two factorisations P (M+, sm.Ep) and Q (M[g], sm.Eg): with
+// d = Q - P per dimension, Q1Q2Q3 - P1P2P3 = d1 P2 P3 + Q1 d2 P3 + Q1 Q2 d3, whose squared
+// norm is a sum of products of 1-D sums (no cancellation of large terms). Likewise the
+// step-1 target s = sum w phi (c (M[g] - g) - r) (eq. (26)) with c g + r = A M+ - A g is
+//   s = sum w phi c M[g] - A sum w phi M+ + A sum w phi g,
+// from the separable sums of the last evaluation (M[g]'s), the moments of M+ and those of
+// g. No pass over the nodes and no cluster reduction. Warps 0-2 form the sums; the caller's
+// thread 0 takes the decisions. Returns the squared norm sum_k (M+ - M[g])^2 in thread 0.
+template <typename E>
+__device__ inline void derived_sums(SweepSmem<E>& sm) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (wid < 3) {
+    const E p = sm.Ep[wid][lane], q = sm.Eg[wid][lane], dl = q - p;
+    E x[6] = {p * p, p * dl, dl * dl, p * q, dl * q, q * q};
+    warp_allsum<6, E>(x);
+    if (lane < 6) {
+      E t = x[0];
+#pragma unroll
+      for (int k = 1; k < 6; k++)
+        if (lane == k) t = x[k];
+      sm.Gs[wid][lane] = t;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename E>
+__device__ inline E derived_norm2(const SweepSmem<E>& sm) {
+  // columns of Gs: 0 PP, 1 Pd, 2 dd, 3 PQ, 4 dQ, 5 QQ
+  const E* a = sm.Gs[0];
+  const E* b = sm.Gs[1];
+  const E* c = sm.Gs[2];
+  E cross = a[4] * b[1] * c[0] + a[4] * b[3] * c[1] + a[5] * b[4] * c[1];
+  return a[2] * b[0] * c[0] + a[5] * b[2] * c[0] + a[5] * b[5] * c[2] + cvt<E>(2.0) * cross;
+}
+
 template <typename E, int EPT>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   cg::cluster_group cl = cg::this_cluster();
@@ -548,49 +588,57 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     have_th = true;
 
     int it = 0;
-    for (;;) {
-      // ---- pass B: cell-equation residual, its scale, and the step-1 target s (eq. (26))
-      E e12 = sm.Eg[0][i1] * sm.Eg[1][i2];
-      E rs = zero, sc = zero, b0 = zero, b3 = zero, b4 = zero;
-      if (own) {
+    // decisions from the step-2 identity (double-float and FP64 scans) after the first update
+    bool derived = false;
+    E momg[5];  // moments of the current iterate g
 #pragma unroll
-        for (int t = 0; t < EPT; t++) {
-          E M = e12 * sm.Eg[2][i30 + t];
-          // (|v1|/dx) g + r - (nu/eps)(M - g) = (|v1|/dx + nu/eps) g + r - (nu/eps) M
-          E res = c1A * g[t] + r[t] - Acoef * M;
-          rs += res * res;
-          E mag = c1A * g[t];
-          sc += mag * mag;
-          E tt = c1 * (M - g[t]) - r[t];
-          b0 += tt;
-          b3 += tt * sm.vv[i30 + t];
-          b4 += tt * sm.vq[i30 + t];
+    for (int k = 0; k < 5; k++) momg[k] = mom[k];
+    for (;;) {
+      if (!derived) {
+        // ---- pass B: cell-equation residual, its scale, and the step-1 target s (eq. (26))
+        E e12 = sm.Eg[0][i1] * sm.Eg[1][i2];
+        E rs = zero, sc = zero, b0 = zero, b3 = zero, b4 = zero;
+        if (own) {
+#pragma unroll
+          for (int t = 0; t < EPT; t++) {
+            E M = e12 * sm.Eg[2][i30 + t];
+            // (|v1|/dx) g + r - (nu/eps)(M - g) = (|v1|/dx + nu/eps) g + r - (nu/eps) M
+            E res = c1A * g[t] + r[t] - Acoef * M;
+            rs += res * res;
+            E mag = c1A * g[t];
+            sc += mag * mag;
+            E tt = c1 * (M - g[t]) - r[t];
+            b0 += tt;
+            b3 += tt * sm.vv[i30 + t];
+            b4 += tt * sm.vq[i30 + t];
+          }
         }
+        E v7[7] = {rs, b0, v1 * b0, v2 * b0, b3, vq12 * b0 + b4, sc};
+        double t6[7];
+        cluster_reduce<7, E>(v7, t6, sm, buf, cl, CS);
+        // thread 0 decides: stop, and whether step 1 is attempted (existence test, eq. (26))
+        if (tid == 0) {
+          const double res = sqrt(wd * t6[0]);
+          double tol = I.inner_tol;
+          if (lowp) tol = fmax(tol, 2e-6 * sqrt(wd * t6[6]));
+          bool stop;
+          if (I.inner_fixed > 0) {
+            stop = it >= I.inner_fixed;
+          } else {
+            stop = res < tol || it >= I.inner_max;
+            if (stop && !(res < tol)) status |= SGS_ST_INNER_CAP;
+          }
+          if (!(res == res)) {
+            status |= SGS_ST_NONFINITE;
+            stop = true;
+          }
+          double sd[5] = {wd * t6[1], wd * t6[2], wd * t6[3], wd * t6[4], wd * t6[5]};
+          bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+          sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
+        }
+        if (tid < 5) sm.svE[tid] = w * sm.red_tote[1 + tid];
+        __syncthreads();
       }
-      E v7[7] = {rs, b0, v1 * b0, v2 * b0, b3, vq12 * b0 + b4, sc};
-      double t6[7];
-      cluster_reduce<7, E>(v7, t6, sm, buf, cl, CS);
-      // thread 0 decides: stop, and whether step 1 is attempted (existence test, eq. (26))
-      if (tid == 0) {
-        const double res = sqrt(wd * t6[0]);
-        double tol = I.inner_tol;
-        if (lowp) tol = fmax(tol, 2e-6 * sqrt(wd * t6[6]));
-        bool stop;
-        if (I.inner_fixed > 0) {
-          stop = it >= I.inner_fixed;
-        } else {
-          stop = res < tol || it >= I.inner_max;
-          if (stop && !(res < tol)) status |= SGS_ST_INNER_CAP;
-        }
-        if (!(res == res)) {
-          status |= SGS_ST_NONFINITE;
-          stop = true;
-        }
-        double sd[5] = {wd * t6[1], wd * t6[2], wd * t6[3], wd * t6[4], wd * t6[5]};
-        bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
-        sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
-      }
-      __syncthreads();
       const int ctl = sm.ctl;
       if (ctl & 1) break;
 
@@ -600,7 +648,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         if (ctl & 2) {
           E sv[5];
 #pragma unroll
-          for (int k = 0; k < 5; k++) sv[k] = w * sm.red_tote[1 + k];
+          for (int k = 0; k < 5; k++) sv[k] = sm.svE[k];
           if (tid < 5) sm.thp[tid] = sm.thg[tid];
           __syncthreads();
           // the last evaluation is M[g]'s: reused as the first one of step 1
@@ -616,6 +664,19 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       }
       const bool eval_at_start = used || !(ctl & 2);  // last evaluation at the warm start below
       E (*Eu)[kMaxN] = used ? sm.Ep : sm.Eg;
+      // moments of M+: step 1's last evaluation is at M+; M[g] has the moments of g
+      E momP[5];
+      if (!lowp) {
+        if (used) {
+          float Aa[15];
+          moments_from_sums<E>(sm.S[0], sm.S[1], sm.S[2], momP, Aa);
+#pragma unroll
+          for (int k = 0; k < 5; k++) momP[k] = w * momP[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 5; k++) momP[k] = momg[k];
+        }
+      }
 
       // ---- step 2 (eq. (25)) and the moments of the new iterate
       E ep = Eu[0][i1] * Eu[1][i2];
@@ -630,6 +691,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           c4 += x * sm.vq[i30 + t];
         }
       }
+      // keep the factors of M+ in sm.Ep (the reduction below orders this before solve_mg)
+      if (!lowp && !used && tid < 3 * kMaxN) sm.Ep[tid / kMaxN][tid % kMaxN] = sm.Eg[tid / kMaxN][tid % kMaxN];
       E m5[5] = {c0, v1 * c0, v2 * c0, c3, vq12 * c0 + c4};
       double t5[5];
       cluster_reduce<5, E>(m5, t5, sm, buf, cl, CS);
@@ -641,6 +704,41 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       int n2 = solve_mg<E>(sm, N, w, mm, used ? sm.thp : sm.thg, eval_at_start, L, ntol, I.newton_max, status);
       if (n2 > 0) c_newton += n2;
       c_solves++;
+      if (!lowp) {
+        // ---- residual and step-1 target of the new iterate from the step-2 identity
+        derived_sums<E>(sm);
+        if (tid == 0) {
+          E mw[5];
+          float Aa[15];
+          moments_from_sums<E>(sm.S1w, sm.S[1], sm.S[2], mw, Aa);  // sum phi (|v1|/dx) M[g]
+          const double Ad = tod(Acoef);
+          const double res = fabs(Ad) * sqrt(wd * tod(derived_norm2<E>(sm)));
+          bool stop;
+          if (I.inner_fixed > 0) {
+            stop = it >= I.inner_fixed;
+          } else {
+            stop = res < I.inner_tol || it >= I.inner_max;
+            if (stop && !(res < I.inner_tol)) status |= SGS_ST_INNER_CAP;
+          }
+          if (!(res == res)) {
+            status |= SGS_ST_NONFINITE;
+            stop = true;
+          }
+          double sd[5];
+#pragma unroll
+          for (int k = 0; k < 5; k++) {
+            E sk = w * mw[k] - Acoef * momP[k] + Acoef * mm[k];
+            sm.svE[k] = sk;
+            sd[k] = tod(sk);
+          }
+          bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+          sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 5; k++) momg[k] = mm[k];
+        derived = true;
+      }
     }
 
     if (own) {
