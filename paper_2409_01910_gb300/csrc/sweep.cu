@@ -905,47 +905,55 @@ __global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int 
   }
 
   int it = 0;
-  for (;;) {
-    // ---- pass B: cell-equation residual, its scale, and the step-1 target s (eq. (26))
-    E e12 = sm.Eg[0][i1] * sm.Eg[1][i2];
-    E rs = zero, sc = zero, b0 = zero, b3 = zero, b4 = zero;
-    if (own) {
+  // decisions from the step-2 identity (double-float and FP64 scans) after the first update
+  bool derived = false;
+  E momg[5];  // moments of the current iterate g
 #pragma unroll
-      for (int t = 0; t < EPT; t++) {
-        E M = e12 * sm.Eg[2][i30 + t];
-        E res = cA * g[t] + r[t] - Acoef * M;
-        rs += res * res;
-        E mag = cA * g[t];
-        sc += mag * mag;
-        E tt = cw * (M - g[t]) - r[t];
-        b0 += tt;
-        b3 += tt * sm.vv[i30 + t];
-        b4 += tt * sm.vq[i30 + t];
+  for (int k = 0; k < 5; k++) momg[k] = mom[k];
+  for (;;) {
+    if (!derived) {
+      // ---- pass B: cell-equation residual, its scale, and the step-1 target s (eq. (26))
+      E e12 = sm.Eg[0][i1] * sm.Eg[1][i2];
+      E rs = zero, sc = zero, b0 = zero, b3 = zero, b4 = zero;
+      if (own) {
+#pragma unroll
+        for (int t = 0; t < EPT; t++) {
+          E M = e12 * sm.Eg[2][i30 + t];
+          E res = cA * g[t] + r[t] - Acoef * M;
+          rs += res * res;
+          E mag = cA * g[t];
+          sc += mag * mag;
+          E tt = cw * (M - g[t]) - r[t];
+          b0 += tt;
+          b3 += tt * sm.vv[i30 + t];
+          b4 += tt * sm.vq[i30 + t];
+        }
       }
+      E v7[7] = {rs, b0, v1 * b0, v2 * b0, b3, vq12 * b0 + b4, sc};
+      double t6[7];
+      cluster_reduce<7, E>(v7, t6, sm, buf, cl, CS);
+      if (tid == 0) {
+        const double res = sqrt(wd * t6[0]);
+        double tol = I.inner_tol;
+        if (lowp) tol = fmax(tol, 2e-6 * sqrt(wd * t6[6]));
+        bool stop;
+        if (I.inner_fixed > 0) {
+          stop = it >= I.inner_fixed;
+        } else {
+          stop = res < tol || it >= I.inner_max;
+          if (stop && !(res < tol)) status |= SGS_ST_INNER_CAP;
+        }
+        if (!(res == res)) {
+          status |= SGS_ST_NONFINITE;
+          stop = true;
+        }
+        double sd[5] = {wd * t6[1], wd * t6[2], wd * t6[3], wd * t6[4], wd * t6[5]};
+        bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+        sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
+      }
+      if (tid < 5) sm.svE[tid] = w * sm.red_tote[1 + tid];
+      __syncthreads();
     }
-    E v7[7] = {rs, b0, v1 * b0, v2 * b0, b3, vq12 * b0 + b4, sc};
-    double t6[7];
-    cluster_reduce<7, E>(v7, t6, sm, buf, cl, CS);
-    if (tid == 0) {
-      const double res = sqrt(wd * t6[0]);
-      double tol = I.inner_tol;
-      if (lowp) tol = fmax(tol, 2e-6 * sqrt(wd * t6[6]));
-      bool stop;
-      if (I.inner_fixed > 0) {
-        stop = it >= I.inner_fixed;
-      } else {
-        stop = res < tol || it >= I.inner_max;
-        if (stop && !(res < tol)) status |= SGS_ST_INNER_CAP;
-      }
-      if (!(res == res)) {
-        status |= SGS_ST_NONFINITE;
-        stop = true;
-      }
-      double sd[5] = {wd * t6[1], wd * t6[2], wd * t6[3], wd * t6[4], wd * t6[5]};
-      bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
-      sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
-    }
-    __syncthreads();
     const int ctl = sm.ctl;
     if (ctl & 1) break;
 
@@ -955,7 +963,7 @@ __global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int 
       if (ctl & 2) {
         E sv[5];
 #pragma unroll
-        for (int k = 0; k < 5; k++) sv[k] = w * sm.red_tote[1 + k];
+        for (int k = 0; k < 5; k++) sv[k] = sm.svE[k];
         if (tid < 5) sm.thp[tid] = sm.thg[tid];
         __syncthreads();
         int n1 = newton_cta<E>(sm, N, w, 2, sv, sm.thp, L, ntol, I.newton_max, true);
@@ -970,6 +978,19 @@ __global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int 
     }
     const bool eval_at_start = used || !(ctl & 2);
     E (*Eu)[kMaxN] = used ? sm.Ep : sm.Eg;
+    // moments of M+: step 1's last evaluation is at M+; M[g] has the moments of g
+    E momP[5];
+    if (!lowp) {
+      if (used) {
+        float Aa[15];
+        moments_from_sums<E>(sm.S[0], sm.S[1], sm.S[2], momP, Aa);
+#pragma unroll
+        for (int k = 0; k < 5; k++) momP[k] = w * momP[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 5; k++) momP[k] = momg[k];
+      }
+    }
 
     // ---- step 2 (eq. (25)) and the moments of the new iterate
     E ep = Eu[0][i1] * Eu[1][i2];
@@ -984,6 +1005,8 @@ __global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int 
         c4 += x * sm.vq[i30 + t];
       }
     }
+    // keep the factors of M+ in sm.Ep (the reduction below orders this before solve_mg)
+    if (!lowp && !used && tid < 3 * kMaxN) sm.Ep[tid / kMaxN][tid % kMaxN] = sm.Eg[tid / kMaxN][tid % kMaxN];
     E m5[5] = {c0, v1 * c0, v2 * c0, c3, vq12 * c0 + c4};
     double t5[5];
     cluster_reduce<5, E>(m5, t5, sm, buf, cl, CS);
@@ -994,6 +1017,43 @@ __global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int 
     int n2 = solve_mg<E>(sm, N, w, mm, used ? sm.thp : sm.thg, eval_at_start, L, ntol, I.newton_max, status);
     if (n2 > 0) c_newton += n2;
     c_solves++;
+    if (!lowp) {
+      // ---- residual and step-1 target of the new iterate from the step-2 identity (the
+      //      step-1 weight |v1|/dx + |v2|/dy is a sum of two separable terms)
+      derived_sums<E>(sm);
+      if (tid == 0) {
+        E mw[5], mw2[5];
+        float Aa[15];
+        moments_from_sums<E>(sm.S1w, sm.S[1], sm.S[2], mw, Aa);
+        moments_from_sums<E>(sm.S[0], sm.S2w, sm.S[2], mw2, Aa);
+        const double Ad = tod(Acoef);
+        const double res = fabs(Ad) * sqrt(wd * tod(derived_norm2<E>(sm)));
+        bool stop;
+        if (I.inner_fixed > 0) {
+          stop = it >= I.inner_fixed;
+        } else {
+          stop = res < I.inner_tol || it >= I.inner_max;
+          if (stop && !(res < I.inner_tol)) status |= SGS_ST_INNER_CAP;
+        }
+        if (!(res == res)) {
+          status |= SGS_ST_NONFINITE;
+          stop = true;
+        }
+        double sd[5];
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+          E sk = w * (mw[k] + mw2[k]) - Acoef * momP[k] + Acoef * mm[k];
+          sm.svE[k] = sk;
+          sd[k] = tod(sk);
+        }
+        bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+        sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 5; k++) momg[k] = mm[k];
+      derived = true;
+    }
   }
 
   if (own) {
