@@ -82,6 +82,31 @@ def dist_env():
     return rank, world, local
 
 
+def rank_barrier(world):
+    """Barrier across the ranks around a timed region (N > 1)."""
+    if world > 1:
+        import torch
+
+        torch.distributed.barrier()
+
+
+def max_over_ranks(ms, world, device="cpu"):
+    """The slowest rank's time: a timed region lasts until every rank is done."""
+    if world <= 1:
+        return float(ms)
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_total):
+    """Units processed by all ranks per second of the slowest rank's time (weak scaling:
+    every rank runs the same independent work)."""
+    return world * units_per_rank / (ms_total * 1e-3)
+
+
 # ------------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
@@ -254,8 +279,7 @@ def run_native(args, rank, world, local):
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    rank_barrier(world)
     s.profile(True)
     s.profile_read()
     launches0 = s.launch_count()
@@ -268,16 +292,13 @@ def run_native(args, rank, world, local):
             step(args.warmup + i)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        rank_barrier(world)
     launches = s.launch_count() - launches0
     prof = s.profile_read()
     s.profile(False)
     ms_steps = [a.elapsed_time(b) for a, b in ev]
-    ms_total = float(sum(ms_steps))
-    if world > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = world * visits_per_step * args.steps / (ms_total * 1e-3)
+    ms_total = max_over_ranks(sum(ms_steps), world, dev)
+    value = whole_job_rate(visits_per_step * args.steps, world, ms_total)
     status = s.read_status()
 
     # dominant kernel class and its roofline
@@ -636,6 +657,7 @@ def run_batch(args, rank, world, local):
     for _ in range(max(0, args.warmup - 1)):
         b.step()
     torch.cuda.synchronize()
+    rank_barrier(world)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stream = torch.cuda.current_stream()
     with ClockSampler(local) as clk:
@@ -645,7 +667,8 @@ def run_batch(args, rank, world, local):
             b.step()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
-    ms_total = float(sum(a.elapsed_time(c) for a, c in ev))
+        rank_barrier(world)
+    ms_total = max_over_ranks(sum(a.elapsed_time(c) for a, c in ev), world, torch.device("cuda", local))
     res = b.residuals()
     # per-kernel timings and launch count of one eager cycle (a replay runs exactly the
     # kernels the captured cycle enqueued; replays themselves are not profiled)
@@ -698,7 +721,7 @@ def run_batch(args, rank, world, local):
     h2d = sum(2 * hostf[nv].numel() * 8 for nv in b.groups)
     d2h = sum(hres[nv].numel() * 8 for nv in b.groups)
     out = {
-        "metric": METRIC, "value": world * visits_per_step * args.steps / (ms_total * 1e-3), "unit": UNIT,
+        "metric": METRIC, "value": whole_job_rate(visits_per_step * args.steps, world, ms_total), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"heat1d_batch{args.batch_size}", "instances": args.batch_size, "cells": cells,
