@@ -358,3 +358,49 @@ def test_dc_vcycle_tracks_fp64_vcycle():
     err = rel(fdc.cpu().numpy(), f64.cpu().numpy())
     print("dc+vcycle vs fp64 vcycle rel", err)
     assert err <= 5e-8
+
+
+@pytest.mark.parametrize("precision,tol", [(sgs.FP64, 1e-12), (sgs.FP32, 1e-11)])
+@pytest.mark.parametrize("direction", [1, -1])
+def test_sweep_plain_fixed_point_parity(oracle, precision, tol, direction):
+    """SGS-FP (eq. (22): no step 1, the Maxwellian of the current iterate in step 2) with a
+    fixed inner count, in the FP64 and the double-float scan."""
+    N, J, L = 8, 6, 6.0
+    d = spec(nx=J, nv=N, v_max=L, eps=0.5, inner_fixed=7, inner_method=sgs.FP, precision=precision)
+    f0 = I.initial_state(J, N, L, T=1.5, seed=12)
+    po = oracle_problem(oracle, d)
+    Qo, Po, nuo = oracle.collide(po, f0)
+    fo = f0.copy()
+    oracle.sweep(po, fo, Po, nuo, direction)
+    s = sgs.Solver(gpu_problem(d))
+    fd = to_dev(f0)
+    Q, P = s.field(), s.field()
+    s.collide(fd, Q, P)
+    if direction > 0:
+        s.sweep_forward(fd, to_dev(Po))
+    else:
+        s.sweep_backward(fd, to_dev(Po))
+    st = s.read_status()
+    assert st["status"] == 0 and st["inner_iters"] == 7 * J and st["fallbacks"] == 0
+    assert rel(fd.cpu().numpy().reshape(f0.shape), fo) <= tol
+
+
+def test_sweep_plain_fixed_point_tolerance_mode(oracle):
+    """SGS-FP to an inner tolerance: the cell equations are solved to that tolerance on both
+    sides (the stopping test on the GPU uses the step-2 identity after the first update)."""
+    N, J, L = 8, 6, 6.0
+    d = spec(nx=J, nv=N, v_max=L, eps=1.0, inner_tol=1e-11, inner_method=sgs.FP)
+    f0 = I.initial_state(J, N, L, T=1.5, seed=13)
+    po = oracle_problem(oracle, d)
+    Qo, Po, nuo = oracle.collide(po, f0)
+    fo = f0.copy()
+    sto = oracle.sweep(po, fo, Po, nuo, 1)
+    s = sgs.Solver(gpu_problem(d))
+    fd = to_dev(f0)
+    Q, P = s.field(), s.field()
+    s.collide(fd, Q, P)
+    s.sweep_forward(fd, to_dev(Po))
+    st = s.read_status()
+    assert st["status"] == 0
+    assert abs(st["inner_iters"] - sto["inner_iters"]) <= J
+    assert rel(fd.cpu().numpy().reshape(f0.shape), fo) <= 1e-9
