@@ -24,7 +24,7 @@ SRC2D = os.path.join(HERE, "sgs_oracle2d.c")
 
 MAXWELL, HARD_SPHERE, BGK = 0, 1, 2
 DIFFUSE, INFLOW = 0, 1
-PFP, FP = 0, 1
+PFP, FP, PFP_RELAX = 0, 1, 2
 
 
 def build(force: bool = False) -> str:

@@ -732,7 +732,7 @@ int or_cell_solve_c(const or_problem* p, const double* c, const double* r, doubl
       if (it == p->inner_max) break;
     }
     const double* Mplus = Mg;
-    if (p->inner_method == OR_PFP) {
+    if (p->inner_method == OR_PFP || p->inner_method == OR_PFP_RELAX) {
       /* s = sum w phi ((|v1|/dx)(M[g] - g) - r) */
       double s[5] = {0, 0, 0, 0, 0};
       for (int i1 = 0; i1 < N; i1++)
@@ -748,6 +748,34 @@ int or_cell_solve_c(const or_problem* p, const double* c, const double* r, doubl
             s[4] += e * vv;
           }
       int exists = s[0] > 0.0 && s[0] * s[4] > s[1] * s[1] + s[2] * s[2] + s[3] * s[3];
+      if (!exists && p->inner_method == OR_PFP_RELAX) {
+        /* Relaxed step 1 (the remark after eq. (26)): with a factor 1 + tau on the weighted
+         * moments of the new and the current Maxwellian, the target becomes
+         *   s_tau = (tau m_w + s) / (1 + tau),   m_w = sum w phi (|v1|/dx) M[g],
+         * tau = 0 being step 1 and tau -> infinity the source iteration (M+ = M[g]).
+         * 1 + tau = 2, 4, 8, ...: the first that passes eq. (26) is taken. */
+        double mw[5] = {0, 0, 0, 0, 0};
+        for (int i1 = 0; i1 < N; i1++)
+          for (int i2 = 0; i2 < N; i2++)
+            for (int i3 = 0; i3 < N; i3++) {
+              long i = ((long)i1 * N + i2) * N + i3;
+              double e = w * c[i] * Mg[i];
+              double vv = v[i1] * v[i1] + v[i2] * v[i2] + v[i3] * v[i3];
+              mw[0] += e;
+              mw[1] += e * v[i1];
+              mw[2] += e * v[i2];
+              mw[3] += e * v[i3];
+              mw[4] += e * vv;
+            }
+        for (double q = 2.0; q <= 1048576.0 && !exists; q *= 2.0) {
+          double t[5];
+          for (int k = 0; k < 5; k++) t[k] = ((q - 1.0) * mw[k] + s[k]) / q;
+          if (t[0] > 0.0 && t[0] * t[4] > t[1] * t[1] + t[2] * t[2] + t[3] * t[3]) {
+            exists = 1;
+            for (int k = 0; k < 5; k++) s[k] = t[k];
+          }
+        }
+      }
       if (exists) {
         double thp[5];
         memcpy(thp, thg, sizeof(thp));

@@ -24,7 +24,7 @@ extern "C" {
 
 enum { OR_MAXWELL = 0, OR_HARD_SPHERE = 1, OR_BGK = 2 };
 enum { OR_DIFFUSE = 0, OR_INFLOW = 1 };
-enum { OR_PFP = 0, OR_FP = 1 };
+enum { OR_PFP = 0, OR_FP = 1, OR_PFP_RELAX = 2 };
 
 typedef struct {
   int N;            /* velocity points per dimension */
@@ -39,7 +39,7 @@ typedef struct {
   double total_mass;   /* C of the mass constraint; <= 0 disables the rescale */
   double inner_tol; int inner_max, inner_fixed;
   double newton_tol; int newton_max;
-  int inner_method;    /* OR_PFP or OR_FP */
+  int inner_method;    /* OR_PFP, OR_FP, or OR_PFP_RELAX (relaxed step 1 when eq. (26) fails) */
   int conserve_proj;   /* 1: project Q onto the zero-moment subspace (not in the paper);
                           2: the same with the correction weighted by the local Maxwellian */
 } or_problem;

@@ -175,3 +175,39 @@ def test_paper_sanity_iteration_counts(oracle):
     assert pfp["inner_iters"] / pfp["visits"] < 11
     assert fp["inner_iters"] / fp["visits"] > 5 * pfp["inner_iters"] / pfp["visits"]
     assert pfp["newton_iters"] / pfp["newton_solves"] < 8
+
+
+def test_relaxed_step1_when_existence_fails(oracle):
+    """A cell equation with a known solution g* (r = A M[g*] - (|v1|/dx + A) g*), started
+    from two counter-moving beams at v1 = +-3 whose step-1 target violates eq. (26)
+    (s0 < 0: the beams carry more |v1|-weighted mass than their Maxwellian). PFP with the
+    fixed-point fallback, plain FP, and PFP with the relaxed step 1 of the remark after
+    eq. (26) all reach g*; the relaxed form needs no fallback."""
+    N, L, dx, eps, nu = 12, 6.0, 0.05, 1.0, 1.0
+    A = nu / eps
+    v = oracle.velocity_nodes(N, L)
+    V = np.stack(np.meshgrid(v, v, v, indexing="ij"), -1)
+    w = (2 * L / N) ** 3
+    c = np.abs(V[..., 0]) / dx
+    gstar = np.exp(-((V - [0.3, 0.0, 0.0]) ** 2).sum(-1) / 2.0) * (1.0 + 0.2 * np.cos(V[..., 1]))
+    gstar /= w * gstar.sum()
+    th, it = oracle.discrete_maxwellian(N, L, oracle.moments(gstar, L))
+    assert it > 0
+    r = A * oracle.eval_maxwellian(N, L, th) - (c + A) * gstar
+    beam = lambda u: np.exp(-((V - [u, 0.0, 0.0]) ** 2).sum(-1) / (2 * 0.25))
+    g0 = beam(3.0) + beam(-3.0)
+    g0 /= w * g0.sum()
+    th0, _ = oracle.discrete_maxwellian(N, L, oracle.moments(g0, L))
+    M0 = oracle.eval_maxwellian(N, L, th0)
+    e = w * (c * (M0 - g0) - r)
+    s = [e.sum(), (e * V[..., 0]).sum(), (e * V[..., 1]).sum(), (e * V[..., 2]).sum(), (e * (V ** 2).sum(-1)).sum()]
+    assert not (s[0] > 0 and s[0] * s[4] > s[1] ** 2 + s[2] ** 2 + s[3] ** 2)
+    out = {}
+    for method in (oracle.PFP, oracle.FP, oracle.PFP_RELAX):
+        prob = oracle.Problem(N=N, L=L, eps=eps, inner_method=method, inner_tol=1e-12, inner_max=5000)
+        g, its, st = oracle.cell_solve(prob, dx, r, nu, g0)
+        assert np.abs(g - gstar).max() <= 1e-9 * gstar.max(), method
+        out[method] = (its, st)
+    assert out[oracle.PFP][1]["existence_fallbacks"] >= 1
+    assert out[oracle.PFP_RELAX][1]["existence_fallbacks"] == 0
+    assert out[oracle.PFP_RELAX][0] <= out[oracle.FP][0]
