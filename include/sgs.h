@@ -55,7 +55,7 @@ enum sgs_bc_kind { SGS_DIFFUSE = 0, SGS_INFLOW = 1 };
  * precision): double-float spectral sums, each value a pair of FP32 numbers (hi + lo), on the
  * FP32 pipes, about 2^-48 relative error per term; available on SGS_FP32 handles. */
 enum sgs_precision { SGS_FP64 = 0, SGS_FP32 = 1, SGS_DF64 = 2 };
-enum sgs_inner_method { SGS_PFP = 0, SGS_FP = 1 };
+enum sgs_inner_method { SGS_PFP = 0, SGS_FP = 1, SGS_PFP_RELAX = 2 };
 
 /* Boundary data of one side: a diffuse wall at temperature T moving with tangential
  * velocity u (eq. (31)), or an inflow Maxwellian (rho, u, T) for incoming velocities. */
@@ -89,7 +89,11 @@ typedef struct {
   int inner_fixed;    /* > 0: exactly this many updates per visit (no tolerance test) */
   double newton_tol;  /* exponent-change tolerance of the Maxwellian Newton, e.g. 1e-10 */
   int newton_max;     /* e.g. 50 */
-  int inner_method;   /* SGS_PFP (eqs. (24)-(25)) or SGS_FP (eq. (22)) */
+  int inner_method;   /* SGS_PFP (eqs. (24)-(25); the fixed-point step of eq. (22) where
+                         eq. (26) fails), SGS_FP (eq. (22)), or SGS_PFP_RELAX (where eq. (26)
+                         fails, the relaxed step 1 of the remark after it: target
+                         (tau m_w + s)/(1 + tau), m_w the weighted moments of M[g], 1 + tau
+                         doubling from 2 until eq. (26) holds) */
   int conserve_proj;  /* 0: the paper's Q (mass conserved to round-off, momentum and energy to
                          spectral accuracy); 1: Q projected in FP64 onto the zero-moment
                          subspace, Q_c = Q - C^T (C C^T)^-1 C Q with C = [w phi_i(v_k)],

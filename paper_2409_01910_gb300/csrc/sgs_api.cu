@@ -368,7 +368,7 @@ int check_problem(const sgs_problem& p) {
   if (p.collision < SGS_MAXWELL || p.collision > SGS_BGK) return SGS_ERR_ARG;
   if (!(p.b0 > 0.0) || !(p.eps > 0.0)) return SGS_ERR_ARG;
   if (p.precision != SGS_FP64 && p.precision != SGS_FP32) return SGS_ERR_ARG;
-  if (p.inner_method != SGS_PFP && p.inner_method != SGS_FP) return SGS_ERR_ARG;
+  if (p.inner_method != SGS_PFP && p.inner_method != SGS_FP && p.inner_method != SGS_PFP_RELAX) return SGS_ERR_ARG;
   if (p.inner_max < 0 || p.inner_fixed < 0 || p.newton_max < 1) return SGS_ERR_ARG;
   if (p.conserve_proj < 0 || p.conserve_proj > 2) return SGS_ERR_ARG;
   for (int s = 0; s < 2; s++) {

@@ -432,6 +432,42 @@ __device__ __noinline__ int solve_mg(SweepSmem<E>& sm, int N, E w, const E* mom,
   return it;
 }
 
+// Relaxed step 1 (the remark after eq. (26)), for thread 0 when eq. (26) fails for the
+// target sd: with a factor 1 + tau on the weighted moments of the new and the current
+// Maxwellian the target becomes (tau m_w + s)/(1 + tau), m_w = sum w phi c M[g] (c the
+// step-1 weight; its moments come from the separable sums of the last evaluation, which is
+// M[g]'s). 1 + tau = 2, 4, 8, ...: the first target that passes eq. (26) replaces sd and
+// sm.svE. Returns whether one was found.
+template <typename E>
+__device__ inline bool relax_target(SweepSmem<E>& sm, E w, bool two_d, double (&sd)[5]) {
+  E m1[5];
+  float Aa[15];
+  moments_from_sums<E>(sm.S1w, sm.S[1], sm.S[2], m1, Aa);
+  double mw[5];
+#pragma unroll
+  for (int k = 0; k < 5; k++) mw[k] = tod(w * m1[k]);
+  if (two_d) {
+    E m2[5];
+    moments_from_sums<E>(sm.S[0], sm.S2w, sm.S[2], m2, Aa);
+#pragma unroll
+    for (int k = 0; k < 5; k++) mw[k] += tod(w * m2[k]);
+  }
+  for (double q = 2.0; q <= 1048576.0; q *= 2.0) {
+    double t[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) t[k] = ((q - 1.0) * mw[k] + sd[k]) / q;
+    if (t[0] > 0.0 && t[0] * t[4] > t[1] * t[1] + t[2] * t[2] + t[3] * t[3]) {
+#pragma unroll
+      for (int k = 0; k < 5; k++) {
+        sd[k] = t[k];
+        sm.svE[k] = cvt<E>(t[k]);
+      }
+      return true;
+    }
+  }
+  return false;
+}
+
 // After a step-2 update the cell equation holds up to the Maxwellians:
 //   (|v1|/dx + A) g + r = A M+   =>   R(g) = A (M+ - M[g]),   A = nu/eps,
 // where M+ is the Maxwellian step 2 used (step 1's, else M[g_old]). The norm of R then comes
@@ -487,7 +523,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   const double inv_dx = 1.0 / I.dx;
   const double L = node(N - 1, N, dv);
   const int tid = threadIdx.x;
-  const bool pfp = I.inner_method == SGS_PFP;
+  const bool pfp = I.inner_method == SGS_PFP || I.inner_method == SGS_PFP_RELAX;
+  const bool relax = I.inner_method == SGS_PFP_RELAX;
   const bool lowp = sizeof(E) == 4;  // plain FP32: tolerances at FP32 resolution
   const double ntol = lowp ? fmax(I.newton_tol, 1e-5) : I.newton_tol;
   const E inv_eps = cvt<E>(1.0 / I.eps);
@@ -633,10 +670,12 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
             stop = true;
           }
           double sd[5] = {wd * t6[1], wd * t6[2], wd * t6[3], wd * t6[4], wd * t6[5]};
+#pragma unroll
+          for (int k = 0; k < 5; k++) sm.svE[k] = w * sm.red_tote[1 + k];
           bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+          if (pfp && !exists && relax) exists = relax_target<E>(sm, w, false, sd);
           sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
         }
-        if (tid < 5) sm.svE[tid] = w * sm.red_tote[1 + tid];
         __syncthreads();
       }
       const int ctl = sm.ctl;
@@ -732,6 +771,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
             sd[k] = tod(sk);
           }
           bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+          if (pfp && !exists && relax) exists = relax_target<E>(sm, w, false, sd);
           sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
         }
         __syncthreads();
@@ -798,7 +838,8 @@ __global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int 
   const double inv_dx = 1.0 / I.dx, inv_dy = 1.0 / I.dy;
   const double L = node(N - 1, N, dv);
   const int tid = threadIdx.x;
-  const bool pfp = I.inner_method == SGS_PFP;
+  const bool pfp = I.inner_method == SGS_PFP || I.inner_method == SGS_PFP_RELAX;
+  const bool relax = I.inner_method == SGS_PFP_RELAX;
   const bool lowp = sizeof(E) == 4;
   const double ntol = lowp ? fmax(I.newton_tol, 1e-5) : I.newton_tol;
   const E inv_eps = cvt<E>(1.0 / I.eps);
@@ -948,10 +989,12 @@ __global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int 
           stop = true;
         }
         double sd[5] = {wd * t6[1], wd * t6[2], wd * t6[3], wd * t6[4], wd * t6[5]};
+#pragma unroll
+        for (int k = 0; k < 5; k++) sm.svE[k] = w * sm.red_tote[1 + k];
         bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+        if (pfp && !exists && relax) exists = relax_target<E>(sm, w, true, sd);
         sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
       }
-      if (tid < 5) sm.svE[tid] = w * sm.red_tote[1 + tid];
       __syncthreads();
     }
     const int ctl = sm.ctl;
@@ -1047,6 +1090,7 @@ __global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int 
           sd[k] = tod(sk);
         }
         bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+        if (pfp && !exists && relax) exists = relax_target<E>(sm, w, true, sd);
         sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
       }
       __syncthreads();

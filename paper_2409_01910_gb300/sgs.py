@@ -21,7 +21,7 @@ ST_NEWTON_FAIL, ST_INNER_CAP, ST_NONPOSITIVE, ST_NONFINITE, ST_TIMEOUT = 1, 2, 4
 MAXWELL, HARD_SPHERE, BGK = 0, 1, 2
 DIFFUSE, INFLOW = 0, 1
 FP64, FP32, DF64 = 0, 1, 2
-PFP, FP = 0, 1
+PFP, FP, PFP_RELAX = 0, 1, 2
 IT_P_VALID, IT_EVAL = 1, 2
 PROF_NAMES = ("moments", "dft", "sum", "reduce_idft", "sweep", "residual", "rescale", "sum_fp64", "sum_df64")
 PROF_CLASSES = len(PROF_NAMES)

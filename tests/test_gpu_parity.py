@@ -404,3 +404,56 @@ def test_sweep_plain_fixed_point_tolerance_mode(oracle):
     assert st["status"] == 0
     assert abs(st["inner_iters"] - sto["inner_iters"]) <= J
     assert rel(fd.cpu().numpy().reshape(f0.shape), fo) <= 1e-9
+
+
+def relax_cell_case(oracle, inner_method, precision):
+    """One cell between inflow sides whose cell equation has the known solution g*: P is
+    chosen so that r = A M[g*] - (|v1|/dx + A) g*; the stored value (two counter-moving
+    beams at v1 = +-3) violates eq. (26) at the first inner iteration."""
+    N, L, eps = 12, 6.0, 1.0
+    bc = dict(bc_kind=(oracle.INFLOW, oracle.INFLOW), bc_rho=(1.0, 1.0), bc_u=((0.3, 0.0, 0.0), (-0.2, 0.0, 0.0)),
+              bc_T=(1.0, 1.2), total_mass=0.0, inner_fixed=8, inner_method=inner_method)
+    po = oracle.Problem(N=N, L=L, J=1, x_lo=0.0, x_hi=0.05, eps=eps, **bc)
+    gp = sgs.Problem(nx=1, x_lo=0.0, x_hi=0.05, nv=N, v_max=L, eps=eps, precision=precision, **bc)
+    v = oracle.velocity_nodes(N, L)
+    V = np.stack(np.meshgrid(v, v, v, indexing="ij"), -1)
+    w = (2 * L / N) ** 3
+    dx = 0.05
+    beam = lambda u: np.exp(-((V - [u, 0.0, 0.0]) ** 2).sum(-1) / (2 * 0.25))
+    g0 = beam(3.0) + beam(-3.0)
+    g0 /= w * g0.sum()
+    f0 = g0[None].copy()
+    Qo, Po_unused, nuo = oracle.collide(po, f0)
+    A = nuo[0] / eps
+    c = np.abs(V[..., 0]) / dx
+    gstar = np.exp(-((V - [0.3, 0.0, 0.0]) ** 2).sum(-1) / 2.0) * (1.0 + 0.2 * np.cos(V[..., 1]))
+    gstar /= w * gstar.sum()
+    th, _ = oracle.discrete_maxwellian(N, L, oracle.moments(gstar, L))
+    r_want = A * oracle.eval_maxwellian(N, L, th) - (c + A) * gstar
+    gl, gr = oracle.ghost(po, 0, g0), oracle.ghost(po, 1, g0)
+    r_ghost = (-np.maximum(V[..., 0], 0.0) * gl + np.minimum(V[..., 0], 0.0) * gr) / dx
+    P = (eps * (r_ghost - r_want))[None]
+    return po, gp, f0, P, nuo, gstar
+
+
+@pytest.mark.parametrize("precision,tol", [(sgs.FP64, 1e-12), (sgs.FP32, 1e-11)])
+def test_relaxed_step1_parity_where_existence_fails(oracle, precision, tol):
+    """PFP with the relaxed step 1 (the remark after eq. (26)) against the oracle on a cell
+    where eq. (26) fails at the first iteration; the plain PFP form falls back to the
+    fixed-point step there instead."""
+    for method in (sgs.PFP_RELAX, sgs.PFP):
+        po, gp, f0, P, nuo, gstar = relax_cell_case(oracle, method, precision)
+        fo = f0.copy()
+        sto = oracle.sweep(po, fo, P, nuo, 1)
+        s = sgs.Solver(gp)
+        fd = to_dev(f0)
+        Q, Ps = s.field(), s.field()
+        s.collide(fd, Q, Ps)  # the scan reads the collision frequency of f0 from this step
+        s.sweep_forward(fd, to_dev(P))
+        st = s.read_status()
+        assert st["status"] == 0 and st["inner_iters"] == 8
+        assert rel(fd.cpu().numpy().reshape(f0.shape), fo) <= tol, method
+        if method == sgs.PFP_RELAX:
+            assert st["fallbacks"] == 0 and sto["existence_fallbacks"] == 0
+        else:
+            assert st["fallbacks"] >= 1 and sto["existence_fallbacks"] >= 1

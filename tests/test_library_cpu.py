@@ -47,7 +47,7 @@ def test_problem_validation_on_host(L):
     assert L.sgs_rescale(h, C.c_void_p(16), None) == sgs.ERR_WORKSPACE
     L.sgs_destroy(h)
     for bad in (dict(nv=10), dict(nv=36), dict(eps=0.0), dict(nx=0), dict(x_hi=-1.0), dict(collision=7),
-                dict(bc_T=(1.0, -1.0)), dict(precision=5), dict(newton_max=0), dict(conserve_proj=3)):
+                dict(bc_T=(1.0, -1.0)), dict(precision=5), dict(newton_max=0), dict(conserve_proj=3), dict(inner_method=3)):
         q = sgs.Problem(**bad)
         arr = (sgs._Problem * 1)(q.c())
         assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.ERR_ARG, bad
