@@ -205,6 +205,7 @@ def lib():
             "or_rescale": (None, [P, C.c_int, C.c_double, d]),
             "or_residual": (C.c_double, [P, C.c_int, C.c_double, d, d, d, d]),
             "or_sgs_iteration": (None, [P, C.c_int, C.c_double, d, d, C.c_int, S]),
+            "or_si_iteration": (None, [P, C.c_int, C.c_double, d, d, C.c_int]),
             "or_vcycle": (None, [P, d, C.c_int, C.c_int, C.c_int, C.c_int, S]),
             "or_cell_solve_c": (C.c_int, [P, d, d, C.c_double, d, S]),
             "or_ghost2d": (None, [P2, C.c_int, d, d]),
@@ -393,6 +394,13 @@ def sgs_iteration(prob: Problem, f, b=None, rescale=True, dx=None):
     lib().or_sgs_iteration(C.byref(p), f.shape[0], prob.dx if dx is None else dx, _p(f),
                            _p(None if b is None else _arr(b)), 1 if rescale else 0, C.byref(st))
     return st.as_dict()
+
+
+def si_iteration(prob: Problem, f, b=None, rescale=True, dx=None):
+    """One source iteration (eq. (SI) with the lagged BGK-penalty source), in place."""
+    p = prob.c()
+    lib().or_si_iteration(C.byref(p), f.shape[0], prob.dx if dx is None else dx, _p(f),
+                          _p(None if b is None else _arr(b)), 1 if rescale else 0)
 
 
 def vcycle(prob: Problem, f, levels, pre=1, post=1, coarse_iters=10):

@@ -998,6 +998,56 @@ void or_sgs_iteration(const or_problem* p, int J, double dx, double* f, const do
  * R_h(f) = T_h(f) - Q(f)/eps includes the nonlinear wall ghosts. The mass rescale acts
  * on the finest level only.
  * ---------------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------------------
+ * Source iteration (eq. (SI)) for the binary collision operator: with the penalty split
+ * Q = P + nu (M - f) (eq. (28)), P[f^n], nu^n and M[f^n] are frozen and f^{n+1} solves, node
+ * by node,
+ *   v1^+ (f_j - f_{j-1})/dx + v1^- (f_{j+1} - f_j)/dx = P_j/eps + (nu_j/eps)(M_j - f_j) + b_j,
+ * i.e. (|v1|/dx + nu_j/eps) f_j = (|v1|/dx) f_upwind + P_j/eps + (nu_j/eps) M_j + b_j,
+ * marched from the node's inflow side; the wall ghosts are built from f^n (lagged like the
+ * scans' ghosts). BGK mode: P = 0 and this is eq. (SI) itself.
+ * ---------------------------------------------------------------------------------- */
+void or_si_iteration(const or_problem* p, int J, double dx, double* f, const double* b, int rescale) {
+  int N = p->N;
+  long K = (long)N * N * N;
+  double* v = (double*)malloc(sizeof(double) * N);
+  double* P = (double*)malloc(sizeof(double) * J * K);
+  double* M = (double*)malloc(sizeof(double) * J * K);
+  double* nu = (double*)malloc(sizeof(double) * J);
+  double* gl = (double*)malloc(sizeof(double) * K);
+  double* gr = (double*)malloc(sizeof(double) * K);
+  or_velocity_nodes(N, p->L, v);
+  for (int j = 0; j < J; j++) {
+    double th[5];
+    or_collide_cell(p, f + (long)j * K, NULL, P + (long)j * K, nu + j, th);
+    or_eval_maxwellian(N, p->L, th, M + (long)j * K);
+  }
+  or_ghost(p, 0, f, gl);
+  or_ghost(p, 1, f + (long)(J - 1) * K, gr);
+  for (int i1 = 0; i1 < N; i1++) {
+    double c = fabs(v[i1]) / dx;
+    for (long t = 0; t < (long)N * N; t++) {
+      long i = (long)i1 * N * N + t;
+      double up = v[i1] > 0.0 ? gl[i] : gr[i];
+      for (int s = 0; s < J; s++) {
+        int j = v[i1] < 0.0 ? J - 1 - s : s;
+        long o = (long)j * K + i;
+        double a = nu[j] / p->eps;
+        double src = P[o] / p->eps + a * M[o] + (b ? b[o] : 0.0);
+        f[o] = (c * up + src) / (c + a);
+        up = f[o];
+      }
+    }
+  }
+  if (rescale && p->total_mass > 0.0) or_rescale(p, J, dx, f);
+  free(v);
+  free(P);
+  free(M);
+  free(nu);
+  free(gl);
+  free(gr);
+}
+
 static void vcycle_rec(const or_problem* p, int level, int levels, int J, double dx, double* f, const double* b,
                        int pre, int post, int coarse_iters, or_stats* st) {
   long K = (long)p->N * p->N * p->N;

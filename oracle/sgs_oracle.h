@@ -98,6 +98,11 @@ double or_residual(const or_problem* p, int J, double dx, const double* f, const
 /* One SGS iteration: collide, forward, collide, backward, rescale (if enabled and rescale != 0). */
 void or_sgs_iteration(const or_problem* p, int J, double dx, double* f, const double* b, int rescale,
                       or_stats* st);
+/* Source iteration (eq. (SI)), first order, the collision term split by the BGK penalty
+ * (eq. (28)) with P, nu and M of the current iterate; one linear transport solve per
+ * velocity node; diffuse-wall densities from the current iterate; then the mass rescale
+ * when rescale != 0 and total_mass > 0. f in place. */
+void or_si_iteration(const or_problem* p, int J, double dx, double* f, const double* b, int rescale);
 /* One FAS V-cycle on the finest level (J cells). */
 void or_vcycle(const or_problem* p, double* f, int levels, int pre, int post, int coarse_iters, or_stats* st);
 
