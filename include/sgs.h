@@ -154,6 +154,16 @@ int sgs_sweep_ordering(sgs_handle* h, double* f, const double* P, const double* 
 /* Uniform rescale of each instance to its total mass (eq. (32)); no-op where <= 0. */
 int sgs_rescale(sgs_handle* h, double* f, void* stream);
 
+/* One source iteration (eq. (SI)), 1-D problems: the collision step of f (P = Q - nu (M - f),
+ * eq. (28), written to P), then for every velocity node the upwind transport with
+ * absorption (|v1|/dx + nu_j/eps) f_j = (|v1|/dx) f_upwind + P_j/eps + (nu_j/eps) M[f_j] + b_j,
+ * marched from the node's inflow side with the diffuse-wall ghosts of the previous iterate,
+ * then the mass rescale of eq. (32). The classical method the paper compares SGS with; it
+ * slows down as eps -> 0 (Section 3.1). f (device) in place; P (device) receives the
+ * penalty of the previous iterate; rhs (device, nullable) is b. SGS_ERR_UNSUPPORTED for
+ * 2-D handles. */
+int sgs_si_iteration(sgs_handle* h, double* f, double* P, const double* rhs, void* stream);
+
 /* Outer residual R = T(f) - Q/eps - rhs (Section 4 stopping rule), res[q] (device,
  * n_inst doubles) = sqrt(dx sum_j sum_k w R^2) per instance. Q from sgs_collide(f). */
 int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, void* stream);

@@ -164,6 +164,53 @@ cudaError_t launch_residual_impl(const AuxArgs& a, const double* f, const double
   return cudaGetLastError();
 }
 
+// Source iteration (eq. (SI)) with the lagged BGK-penalty source (eq. (28)): for every
+// velocity node of every instance,
+//   (|v1|/dx + nu_j/eps) f_j = (|v1|/dx) f_upwind + P_j/eps + (nu_j/eps) M_j + b_j,
+// marched from the node's inflow side, with P, nu and the Maxwellian factors (efac) of the
+// previous iterate and its wall fluxes (flux) for the diffuse-wall ghosts. One thread per
+// (node, instance): nodes are independent, cells are visited in order.
+__global__ void __launch_bounds__(256) k_si_transport(AuxArgs a, double* f, const double* __restrict__ P,
+                                                      const double* __restrict__ rhs,
+                                                      const double* __restrict__ efac,
+                                                      const double* __restrict__ nu,
+                                                      const double* __restrict__ flux) {
+  const int q = blockIdx.y;
+  if (a.active && !a.active[q]) return;
+  const InstDev& I = a.inst[q];
+  const int N = a.N, K = N * N * N;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K) return;
+  const int i1 = e / (N * N), i2 = (e / N) % N, i3 = e % N;
+  const double v1 = node(i1, N, a.dv);
+  const double c = fabs(v1) / I.dx, inv_eps = 1.0 / I.eps;
+  const int side = v1 > 0.0 ? 0 : 1;  // the node's inflow side (v1 = 0 needs none: c = 0)
+  const double rho_w = I.bc_kind[side] == SGS_INFLOW ? I.bc_rho[side] : -flux[2 * q + side] / I.wall_denom[side];
+  double up = rho_w * I.wall[side][0][i1] * I.wall[side][1][i2] * I.wall[side][2][i3];
+  for (int s = 0; s < I.J; s++) {
+    const int j = v1 < 0.0 ? I.J - 1 - s : s;
+    const int cell = I.cell0 + j;
+    const long long o = I.f_off + (long long)j * K + e;
+    const double* ef = efac + (long long)cell * 3 * kMaxN;
+    const double M = ef[i1] * ef[kMaxN + i2] * ef[2 * kMaxN + i3];
+    const double A = nu[cell] * inv_eps;
+    double src = P[o] * inv_eps + A * M;
+    if (rhs) src += rhs[o];
+    const double x = (c * up + src) / (c + A);
+    f[o] = x;
+    up = x;
+  }
+}
+
+cudaError_t launch_si_transport(const AuxArgs& a, double* f, const double* P, const double* rhs, const double* efac,
+                                const double* nu, cudaStream_t st) {
+  double* flux = a.scratch;  // [2 n_inst], the walls' outgoing fluxes of the previous iterate
+  k_wall_flux<<<2 * a.n_inst, 256, 0, st>>>(a.inst, f, a.N, a.dv, flux);
+  const int K = a.N * a.N * a.N;
+  k_si_transport<<<dim3((K + 255) / 256, a.n_inst), 256, 0, st>>>(a, f, P, rhs, efac, nu, flux);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_residual(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
                             cudaStream_t st) {
   return launch_residual_impl(a, f, Q, rhs, res, nullptr, st);

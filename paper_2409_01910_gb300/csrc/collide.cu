@@ -1039,6 +1039,11 @@ cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const Coll
   return cudaGetLastError();
 }
 
+cudaError_t launch_factors(const double* theta, int C, int N, double dv, double* efac, cudaStream_t st) {
+  k_factors<<<C, 3 * N, 0, st>>>(theta, N, dv, efac);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_moments(const double* f, const CellTables& ct, int C, int N, double dv, double tol, int maxit,
                            double* theta, double* nu, Counters* cnt, cudaStream_t st) {
   k_moments<<<C, 256, 0, st>>>(f, ct, N, dv, tol, maxit, theta, nu, cnt);

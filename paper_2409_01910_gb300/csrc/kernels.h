@@ -155,6 +155,11 @@ cudaError_t func_attr(const void* fn, cudaFuncAttribute attr, int value);
 cudaError_t launch_update_active(const double* res, int n, double tol, int* active, cudaStream_t st);
 cudaError_t launch_fill_int(int* p, int n, int value, cudaStream_t st);
 
+// Separable factors of every cell's discrete Maxwellian from theta (efac [C][3][kMaxN]).
+cudaError_t launch_factors(const double* theta, int C, int N, double dv, double* efac, cudaStream_t st);
+// Source iteration: wall fluxes of f, then the per-node transport march (1-D problems).
+cudaError_t launch_si_transport(const AuxArgs& a, double* f, const double* P, const double* rhs, const double* efac,
+                                const double* nu, cudaStream_t st);
 cudaError_t launch_moments(const double* f, const CellTables& ct, int C, int N, double dv, double tol, int maxit,
                            double* theta, double* nu, Counters* cnt, cudaStream_t st);
 cudaError_t launch_collide_bgk(const double* f, const CellTables& ct, int C, int N, double dv, const double* theta,

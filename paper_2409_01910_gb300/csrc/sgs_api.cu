@@ -1074,6 +1074,23 @@ int sgs_rescale(sgs_handle* h, double* f, void* stream) {
   return rescale_impl(h, f, as_stream(stream));
 }
 
+int sgs_si_iteration(sgs_handle* h, double* f, double* P, const double* rhs, void* stream) {
+  if (!h || !f || !P) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  if (h->two_d) return SGS_ERR_UNSUPPORTED;
+  cudaStream_t st = as_stream(stream);
+  int r = collide_impl(h, f, nullptr, P, h->precision, st);  // P, nu, theta of the current iterate
+  if (r) return r;
+  {
+    Scope sc(h, SGS_PROF_SWEEP, st, 3);
+    double* efac = h->at<double>(h->off.efac);
+    cudaError_t e = launch_factors(h->at<double>(h->off.theta), h->C, h->N, h->dv, efac, st);
+    if (e == cudaSuccess) e = launch_si_transport(aux_args(h), f, P, rhs, efac, h->at<double>(h->off.nu), st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return rescale_impl(h, f, st);
+}
+
 int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, void* stream) {
   if (!h || !f || !Q || !res) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;

@@ -160,6 +160,7 @@ def lib(build: bool = True):
             "sgs_collide": (C.c_int, [vp, vp, vp, vp, vp]),
             "sgs_collide_prec": (C.c_int, [vp, vp, vp, vp, C.c_int, vp]),
             "sgs_sweep_forward": (C.c_int, [vp, vp, vp, vp, vp]),
+            "sgs_si_iteration": (C.c_int, [vp, vp, vp, vp, vp]),
             "sgs_sweep_backward": (C.c_int, [vp, vp, vp, vp, vp]),
             "sgs_sweep_ordering": (C.c_int, [vp, vp, vp, vp, C.c_int, vp]),
             "sgs_rescale": (C.c_int, [vp, vp, vp]),
@@ -274,6 +275,10 @@ class Solver:
     def sweep_ordering(self, f, P, ordering, rhs=None, stream=None):
         _check(lib().sgs_sweep_ordering(self.h, _ptr(f), _ptr(P), _ptr(rhs), ordering, _stream(stream)),
                "sgs_sweep_ordering")
+
+    def si_iteration(self, f, P, rhs=None, stream=None):
+        """One source iteration (eq. (SI)); P receives the penalty of the previous iterate."""
+        _check(lib().sgs_si_iteration(self.h, _ptr(f), _ptr(P), _ptr(rhs), _stream(stream)), "sgs_si_iteration")
 
     def rescale(self, f, stream=None):
         _check(lib().sgs_rescale(self.h, _ptr(f), _stream(stream)), "sgs_rescale")
