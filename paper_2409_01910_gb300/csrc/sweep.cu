@@ -11,9 +11,13 @@
 //   - a velocity sum: per-thread partials -> warp butterfly -> block -> one thread per
 //     (value, CTA rank) reads the partial through distributed shared memory and a shuffle
 //     tree forms the total, identical in every CTA of the cluster (identical branches);
-//   - a Newton iteration: the Maxwellian is separable, so warps 0, 1, 2 evaluate the
-//     factors and 1-D sums of the three velocity dimensions concurrently, and warp 0
-//     combines them, factorises the Jacobian (FP32: inexact Newton) and updates theta.
+//   - a Newton iteration: the Maxwellian is separable, so warps 0, 1, 2 (and one warp per
+//     step-1 weight) evaluate the factors and 1-D sums of their velocity dimension
+//     concurrently; after one barrier among those warps, each of them combines the sums,
+//     factorises the Jacobian (FP32: inexact Newton) and takes the same decisions itself;
+//   - after the first inner update, the residual and the step-1 target come from the
+//     step-2 identity (|v1|/dx + A) g + r = A M+ and separable sums, without a pass over the
+//     nodes or a cluster reduction.
 //
 // E is the arithmetic of the elementwise work, the sums and the Newton residuals: double for
 // the FP64 solver, double-float (two FP32 numbers, FP64-class accuracy, no FP64 instruction
