@@ -63,6 +63,7 @@ class _Problem(C.Structure):
         ("newton_max", C.c_int),
         ("inner_method", C.c_int),
         ("conserve_proj", C.c_int),
+        ("order", C.c_int),
     ]
 
 
@@ -104,6 +105,7 @@ class Problem:
     newton_max: int = 50
     inner_method: int = PFP
     conserve_proj: int = 0
+    order: int = 1
 
     @property
     def dx(self) -> float:
@@ -112,7 +114,7 @@ class Problem:
     def c(self) -> _Problem:
         p = _Problem()
         for name in ("N", "L", "kernel", "b0", "J", "x_lo", "x_hi", "eps", "total_mass", "inner_tol",
-                     "inner_max", "inner_fixed", "newton_tol", "newton_max", "inner_method", "conserve_proj"):
+                     "inner_max", "inner_fixed", "newton_tol", "newton_max", "inner_method", "conserve_proj", "order"):
             setattr(p, name, getattr(self, name))
         for s in range(2):
             p.bc_kind[s] = self.bc_kind[s]

@@ -886,27 +886,62 @@ void or_ghost(const or_problem* p, int side, const double* f_adj, double* ghost)
  * the scan), and P_j, nu_j come from the collision evaluation that preceded the scan.
  * Wall ghosts use the adjacent cell's value stored before the visit.
  * ---------------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------------------
+ * Slopes of the linear reconstruction (eq. (reconstruction), eq. (slope)):
+ *   s_0 = f_1 - f_0,  s_j = (f_{j+1} - f_{j-1})/2 inside,  s_{J-1} = f_{J-1} - f_{J-2};
+ * face values f^-_{j+1/2} = f_j + s_j/2 and f^+_{j-1/2} = f_j - s_j/2. First order: s = 0.
+ * ---------------------------------------------------------------------------------- */
+void or_slopes(const or_problem* p, int J, const double* f, double* s) {
+  long K = (long)p->N * p->N * p->N;
+  if (p->order != 2 || J < 2) {
+    memset(s, 0, sizeof(double) * J * K);
+    return;
+  }
+  for (int j = 0; j < J; j++)
+    for (long i = 0; i < K; i++) {
+      double d;
+      if (j == 0)
+        d = f[K + i] - f[i];
+      else if (j == J - 1)
+        d = f[(long)j * K + i] - f[(long)(j - 1) * K + i];
+      else
+        d = 0.5 * (f[(long)(j + 1) * K + i] - f[(long)(j - 1) * K + i]);
+      s[(long)j * K + i] = d;
+    }
+}
+
 void or_sweep(const or_problem* p, int J, double dx, int dir, double* f, const double* P, const double* nu,
               const double* b, or_stats* st) {
+  /* Second order: the slopes are explicit, taken from the state before this scan (eq.
+   * (SGS_BGK): s^(n) in the forward and s^(n+1/2) in the backward scan), and enter r as
+   *   -(v1^+ s_{j-1} - v1 s_j + v1^- s_{j+1}) / (2 dx),   with zero ghost slopes.
+   * The wall ghosts take their density from the outgoing face value (f_0 - s_0/2 on the
+   * left, f_{J-1} + s_{J-1}/2 on the right) of the stored state, like the first-order
+   * ghosts from the stored cell value. */
   int N = p->N;
   long K = (long)N * N * N;
   double* v = (double*)malloc(sizeof(double) * N);
   double* r = (double*)malloc(sizeof(double) * K);
   double* gl = (double*)malloc(sizeof(double) * K);
   double* gr = (double*)malloc(sizeof(double) * K);
+  double* face = (double*)malloc(sizeof(double) * K);
+  double* sl = (double*)malloc(sizeof(double) * J * K);
   or_velocity_nodes(N, p->L, v);
+  or_slopes(p, J, f, sl);
   for (int s = 0; s < J; s++) {
     int j = dir > 0 ? s : J - 1 - s;
     const double* left;
     const double* right;
     if (j == 0) {
-      or_ghost(p, 0, f, gl);
+      for (long i = 0; i < K; i++) face[i] = f[i] - 0.5 * sl[i];
+      or_ghost(p, 0, face, gl);
       left = gl;
     } else {
       left = f + (long)(j - 1) * K;
     }
     if (j == J - 1) {
-      or_ghost(p, 1, f + (long)(J - 1) * K, gr);
+      for (long i = 0; i < K; i++) face[i] = f[(long)(J - 1) * K + i] + 0.5 * sl[(long)(J - 1) * K + i];
+      or_ghost(p, 1, face, gr);
       right = gr;
     } else {
       right = f + (long)(j + 1) * K;
@@ -916,6 +951,11 @@ void or_sweep(const or_problem* p, int J, double dx, int dir, double* f, const d
       for (long t = 0; t < (long)N * N; t++) {
         long i = (long)i1 * N * N + t;
         r[i] = (-vp * left[i] + vm * right[i]) / dx - P[(long)j * K + i] / p->eps - (b ? b[(long)j * K + i] : 0.0);
+        if (p->order == 2) {
+          double sm = j > 0 ? sl[(long)(j - 1) * K + i] : 0.0;
+          double sp = j < J - 1 ? sl[(long)(j + 1) * K + i] : 0.0;
+          r[i] -= (vp * sm - v[i1] * sl[(long)j * K + i] + vm * sp) / (2.0 * dx);
+        }
       }
     }
     or_cell_solve(p, dx, r, nu[j], f + (long)j * K, st);
@@ -924,6 +964,8 @@ void or_sweep(const or_problem* p, int J, double dx, int dir, double* f, const d
   free(r);
   free(gl);
   free(gr);
+  free(face);
+  free(sl);
 }
 
 /* Uniform scaling after each iteration to keep the total mass C (eq. (32)). */
@@ -945,25 +987,36 @@ void or_rescale(const or_problem* p, int J, double dx, double* f) {
  * same f, norm sqrt(dx sum_j sum_k w R^2). */
 double or_residual(const or_problem* p, int J, double dx, const double* f, const double* Q, const double* b,
                    double* Rout) {
+  /* R_j = (v1^+ (f^-_{j+1/2} - f^-_{j-1/2}) + v1^- (f^+_{j+1/2} - f^+_{j-1/2}))/dx - Q_j/eps - b_j
+   * (eq. (upwind)) with the face values of the reconstruction (first order: the cell
+   * values) and wall ghosts from the same f. */
   int N = p->N;
   long K = (long)N * N * N;
   double w = weight(N, p->L);
   double* v = (double*)malloc(sizeof(double) * N);
   double* gl = (double*)malloc(sizeof(double) * K);
   double* gr = (double*)malloc(sizeof(double) * K);
+  double* face = (double*)malloc(sizeof(double) * K);
+  double* sl = (double*)malloc(sizeof(double) * J * K);
   or_velocity_nodes(N, p->L, v);
-  or_ghost(p, 0, f, gl);
-  or_ghost(p, 1, f + (long)(J - 1) * K, gr);
+  or_slopes(p, J, f, sl);
+  for (long i = 0; i < K; i++) face[i] = f[i] - 0.5 * sl[i];
+  or_ghost(p, 0, face, gl);
+  for (long i = 0; i < K; i++) face[i] = f[(long)(J - 1) * K + i] + 0.5 * sl[(long)(J - 1) * K + i];
+  or_ghost(p, 1, face, gr);
   double acc = 0.0;
   for (int j = 0; j < J; j++) {
-    const double* fl = j == 0 ? gl : f + (long)(j - 1) * K;
-    const double* fr = j == J - 1 ? gr : f + (long)(j + 1) * K;
     const double* fj = f + (long)j * K;
+    const double* sj = sl + (long)j * K;
     for (int i1 = 0; i1 < N; i1++) {
       double vp = v[i1] > 0.0 ? v[i1] : 0.0, vm = v[i1] < 0.0 ? v[i1] : 0.0;
       for (long t = 0; t < (long)N * N; t++) {
         long i = (long)i1 * N * N + t;
-        double R = (vp * (fj[i] - fl[i]) + vm * (fr[i] - fj[i])) / dx - Q[(long)j * K + i] / p->eps -
+        double mr = fj[i] + 0.5 * sj[i];  /* f^-_{j+1/2} */
+        double pl = fj[i] - 0.5 * sj[i];  /* f^+_{j-1/2} */
+        double ml = j == 0 ? gl[i] : f[(long)(j - 1) * K + i] + 0.5 * sl[(long)(j - 1) * K + i];
+        double pr = j == J - 1 ? gr[i] : f[(long)(j + 1) * K + i] - 0.5 * sl[(long)(j + 1) * K + i];
+        double R = (vp * (mr - ml) + vm * (pr - pl)) / dx - Q[(long)j * K + i] / p->eps -
                    (b ? b[(long)j * K + i] : 0.0);
         if (Rout) Rout[(long)j * K + i] = R;
         acc += w * R * R;
@@ -973,6 +1026,8 @@ double or_residual(const or_problem* p, int J, double dx, const double* f, const
   free(v);
   free(gl);
   free(gr);
+  free(face);
+  free(sl);
   return sqrt(dx * acc);
 }
 

@@ -42,6 +42,7 @@ typedef struct {
   int inner_method;    /* OR_PFP, OR_FP, or OR_PFP_RELAX (relaxed step 1 when eq. (26) fails) */
   int conserve_proj;   /* 1: project Q onto the zero-moment subspace (not in the paper);
                           2: the same with the correction weighted by the local Maxwellian */
+  int order;           /* spatial order of the 1-D scheme: 1 (s = 0) or 2 (eq. (slope)); 0 means 1 */
 } or_problem;
 
 typedef struct {
@@ -62,6 +63,10 @@ void or_idft(int N, const double* qhat, double* q);
 void or_qhat_direct(int N, double L, int kernel, double b0, const double* ahat, const double* bhat, double* qhat);
 /* Q^FSM[f, f] on the velocity nodes. */
 void or_qfsm(int N, double L, int kernel, double b0, const double* f, double* q);
+/* Slopes of eq. (slope) for the second-order scheme (central inside, one-sided in the first
+ * and the last cell, no limiter); all zero for the first-order scheme or a single cell.
+ * f, s: J cells of N^3 values. */
+void or_slopes(const or_problem* p, int J, const double* f, double* s);
 /* Orthogonal projection of q (in place) onto {q : sum_k phi_i(v_k) q_k = 0, i = 0..4},
  * phi = (1, v1, v2, v3, |v|^2). Returns 0, or -1 if the 5x5 Gram matrix is singular. */
 int or_conserve_project(int N, double L, double* q);
