@@ -103,6 +103,12 @@ typedef struct {
                          far velocity tails). Applied in FP64 in every collision step (all
                          levels and precisions) before P = Q_c - nu (M - f) is formed. Not in
                          the paper; equal in every instance of a handle; ignored for BGK. */
+  int order;          /* spatial order, 1-D only: 1 (or 0): first order (s = 0); 2: linear
+                         reconstruction with the slopes of eq. (slope) (central inside,
+                         one-sided in the end cells, no limiter), explicit in the scans (taken
+                         from the state before each scan, eq. (SGS_BGK)), zero ghost slopes,
+                         diffuse-wall densities from the outgoing face value. Equal in every
+                         instance of a handle; SGS_ERR_UNSUPPORTED with space_dim 2. */
 } sgs_problem;
 
 /* Counters accumulated on the device since setup or the last sgs_reset_stats(). */
@@ -182,7 +188,8 @@ int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* 
  * stream capture. All calls share the array: calls that overlap on the GPU race, so order
  * them on one stream. Every slot a call reads is written earlier in the same call. */
 int sgs_residual_noalloc(const sgs_problem* p, const double* f, const double* Q, const double* rhs, double* res,
-                         void* stream);  /* 1-D problems only (SGS_ERR_ARG otherwise) */
+                         void* stream);  /* 1-D problems only (SGS_ERR_ARG otherwise); first order
+                                            only (SGS_ERR_UNSUPPORTED for order 2) */
 
 /* Collision step in a chosen arithmetic (SGS_FP32 and SGS_DF64 need a handle set up with
  * precision SGS_FP32, whose workspace then carries the FP64 and FP32 weight tables and the

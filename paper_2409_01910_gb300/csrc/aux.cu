@@ -147,6 +147,109 @@ __global__ void __launch_bounds__(256) k_residual_cells2d(AuxArgs a, const doubl
   if (threadIdx.x == 0) part[c] = w * t;
 }
 
+// ---------------------------------------------------------------------------------------
+// Second-order scheme, 1-D (eq. (reconstruction), eq. (slope)): slopes central inside and
+// one-sided in the first and last cell, faces f^-_{j+1/2} = f_j + s_j/2, f^+_{j-1/2} =
+// f_j - s_j/2, zero ghost slopes; diffuse-wall densities from the outgoing face value.
+// ---------------------------------------------------------------------------------------
+__device__ inline double slope1d(const InstDev& I, const double* f, long long base, int j, int e, int K) {
+  if (I.J < 2) return 0.0;
+  if (j == 0) return f[base + K + e] - f[base + e];
+  if (j == I.J - 1) return f[base + e] - f[base - K + e];
+  return 0.5 * (f[base + K + e] - f[base - K + e]);
+}
+
+// sflux[2 q + side] = w sum over the outgoing velocities of v1 s at the wall cell.
+__global__ void __launch_bounds__(256) k_wall_slope_flux(AuxArgs a, const double* __restrict__ f, double* sflux) {
+  __shared__ double sh[32];
+  int q = blockIdx.x >> 1, side = blockIdx.x & 1;
+  const InstDev& I = a.inst[q];
+  int N = a.N, K = N * N * N;
+  int j = side ? I.J - 1 : 0;
+  long long base = I.f_off + (long long)j * K;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    double v1 = node(e / (N * N), N, a.dv);
+    if ((side == 0 && v1 < 0.0) || (side == 1 && v1 > 0.0)) acc += v1 * slope1d(I, f, base, j, e, K);
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) sflux[blockIdx.x] = a.dv * a.dv * a.dv * t;
+}
+
+// Right-hand side of a second-order scan from the state f before it:
+//   out = rhs + (v1^+ s_{j-1} - v1 s_j + v1^- s_{j+1}) / (2 dx)    (eq. (SGS_BGK), r = ... - out)
+// plus, in the wall cells, the change of the lagged ghost from the cell value the scan uses
+// to the face value (rho = -flux_out / wall_denom, flux_out of f_0 - s_0/2 resp. f_{J-1} +
+// s_{J-1}/2): + v1^+ drho_l Mhat_l / dx in cell 0, - v1^- drho_r Mhat_r / dx in cell J-1.
+__global__ void __launch_bounds__(256) k_slope_rhs(AuxArgs a, const double* __restrict__ f,
+                                                   const double* __restrict__ rhs, const double* __restrict__ sflux,
+                                                   double* __restrict__ out) {
+  int c = blockIdx.x;
+  int q = a.cell_inst[c];
+  const InstDev& I = a.inst[q];
+  int N = a.N, K = N * N * N;
+  long long base = a.cell_off[c];
+  int j = (int)((base - I.f_off) / K);
+  double inv_dx = 1.0 / I.dx;
+  double drho_l = (j == 0 && I.bc_kind[0] != SGS_INFLOW) ? 0.5 * sflux[2 * q] / I.wall_denom[0] : 0.0;
+  double drho_r = (j == I.J - 1 && I.bc_kind[1] != SGS_INFLOW) ? -0.5 * sflux[2 * q + 1] / I.wall_denom[1] : 0.0;
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < K; e += gridDim.y * blockDim.x) {
+    int i1 = e / (N * N), i2 = (e / N) % N, i3 = e % N;
+    double v1 = node(i1, N, a.dv);
+    double sj = slope1d(I, f, base, j, e, K);
+    double sm = j > 0 ? slope1d(I, f, base - K, j - 1, e, K) : 0.0;
+    double sp = j < I.J - 1 ? slope1d(I, f, base + K, j + 1, e, K) : 0.0;
+    double b = (rhs ? rhs[base + e] : 0.0) + (fmax(v1, 0.0) * sm - v1 * sj + fmin(v1, 0.0) * sp) * (0.5 * inv_dx);
+    if (drho_l != 0.0) b += fmax(v1, 0.0) * drho_l * I.wall[0][0][i1] * I.wall[0][1][i2] * I.wall[0][2][i3] * inv_dx;
+    if (drho_r != 0.0) b -= fmin(v1, 0.0) * drho_r * I.wall[1][0][i1] * I.wall[1][1][i2] * I.wall[1][2][i3] * inv_dx;
+    out[base + e] = b;
+  }
+}
+
+cudaError_t launch_slope_rhs(const AuxArgs& a, const double* f, const double* rhs, double* out, cudaStream_t st) {
+  k_wall_slope_flux<<<2 * a.n_inst, 256, 0, st>>>(a, f, a.sflux);
+  k_slope_rhs<<<dim3(a.C, 4), 256, 0, st>>>(a, f, rhs, a.sflux, out);
+  return cudaGetLastError();
+}
+
+// Second-order residual per cell: R = (v1^+ (f^-_{j+1/2} - f^-_{j-1/2}) + v1^- (f^+_{j+1/2} -
+// f^+_{j-1/2}))/dx - Q_j/eps - b_j (eq. (upwind)), ghosts from the face values of the same f.
+__global__ void __launch_bounds__(256) k_residual_cells_o2(AuxArgs a, const double* __restrict__ f,
+                                                            const double* __restrict__ Q,
+                                                            const double* __restrict__ rhs, const double* flux,
+                                                            const double* sflux, double* part, double* Rout) {
+  __shared__ double sh[32];
+  int c = blockIdx.x;
+  int q = a.cell_inst[c];
+  const InstDev& I = a.inst[q];
+  int N = a.N, K = N * N * N;
+  long long base = a.cell_off[c];
+  int j = (int)((base - I.f_off) / K);
+  double w = a.dv * a.dv * a.dv;
+  double inv_dx = 1.0 / I.dx, inv_eps = 1.0 / I.eps;
+  double rho_l = I.bc_kind[0] == SGS_INFLOW ? I.bc_rho[0] : -(flux[2 * q] - 0.5 * sflux[2 * q]) / I.wall_denom[0];
+  double rho_r =
+      I.bc_kind[1] == SGS_INFLOW ? I.bc_rho[1] : -(flux[2 * q + 1] + 0.5 * sflux[2 * q + 1]) / I.wall_denom[1];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    int i1 = e / (N * N), i2 = (e / N) % N, i3 = e % N;
+    double v1 = node(i1, N, a.dv);
+    double fj = f[base + e];
+    double sj = slope1d(I, f, base, j, e, K);
+    double mr = fj + 0.5 * sj, pl = fj - 0.5 * sj;
+    double ml = j == 0 ? rho_l * I.wall[0][0][i1] * I.wall[0][1][i2] * I.wall[0][2][i3]
+                       : f[base - K + e] + 0.5 * slope1d(I, f, base - K, j - 1, e, K);
+    double pr = j == I.J - 1 ? rho_r * I.wall[1][0][i1] * I.wall[1][1][i2] * I.wall[1][2][i3]
+                             : f[base + K + e] - 0.5 * slope1d(I, f, base + K, j + 1, e, K);
+    double R = (fmax(v1, 0.0) * (mr - ml) + fmin(v1, 0.0) * (pr - pl)) * inv_dx - Q[base + e] * inv_eps;
+    if (rhs) R -= rhs[base + e];
+    if (Rout) Rout[base + e] = R;
+    acc += R * R;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[c] = w * t;
+}
+
 cudaError_t launch_residual_impl(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
                                  double* R, cudaStream_t st) {
   double* flux = a.scratch;                  // [2 n_inst]
@@ -159,7 +262,12 @@ cudaError_t launch_residual_impl(const AuxArgs& a, const double* f, const double
     return cudaGetLastError();
   }
   k_wall_flux<<<2 * a.n_inst, 256, 0, st>>>(a.inst, f, a.N, a.dv, flux);
-  k_residual_cells<<<a.C, 256, 0, st>>>(a, f, Q, rhs, flux, part, R);
+  if (a.sflux) {  // second-order scheme
+    k_wall_slope_flux<<<2 * a.n_inst, 256, 0, st>>>(a, f, a.sflux);
+    k_residual_cells_o2<<<a.C, 256, 0, st>>>(a, f, Q, rhs, flux, a.sflux, part, R);
+  } else {
+    k_residual_cells<<<a.C, 256, 0, st>>>(a, f, Q, rhs, flux, part, R);
+  }
   if (res) k_residual_final<<<(a.n_inst + 127) / 128, 128, 0, st>>>(a.inst, a.n_inst, part, res);
   return cudaGetLastError();
 }

@@ -147,6 +147,7 @@ struct AuxArgs {
   const int* active;      // per instance: 0 = converged, its rescale is skipped
   int two_d;              // 2-D space (one instance): grid nx x ny
   int nx, ny;
+  double* sflux;          // second-order scheme: [2 n_inst] slope fluxes of the walls; null at first order
 };
 
 // cudaFuncSetAttribute through a per-device cache: the call is made once per (kernel,
@@ -157,6 +158,9 @@ cudaError_t launch_fill_int(int* p, int n, int value, cudaStream_t st);
 
 // Separable factors of every cell's discrete Maxwellian from theta (efac [C][3][kMaxN]).
 cudaError_t launch_factors(const double* theta, int C, int N, double dv, double* efac, cudaStream_t st);
+// Second-order scheme (1-D): out = rhs + the explicit slope terms of the scan and the
+// face-value correction of the lagged wall densities, all from the state f before the scan.
+cudaError_t launch_slope_rhs(const AuxArgs& a, const double* f, const double* rhs, double* out, cudaStream_t st);
 // Source iteration: wall fluxes of f, then the per-node transport march (1-D problems).
 cudaError_t launch_si_transport(const AuxArgs& a, double* f, const double* P, const double* rhs, const double* efac,
                                 const double* nu, cudaStream_t st);

@@ -154,6 +154,7 @@ extern "C" int sgs_residual_noalloc(const sgs_problem* p, const double* f, const
                                     double* res, void* stream) {
   using namespace sgs;
   if (!p || !f || !Q || !res) return SGS_ERR_ARG;
+  if (p->order == 2) return SGS_ERR_UNSUPPORTED;  // the first-order residual only
   if (p->nx > kNoAllocMaxCells) {
     fprintf(stderr, "sgs_residual_noalloc: %d cells exceed the static scratch capacity of %d cells\n", p->nx,
             kNoAllocMaxCells);

@@ -99,9 +99,10 @@ struct sgs_handle {
   struct {
     size_t inst, cell_off, cell_inst, cnt, theta, nu, scratch, tw_cos, tw_sin, G, Lo, units, step0, row_k, row_start,
         row_units, W64, W32, st1a, st1b, st2a, st2b, ahat, bhat, qhat, partial, partial2, f_ref, Q_ref, theta_ref,
-        ahat_ref, active, W32lo, tw_cos32, tw_sin32, efac, efac_ref, cproj_A, mom, end;
+        ahat_ref, active, W32lo, tw_cos32, tw_sin32, efac, efac_ref, cproj_A, mom, sflux, o2rhs, end;
   } off;
   int cproj = 0;  // conservation projection of Q after every spectral collision step (mode 1 or 2)
+  bool order2 = false;  // second-order reconstruction (1-D)
   bool dc_ref = false;  // FP32 collisions use the increment form against the stored reference
   int dc_prec = SGS_DF64;  // arithmetic of the high-precision evaluation in sgs_dc_step
   bool two_d = false;      // 2-D space: one instance, wavefront scans, four orderings
@@ -288,6 +289,8 @@ void layout(sgs_handle* h) {
   f.efac_ref = take(sizeof(double) * 3 * kMaxN * C);  // is the largest) and those of the reference
   f.cproj_A = take(h->cproj == 1 ? sizeof(double) * 25 : 0);  // inverse Gram matrix of (1, v, |v|^2)
   f.mom = take(h->cproj ? sizeof(double) * 5 * (size_t)C * N : 0);  // moments of Q per (cell, i1) slab
+  f.sflux = take(h->order2 ? sizeof(double) * 2 * h->n_inst : 0);     // second order: wall slope fluxes
+  f.o2rhs = take(h->order2 ? sizeof(double) * h->field : 0);         // second order: scan right-hand side
   bool sp = h->spectral;
   size_t U = h->units.size();
   f.G = take(sp ? sizeof(double) * h->na * h->nb : 0);
@@ -371,6 +374,8 @@ int check_problem(const sgs_problem& p) {
   if (p.inner_method != SGS_PFP && p.inner_method != SGS_FP && p.inner_method != SGS_PFP_RELAX) return SGS_ERR_ARG;
   if (p.inner_max < 0 || p.inner_fixed < 0 || p.newton_max < 1) return SGS_ERR_ARG;
   if (p.conserve_proj < 0 || p.conserve_proj > 2) return SGS_ERR_ARG;
+  if (p.order < 0 || p.order > 2) return SGS_ERR_ARG;
+  if (p.order == 2 && p.space_dim == 2) return SGS_ERR_UNSUPPORTED;
   for (int s = 0; s < 2; s++) {
     if (p.bc[s].kind != SGS_DIFFUSE && p.bc[s].kind != SGS_INFLOW) return SGS_ERR_ARG;
     if (!(p.bc[s].T > 0.0)) return SGS_ERR_ARG;
@@ -486,6 +491,7 @@ AuxArgs aux_args(const sgs_handle* h, int l = 0) {
   a.two_d = h->two_d ? 1 : 0;
   a.nx = L.hinst0.nx;
   a.ny = L.hinst0.ny;
+  a.sflux = h->order2 ? h->at<double>(h->off.sflux) : nullptr;
   return a;
 }
 
@@ -687,7 +693,15 @@ int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int
     }
     return SGS_OK;
   }
-  Scope sc(h, SGS_PROF_SWEEP, st, 1);
+  Scope sc(h, SGS_PROF_SWEEP, st, h->order2 ? 3 : 1);
+  if (h->order2) {
+    // second order: the explicit slope terms (and the face-value wall correction) of this
+    // scan depend only on the state before it, so they join the right-hand side
+    double* b2 = h->at<double>(h->off.o2rhs);
+    cudaError_t e = launch_slope_rhs(aux_args(h, l), f, rhs, b2, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    a.rhs = b2;
+  }
   return cuda_status(launch_sweep(a, h->sweep, h->sweep_arith, st));
 }
 
@@ -872,7 +886,8 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
         problems[q].precision != problems[0].precision || problems[q].b0 != problems[0].b0 ||
         (problems[q].collision == SGS_BGK) != (problems[0].collision == SGS_BGK) ||
         (problems[q].collision != SGS_BGK && problems[q].collision != problems[0].collision) ||
-        problems[q].conserve_proj != problems[0].conserve_proj)
+        problems[q].conserve_proj != problems[0].conserve_proj ||
+        (problems[q].order == 2) != (problems[0].order == 2))
       return SGS_ERR_UNSUPPORTED;
   }
   if (problems[0].space_dim == 2 && n_inst != 1) return SGS_ERR_UNSUPPORTED;  // one 2-D instance per handle
@@ -886,6 +901,7 @@ int sgs_setup(const sgs_problem* problems, int n_inst, sgs_handle** out, size_t*
   h->precision = problems[0].precision;
   h->spectral = problems[0].collision != SGS_BGK;
   h->cproj = h->spectral ? problems[0].conserve_proj : 0;
+  h->order2 = problems[0].order == 2;
   h->two_d = problems[0].space_dim == 2;
   long long K = (long long)h->N * h->N * h->N;
   h->inst.resize(n_inst);

@@ -55,6 +55,7 @@ class _Problem(C.Structure):
         ("newton_max", C.c_int),
         ("inner_method", C.c_int),
         ("conserve_proj", C.c_int),
+        ("order", C.c_int),
     ]
 
 
@@ -107,6 +108,7 @@ class Problem:
     newton_max: int = 50
     inner_method: int = PFP
     conserve_proj: int = 0  # 1: FP64 projection of Q onto the zero-moment subspace (not in the paper)
+    order: int = 1          # spatial order of the 1-D scheme: 1, or 2 (linear reconstruction, eq. (slope))
     space_dim: int = 1
     ny: int = 1
     y_lo: float = 0.0
@@ -125,7 +127,7 @@ class Problem:
         p = _Problem()
         for name in ("space_dim", "nx", "x_lo", "x_hi", "ny", "y_lo", "y_hi", "nv", "v_max", "collision", "b0",
                      "eps", "total_mass", "precision", "inner_tol", "inner_max", "inner_fixed", "newton_tol",
-                     "newton_max", "inner_method", "conserve_proj"):
+                     "newton_max", "inner_method", "conserve_proj", "order"):
             setattr(p, name, getattr(self, name))
         kinds = list(self.bc_kind) + list(self.bc_kind_y)
         rhos = list(self.bc_rho) + list(self.bc_rho_y)
