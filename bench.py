@@ -20,7 +20,8 @@ four orderings per SGS iteration, V-cycles on 64^2/32^2/16^2 cells).
 data, V-cycles on 128/64/32/16 cells) and records the shock position.
 
 --conserve-proj 1|2 adds the FP64 conservation projection of Q (plain or Maxwellian-weighted;
-not in the paper); --pin-mass holds the shock's total mass at its initial value (eq. (32)).
+not in the paper); --pin-mass holds the shock's total mass at its initial value (eq. (32));
+--order 2 runs the second-order scheme (1-D workloads).
 
 N > 1 runs independent replicas (one per GPU, launched by torchrun): the method is a
 sequential scan per problem, so work is replicated, not sharded ("scaling": "weak").
@@ -68,6 +69,8 @@ def parse():
     ap.add_argument("--t2tol-cap", type=float, default=150.0, help="seconds allowed per time-to-residual run")
     ap.add_argument("--conserve-proj", type=int, choices=[0, 1, 2], default=0,
                     help="conservation projection of Q: 0 the paper's operator, 1 plain, 2 Maxwellian-weighted")
+    ap.add_argument("--order", type=int, choices=[1, 2], default=1,
+                    help="spatial order of the 1-D scheme (2: linear reconstruction, eq. (slope))")
     ap.add_argument("--pin-mass", action="store_true",
                     help="shock: hold the total mass at the initial state's (eq. (32) rescale), pinning the shock")
     ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d", "dft"], default=None,
@@ -164,6 +167,7 @@ class ClockSampler:
 WORKLOAD = "heat"
 CONSERVE_PROJ = 0   # --conserve-proj
 PIN_MASS = False    # --pin-mass (shock)
+ORDER = 1           # --order
 
 
 def workload():
@@ -214,6 +218,8 @@ def make_solver(wl, precision):
         p = sgs.Problem(nx=wl.J, x_lo=wl.x_lo, x_hi=wl.x_hi, nv=wl.N, v_max=wl.L, eps=wl.eps,
                         bc_T=(wl.T_left, wl.T_right), total_mass=wl.total_mass, precision=precision)
     p.conserve_proj = CONSERVE_PROJ
+    if ORDER != 1:
+        p.order = ORDER
     return sgs.Solver(p)
 
 
@@ -223,6 +229,8 @@ def config_of(wl):
         c["conserve_proj"] = ["plain", "maxwellian_weighted"][CONSERVE_PROJ - 1]
     if PIN_MASS and is_shock(wl):
         c["total_mass_pinned"] = True
+    if ORDER != 1:
+        c["order"] = ORDER
     return c
 
 
@@ -795,11 +803,12 @@ def profile_case(which):
 
 
 def main():
-    global WORKLOAD, CONSERVE_PROJ, PIN_MASS
+    global WORKLOAD, CONSERVE_PROJ, PIN_MASS, ORDER
     args = parse()
     WORKLOAD = args.workload
     CONSERVE_PROJ = args.conserve_proj
     PIN_MASS = args.pin_mass
+    ORDER = args.order
     if args.case:
         profile_case(args.case)
         return
