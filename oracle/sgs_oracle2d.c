@@ -85,20 +85,54 @@ void or_ghost2d(const or_problem2d* q, int s, const double* f_adj, double* ghost
 }
 
 /* Neighbour of cell (i, j) across side s, or its ghost (computed into buf). */
-static const double* neighbour(const or_problem2d* q, const double* f, int i, int j, int s, double* buf) {
+/* Second-order scheme in 2-D: the slopes of eq. (slope) in each direction, x along each row
+ * and y along each column (central inside, one-sided in the end cells; zero for the
+ * first-order scheme or a single cell in that direction). */
+static void slopes2d(const or_problem2d* q, const double* f, double* sx, double* sy) {
   int nx = q->p.J, ny = q->ny, N = q->p.N;
   long K = (long)N * N * N;
-  const double* self = f + ((long)j * nx + i) * K;
-  int ii = i, jj = j;
-  if (s == 0) ii = i - 1;
-  if (s == 1) ii = i + 1;
-  if (s == 2) jj = j - 1;
-  if (s == 3) jj = j + 1;
-  if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) {
-    or_ghost2d(q, s, self, buf);
-    return buf;
-  }
-  return f + ((long)jj * nx + ii) * K;
+  int o2 = q->p.order == 2;
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      long c = (long)j * nx + i;
+      for (long k = 0; k < K; k++) {
+        double a = 0.0, b = 0.0;
+        if (o2 && nx >= 2) {
+          if (i == 0)
+            a = f[(c + 1) * K + k] - f[c * K + k];
+          else if (i == nx - 1)
+            a = f[c * K + k] - f[(c - 1) * K + k];
+          else
+            a = 0.5 * (f[(c + 1) * K + k] - f[(c - 1) * K + k]);
+        }
+        if (o2 && ny >= 2) {
+          if (j == 0)
+            b = f[(c + nx) * K + k] - f[c * K + k];
+          else if (j == ny - 1)
+            b = f[c * K + k] - f[(c - nx) * K + k];
+          else
+            b = 0.5 * (f[(c + nx) * K + k] - f[(c - nx) * K + k]);
+        }
+        sx[c * K + k] = a;
+        sy[c * K + k] = b;
+      }
+    }
+}
+
+/* The neighbour across side s, or the wall ghost built from the outgoing face value of the
+ * cell itself (f -/+ s/2 of the slope normal to that side; the cell value at first order). */
+static const double* neighbour_face(const or_problem2d* q, const double* f, const double* sx, const double* sy,
+                                    int i, int j, int s, double* buf, double* face) {
+  int nx = q->p.J, ny = q->ny, N = q->p.N;
+  long K = (long)N * N * N;
+  int ii = i + (s == 1) - (s == 0), jj = j + (s == 3) - (s == 2);
+  if (ii >= 0 && ii < nx && jj >= 0 && jj < ny) return f + ((long)jj * nx + ii) * K;
+  long c = (long)j * nx + i;
+  const double* sl = (s < 2 ? sx : sy) + c * K;
+  double sign = (s == 0 || s == 2) ? -0.5 : 0.5;
+  for (long k = 0; k < K; k++) face[k] = f[c * K + k] + sign * sl[k];
+  or_ghost2d(q, s, face, buf);
+  return buf;
 }
 
 double or_dx2d(const or_problem2d* q) { return (q->p.x_hi - q->p.x_lo) / q->p.J; }
@@ -110,17 +144,25 @@ double or_dy2d(const or_problem2d* q) { return (q->y_hi - q->y_lo) / q->ny; }
  * stored before the visit. P, nu from the collision evaluation that preceded the sweep. */
 void or_sweep2d(const or_problem2d* q, int o, double* f, const double* P, const double* nu, const double* b,
                 or_stats* st) {
+  /* Second order: the slopes are explicit, taken from the state before this ordering, and
+   * enter r as -(v1^+ sx_W - v1 sx + v1^- sx_E)/(2 dx) - (v2^+ sy_S - v2 sy + v2^- sy_N)/(2 dy)
+   * with zero slopes beyond the walls; wall ghosts from the outgoing face values. */
   int nx = q->p.J, ny = q->ny, N = q->p.N;
   long K = (long)N * N * N;
   double dx = or_dx2d(q), dy = or_dy2d(q), eps = q->p.eps;
   int dirx = (o == 0 || o == 2) ? 1 : -1;
   int diry = (o == 0 || o == 3) ? 1 : -1;
+  int o2 = q->p.order == 2;
   double* v = (double*)malloc(sizeof(double) * N);
   double* c = (double*)malloc(sizeof(double) * K);
   double* r = (double*)malloc(sizeof(double) * K);
+  double* face = (double*)malloc(sizeof(double) * K);
+  double* sx = (double*)malloc(sizeof(double) * nx * ny * K);
+  double* sy = (double*)malloc(sizeof(double) * nx * ny * K);
   double* gb[4];
   for (int s = 0; s < 4; s++) gb[s] = (double*)malloc(sizeof(double) * K);
   or_velocity_nodes(N, q->p.L, v);
+  slopes2d(q, f, sx, sy);
   for (int i1 = 0; i1 < N; i1++)
     for (int i2 = 0; i2 < N; i2++)
       for (int i3 = 0; i3 < N; i3++) c[((long)i1 * N + i2) * N + i3] = fabs(v[i1]) / dx + fabs(v[i2]) / dy;
@@ -130,7 +172,7 @@ void or_sweep2d(const or_problem2d* q, int o, double* f, const double* P, const 
       int i = dirx > 0 ? ii : nx - 1 - ii;
       long cell = (long)j * nx + i;
       const double* nb[4];
-      for (int s = 0; s < 4; s++) nb[s] = neighbour(q, f, i, j, s, gb[s]);
+      for (int s = 0; s < 4; s++) nb[s] = neighbour_face(q, f, sx, sy, i, j, s, gb[s], face);
       for (int i1 = 0; i1 < N; i1++) {
         double v1p = v[i1] > 0.0 ? v[i1] : 0.0, v1m = v[i1] < 0.0 ? v[i1] : 0.0;
         for (int i2 = 0; i2 < N; i2++) {
@@ -139,6 +181,12 @@ void or_sweep2d(const or_problem2d* q, int o, double* f, const double* P, const 
             long k = ((long)i1 * N + i2) * N + i3;
             r[k] = (-v1p * nb[0][k] + v1m * nb[1][k]) / dx + (-v2p * nb[2][k] + v2m * nb[3][k]) / dy -
                    P[cell * K + k] / eps - (b ? b[cell * K + k] : 0.0);
+            if (o2) {
+              double xw = i > 0 ? sx[(cell - 1) * K + k] : 0.0, xe = i < nx - 1 ? sx[(cell + 1) * K + k] : 0.0;
+              double ys = j > 0 ? sy[(cell - nx) * K + k] : 0.0, yn = j < ny - 1 ? sy[(cell + nx) * K + k] : 0.0;
+              r[k] -= (v1p * xw - v[i1] * sx[cell * K + k] + v1m * xe) / (2.0 * dx) +
+                      (v2p * ys - v[i2] * sy[cell * K + k] + v2m * yn) / (2.0 * dy);
+            }
           }
         }
       }
@@ -149,6 +197,9 @@ void or_sweep2d(const or_problem2d* q, int o, double* f, const double* P, const 
   free(v);
   free(c);
   free(r);
+  free(face);
+  free(sx);
+  free(sy);
 }
 
 /* Mass rescale (eq. (32)) with the cell area dx dy. */
@@ -168,27 +219,41 @@ void or_rescale2d(const or_problem2d* q, double* f) {
 /* Outer residual R = T(f) - Q/eps - b with ghosts from the same f; returns
  * sqrt(dx dy sum_cells sum_k w R^2). Rout may be NULL. */
 double or_residual2d(const or_problem2d* q, const double* f, const double* Q, const double* b, double* Rout) {
+  /* The 2-D upwind residual with the face values of the reconstruction in each direction
+   * (the cell values at first order) and wall ghosts from the outgoing face values. */
   int nx = q->p.J, ny = q->ny, N = q->p.N;
   long K = (long)N * N * N;
   double dx = or_dx2d(q), dy = or_dy2d(q), w = weight2(N, q->p.L), acc = 0.0;
   double* v = (double*)malloc(sizeof(double) * N);
+  double* face = (double*)malloc(sizeof(double) * K);
+  double* sx = (double*)malloc(sizeof(double) * nx * ny * K);
+  double* sy = (double*)malloc(sizeof(double) * nx * ny * K);
   double* gb[4];
   for (int s = 0; s < 4; s++) gb[s] = (double*)malloc(sizeof(double) * K);
   or_velocity_nodes(N, q->p.L, v);
+  slopes2d(q, f, sx, sy);
   for (int j = 0; j < ny; j++)
     for (int i = 0; i < nx; i++) {
       long cell = (long)j * nx + i;
       const double* fc = f + cell * K;
       const double* nb[4];
-      for (int s = 0; s < 4; s++) nb[s] = neighbour(q, f, i, j, s, gb[s]);
+      for (int s = 0; s < 4; s++) nb[s] = neighbour_face(q, f, sx, sy, i, j, s, gb[s], face);
+      /* slopes of the neighbours across each side (zero beyond a wall) */
+      const double* sW = i > 0 ? sx + (cell - 1) * K : NULL;
+      const double* sE = i < nx - 1 ? sx + (cell + 1) * K : NULL;
+      const double* sS = j > 0 ? sy + (cell - nx) * K : NULL;
+      const double* sN = j < ny - 1 ? sy + (cell + nx) * K : NULL;
       for (int i1 = 0; i1 < N; i1++) {
         double v1p = v[i1] > 0.0 ? v[i1] : 0.0, v1m = v[i1] < 0.0 ? v[i1] : 0.0;
         for (int i2 = 0; i2 < N; i2++) {
           double v2p = v[i2] > 0.0 ? v[i2] : 0.0, v2m = v[i2] < 0.0 ? v[i2] : 0.0;
           for (int i3 = 0; i3 < N; i3++) {
             long k = ((long)i1 * N + i2) * N + i3;
-            double R = (v1p * (fc[k] - nb[0][k]) + v1m * (nb[1][k] - fc[k])) / dx +
-                       (v2p * (fc[k] - nb[2][k]) + v2m * (nb[3][k] - fc[k])) / dy - Q[cell * K + k] / q->p.eps -
+            double hx = 0.5 * sx[cell * K + k], hy = 0.5 * sy[cell * K + k];
+            double xw = nb[0][k] + (sW ? 0.5 * sW[k] : 0.0), xe = nb[1][k] - (sE ? 0.5 * sE[k] : 0.0);
+            double ys = nb[2][k] + (sS ? 0.5 * sS[k] : 0.0), yn = nb[3][k] - (sN ? 0.5 * sN[k] : 0.0);
+            double R = (v1p * ((fc[k] + hx) - xw) + v1m * (xe - (fc[k] - hx))) / dx +
+                       (v2p * ((fc[k] + hy) - ys) + v2m * (yn - (fc[k] - hy))) / dy - Q[cell * K + k] / q->p.eps -
                        (b ? b[cell * K + k] : 0.0);
             if (Rout) Rout[cell * K + k] = R;
             acc += w * R * R;
@@ -198,6 +263,9 @@ double or_residual2d(const or_problem2d* q, const double* f, const double* Q, co
     }
   for (int s = 0; s < 4; s++) free(gb[s]);
   free(v);
+  free(face);
+  free(sx);
+  free(sy);
   return sqrt(dx * dy * acc);
 }
 
