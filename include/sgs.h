@@ -141,13 +141,16 @@ size_t sgs_field_elems(const sgs_handle* h);
 /* Collision step for every cell (eqs. (16), (28)):
  *   moments and discrete Maxwellian M (eqs. (13)-(14)), Q = Q^FSM[f,f] - Q^FSM[M,M]
  *   computed as the single symmetric bilinear sum Q_s(f - M, f + M), and
- *   P = Q - nu (M - f). f, Q (device, nullable), P (device, nullable). */
+ *   P = Q - nu (M - f). With conserve_proj, Q is projected (FP64) before P is formed.
+ *   f, Q (device, nullable), P (device, nullable). */
 int sgs_collide(sgs_handle* h, const double* f, double* Q, double* P, void* stream);
 
 /* One SGS scan (eq. (29)) over every instance, forward (x_lo -> x_hi) or backward, in a
  * single persistent launch (one thread-block cluster per instance, no host round trip).
  * f (device) is updated in place; P (device) from the preceding sgs_collide; rhs (device,
- * nullable) is the b of R(f) = b (multigrid / defect correction). */
+ * nullable) is the b of R(f) = b (multigrid / defect correction). Second order (order 2,
+ * 1-D): the slope terms of eq. (SGS_BGK) and the face-value wall densities are taken from f
+ * as it is when the scan starts (explicit slopes). */
 int sgs_sweep_forward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream);
 int sgs_sweep_backward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream);
 /* One scan in a given ordering. 1-D: 0 forward, 1 backward. 2-D (eq. (29) in each
@@ -171,7 +174,9 @@ int sgs_rescale(sgs_handle* h, double* f, void* stream);
 int sgs_si_iteration(sgs_handle* h, double* f, double* P, const double* rhs, void* stream);
 
 /* Outer residual R = T(f) - Q/eps - rhs (Section 4 stopping rule), res[q] (device,
- * n_inst doubles) = sqrt(dx sum_j sum_k w R^2) per instance. Q from sgs_collide(f). */
+ * n_inst doubles) = sqrt(dx sum_j sum_k w R^2) per instance. Q from sgs_collide(f). T is
+ * the upwind transport of eq. (upwind) with the face values of the reconstruction (the
+ * cell values at first order) and wall ghosts from the same f. */
 int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* rhs, double* res, void* stream);
 
 /* Outer residual of ONE instance that allocates nothing (no counterpart in the paper: it
