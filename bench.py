@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-t2tol", action="store_true", help="skip the time-to-residual runs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default scan shape")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="sequential iterations (no collision steps pipelined behind the scans)")
     ap.add_argument("--t2tol-all", action="store_true", help="also time the plain FP64 SGS form to 1e-8")
     ap.add_argument("--t2tol-cap", type=float, default=150.0, help="seconds allowed per time-to-residual run")
     ap.add_argument("--conserve-proj", type=int, choices=[0, 1, 2], default=0,
@@ -73,7 +75,7 @@ def parse():
                     help="spatial order of the 1-D scheme (2: linear reconstruction, eq. (slope))")
     ap.add_argument("--pin-mass", action="store_true",
                     help="shock: hold the total mass at the initial state's (eq. (32) rescale), pinning the shock")
-    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d", "dft"], default=None,
+    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d", "dft", "peaks"], default=None,
                     help="run a small case of one kernel class (for profiler captures) and exit")
     return ap.parse_args()
 
@@ -263,6 +265,8 @@ def run_native(args, rank, world, local):
     wl = workload()
     f0 = torch.from_numpy(wl.initial_state().reshape(-1)).to(dev)
     s = make_solver(wl, sgs.FP32)
+    if args.no_overlap:
+        s.set_overlap(False)
     f = f0.clone()
     Q, P = s.field(), s.field()
     res_hi = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -283,38 +287,50 @@ def run_native(args, rank, world, local):
             s.dc_step(f, Q, P, 0, res=res_hi)
         s.iterate(f, Q, P, flags=sgs.IT_P_VALID | sgs.IT_EVAL)
 
+    # measured denominators of the rooflines (FMA pipes, SM count, scan latencies), untimed
+    peaks = measure_peaks(wl, s.sweep_shape(), local)
+
     # warm-up (untimed): the first DC evaluation also initialises P
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
     rank_barrier(world)
-    s.profile(True)
-    s.profile_read()
-    launches0 = s.launch_count()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
+
+    def timed_pass(first, profiled):
+        """K steps from step index `first`, each bracketed by CUDA events on the launching
+        stream, an L2 flush between steps; the library's per-class event profiler on or off."""
+        s.profile(profiled)
+        s.profile_read()
+        n0 = s.launch_count()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         torch.cuda.synchronize()
         for i in range(args.steps):
             flush.zero_()  # L2 flush between timed steps (outside the events)
             ev[i][0].record(stream)
-            step(args.warmup + i)
+            step(first + i)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        prof = s.profile_read()
+        s.profile(False)
+        return [a.elapsed_time(b) for a, b in ev], s.launch_count() - n0, prof
+
+    # the headline: profiler off
+    with ClockSampler(local) as clk:
+        ms_steps, launches, _ = timed_pass(args.warmup, False)
         rank_barrier(world)
-    launches = s.launch_count() - launches0
-    prof = s.profile_read()
-    s.profile(False)
-    ms_steps = [a.elapsed_time(b) for a, b in ev]
     ms_total = max_over_ranks(sum(ms_steps), world, dev)
     value = whole_job_rate(visits_per_step * args.steps, world, ms_total)
+    # the per-class split: the same K steps again with every launch group bracketed by events
+    ms_prof_steps, _, prof = timed_pass(args.warmup + args.steps, True)
     status = s.read_status()
 
     # dominant kernel class and its roofline
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     dom = max(prof, key=lambda k: prof[k][0])
-    roofs = {k: roofline(k, prof, wl, sm_mhz) for k in ("sweep", "sum", "sum_fp64", "sum_df64") if prof[k][1] > 0}
-    roof = roofs.get(dom) or roofline(dom, prof, wl, sm_mhz)
+    roofs = {k: roofline(k, prof, wl, sm_mhz, peaks, status) for k in ("sweep", "sum", "sum_fp64", "sum_df64")
+             if prof[k][1] > 0}
+    roof = roofs.get(dom) or roofline(dom, prof, wl, sm_mhz, peaks, status)
 
     # end to end through the C ABI with host buffers: H2D of the state (f, P), one step,
     # D2H of the step's residual
@@ -341,6 +357,7 @@ def run_native(args, rank, world, local):
             "steps": args.steps,
             "warmup": args.warmup,
             "ms_per_step": ms_total / args.steps,
+            "ms_steps": [round(x, 3) for x in ms_steps],
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
@@ -355,10 +372,15 @@ def run_native(args, rank, world, local):
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "roofline_kernels": roofs,
+            "pipelined": s.overlap(),
             "scan_shape": {"nodes_per_thread": s.sweep_shape()[0], "ctas_per_cluster": s.sweep_shape()[1],
                            "threads_per_cta": s.sweep_shape()[2],
                            "chosen_by": "autotuner" if tuning else "default", "tuning": tuning},
             "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
+            "kernels_ms_from": (f"a second pass of the same {args.steps} steps with the library's event profiler on "
+                                f"({sum(ms_prof_steps) / args.steps:.3f} ms per step there); the headline pass "
+                                "runs without it"),
+            "measured_peaks": peaks,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": int(launches),
@@ -396,12 +418,40 @@ def kernel_traffic(name, units):
     return rec["dram_bytes_per_unit"] * units
 
 
-def roofline(cls, prof, wl, sm_mhz):
-    """Roofline of one kernel class over the timed region: algorithmic work per launch over
-    the average launch time (CUDA events on the launching stream)."""
+def measure_peaks(wl, shape, local=0):
+    """Denominators measured on this device, untimed, before the timed region: the FFMA and
+    DFMA throughput of the CUDA cores (sgs_peak_fma: independent FMA chains on every SM), the
+    SM count, the SM clock sampled while the FFMA probe runs, and the latencies of the
+    scan's building blocks in the scan's launch shape (sgs_probe_scan: a cluster reduction,
+    a Newton iteration of the discrete Maxwellian)."""
+    from paper_2409_01910_gb300 import sgs
+
+    with ClockSampler(local) as clk:
+        t_end = time.perf_counter() + 1.0
+        fp32 = []
+        while time.perf_counter() < t_end:  # about a second of FFMA load for the clock samples
+            fp32.append(sgs.peak_fma(sgs.FP32, iters=1 << 20))
+    fp64 = max((sgs.peak_fma(sgs.FP64, iters=1 << 14) for _ in range(3)), key=lambda x: x["tflops"])
+    best32 = max(fp32, key=lambda x: x["tflops"])
+    ept, cluster, threads = shape
+    precision = sgs.FP32  # the mixed solver's scans run in double-float
+    red = sgs.probe_scan(wl.N, wl.L, precision, cluster, threads, 0, reps=4000)
+    newt = sgs.probe_scan(wl.N, wl.L, precision, cluster, threads, 1, reps=4000)
+    return {"fp32_ffma_tflops": round(best32["tflops"], 3), "fp64_dfma_tflops": round(fp64["tflops"], 4),
+            "sms": best32["sms"], "sm_mhz_during_probe": clk.summary().get("sm_mhz"),
+            "scan_cluster_reduce_us": round(red, 3), "scan_newton_iteration_us": round(newt, 3),
+            "scan_probe_shape": {"ctas_per_cluster": cluster, "threads_per_cta": threads, "arith": "double-float"},
+            "how": ("sgs_peak_fma: 8 independent FMA chains per thread, every SM fully occupied, CUDA events; "
+                    "sgs_probe_scan: 4000 dependent operations in one cluster minus an empty launch")}
+
+
+def roofline(cls, prof, wl, sm_mhz, peaks, stats=None):
+    """Roofline of one kernel class over the profiled pass: algorithmic work per launch over
+    the average launch time (CUDA events on the launching stream), against the measured peak
+    of the pipe that bounds it (measure_peaks) or the measured HBM bandwidth."""
     ms, n = prof[cls]
     avg = ms / max(1, n)
-    peaks, src = measured_peaks()
+    hbm, src = measured_peaks()
     K = wl.N ** 3
     if cls in ("sum", "sum_fp64"):
         # algorithmic work: 10 flops per mode pair over the Hermitian half, every cell of the
@@ -409,37 +459,60 @@ def roofline(cls, prof, wl, sm_mhz):
         flops = 10 * 0.5 * pairs_per_cell(wl.N) * wl.J
         ach = flops / (avg * 1e-3) / 1e12
         if cls == "sum":
-            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+            peak = peaks["fp32_ffma_tflops"]
             return {"kernel": "k_sum<float> (direct spectral sum, FP32)", "bound": "alu", "achieved": ach,
                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
-        peak = 1.25
+                    "peak_source": f"FFMA rate measured by sgs_peak_fma on {peaks['sms']} SMs (of measured)"}
+        peak = peaks["fp64_dfma_tflops"]
         return {"kernel": "k_sum<double> (direct spectral sum, FP64)", "bound": "alu", "achieved": ach,
                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (of nominal)"}
+                "peak_source": f"DFMA rate measured by sgs_peak_fma on {peaks['sms']} SMs (of measured)"}
     if cls == "sum_df64":
         # FP32-pipe operations of one pair in the double-float sum: 8 for w b (two
         # two-products with cross terms) + 4 x 12 for the products with a and their two-sum
-        # accumulation
+        # accumulation; the pipe issues one operation per lane per clock, half the FFMA flop rate
         ops = 56 * 0.5 * pairs_per_cell(wl.N) * wl.J
         ach = ops / (avg * 1e-3) / 1e12
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+        peak = peaks["fp32_ffma_tflops"] / 2.0
         return {"kernel": "k_sum_df (direct spectral sum, double-float on the FP32 pipes)", "bound": "alu",
                 "achieved": ach, "peak": peak, "unit": "T FP32-pipe op/s", "frac": ach / peak, "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 1 op x {sm_mhz:.0f} MHz (median sampled)"}
+                "peak_source": "half the FFMA flop rate measured by sgs_peak_fma (one op per lane per clock; "
+                               "of measured)"}
     if cls == "sweep":
         # per visit: read the upwind/downwind neighbours, f_j and P_j, write f_j (1-D: 5 K
         # doubles; 2-D: 7 K doubles); one profiled group = one scan over every cell
         byts = (7 if is_cavity(wl) else 5) * K * 8 * wl.J
         ach = byts / (avg * 1e-3) / 1e9
-        return {"kernel": "k_sweep<dfloat,8> (persistent SGS scan, one cluster of 16 CTAs)", "bound": "hbm",
-                "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
-                "traffic": kernel_traffic("k_sweep<dfloat,8>", wl.J), "peak_source": f"hbm_gbs ({src})",
-                "note": "latency-bound: one visit is a chain of cluster reductions and Newton solves"}
+        out = {"kernel": "k_sweep<dfloat,8> (persistent SGS scan, one cluster per instance)", "bound": "hbm",
+               "achieved": ach, "peak": hbm["hbm_gbs"], "unit": "GB/s", "frac": ach / hbm["hbm_gbs"],
+               "traffic": kernel_traffic("k_sweep<dfloat,8>", wl.J), "peak_source": f"hbm_gbs ({src})",
+               "note": "latency-bound: one visit is a chain of cluster reductions and Newton solves"}
+        if stats and stats.get("visits") and not is_cavity(wl):
+            out["latency_model"] = scan_latency_model(avg * 1e3 / wl.J, stats, peaks)
+        return out
     byts = 2 * K * 8 * wl.J
     ach = byts / (avg * 1e-3) / 1e9
-    return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+    return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": hbm["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / hbm["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+
+
+def scan_latency_model(us_per_visit, stats, peaks):
+    """The scan's time per cell visit against the chain it runs: cluster reductions (two per
+    visit, then one per inner update) and Newton iterations (each an evaluation of the
+    separable Maxwellian with its combination and factorisation; one more evaluation per
+    solve that starts without one), at the latencies measured by sgs_probe_scan."""
+    v = stats["visits"]
+    inner = stats["inner_iters"] / v
+    reductions = 2.0 + inner
+    evaluations = (stats["newton_iters"] + stats["newton_solves"]) / v
+    t_red = reductions * peaks["scan_cluster_reduce_us"]
+    t_newton = evaluations * peaks["scan_newton_iteration_us"]
+    return {"us_per_visit_measured": round(us_per_visit, 2), "inner_updates_per_visit": round(inner, 3),
+            "cluster_reductions_per_visit": round(reductions, 3),
+            "newton_evaluations_per_visit": round(evaluations, 3),
+            "us_cluster_reductions": round(t_red, 2), "us_newton": round(t_newton, 2),
+            "modelled_fraction": round((t_red + t_newton) / us_per_visit, 3),
+            "rest": "elementwise passes over the cell's nodes, loads of neighbours and P, the per-visit set-up"}
 
 
 def time_to_tol(wl, f0, dev, kind, cap_s, tol=1e-8, shape=None):
@@ -652,6 +725,7 @@ def run_batch(args, rank, world, local):
     probs = [sgs.Problem(nx=w.J, nv=w.N, v_max=w.L, eps=w.eps, bc_T=(w.T_left, w.T_right),
                          total_mass=w.total_mass, precision=sgs.FP32) for w in wls]
     b = sgs.Batch(probs)
+    peaks = measure_peaks(wls[0], next(iter(b.solvers.values())).sweep_shape(), local)
     states = [w.initial_state() for w in wls]
     b.load(states)
     tuning = None if args.no_autotune else b.autotune(reps=1)
@@ -701,10 +775,10 @@ def run_batch(args, rank, world, local):
     flops = sum(10 * 0.5 * pairs_per_cell(N) * sum(w.J for w in wls if w.N == N) for N in b.groups)
     n_sum = prof["sum"][1]
     ach = flops * (n_sum / max(1, len(b.groups))) / (prof["sum"][0] * 1e-3) / 1e12 if prof["sum"][0] else None
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    peak = peaks["fp32_ffma_tflops"]
     roof = {"kernel": "k_sum<float> (direct spectral sum, FP32), all groups", "bound": "alu", "achieved": ach,
             "peak": peak, "unit": "TFLOP/s", "frac": ach / peak if ach else None, "traffic": None,
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)",
+            "peak_source": f"FFMA rate measured by sgs_peak_fma on {peaks['sms']} SMs (of measured)",
             "from": "one eager cycle (graph replays are not profiled)"}
     shapes = {str(nv): dict(zip(("nodes_per_thread", "ctas_per_cluster", "threads_per_cta"), s.sweep_shape()))
               for nv, s in b.solvers.items()}
@@ -745,7 +819,7 @@ def run_batch(args, rank, world, local):
         "e2e": {"value": visits_per_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "note": "every group's (f, P) copied from pinned host memory, one replay, residuals read back"},
-        "clocks": clocks, "gpu_launches": int(launches_per_cycle * args.steps),
+        "clocks": clocks, "gpu_launches": int(launches_per_cycle * args.steps), "measured_peaks": peaks,
         "residuals_after": {"max": max(res), "converged_1e-8": int(sum(r < 1e-8 for r in res))},
         "device_status": b.status(),
     }
@@ -761,6 +835,11 @@ def profile_case(which):
     from paper_2409_01910_gb300 import inputs as I
     from paper_2409_01910_gb300 import sgs
 
+    if which == "peaks":
+        wl = I.heat_64cells_32v()
+        s = make_solver(wl, sgs.FP32)
+        print(json.dumps({"case": which, "peaks": measure_peaks(wl, s.sweep_shape())}))
+        return
     if which == "dft":
         # the transforms of the mixed solver's increment-form collision on the 64-cell workload
         wl = I.heat_64cells_32v()

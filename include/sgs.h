@@ -191,10 +191,13 @@ int sgs_residual(sgs_handle* h, const double* f, const double* Q, const double* 
  * SGS_ERR_ARG with a message naming the limit. The first call on a device looks up the
  * array's device address with that device current; make that first call before any
  * stream capture. All calls share the array: calls that overlap on the GPU race, so order
- * them on one stream. Every slot a call reads is written earlier in the same call. */
+ * them on one stream. Every slot a call reads is written earlier in the same call.
+ * The problem is validated as sgs_setup validates it (same return codes), then restricted to
+ * one 1-D instance (SGS_ERR_ARG otherwise) at first order (SGS_ERR_UNSUPPORTED for order 2).
+ * The looked-up address belongs to the device's context at the first call: after a
+ * cudaDeviceReset() of that device the entry point must not be called again in the process. */
 int sgs_residual_noalloc(const sgs_problem* p, const double* f, const double* Q, const double* rhs, double* res,
-                         void* stream);  /* 1-D problems only (SGS_ERR_ARG otherwise); first order
-                                            only (SGS_ERR_UNSUPPORTED for order 2) */
+                         void* stream);
 
 /* Collision step in a chosen arithmetic (SGS_FP32 and SGS_DF64 need a handle set up with
  * precision SGS_FP32, whose workspace then carries the FP64 and FP32 weight tables and the
@@ -240,6 +243,21 @@ int sgs_set_dc_precision(sgs_handle* h, int precision);
 int sgs_vcycle(sgs_handle* h, double* f, int levels, int pre, int post, int coarse_iters, void* stream);
 /* Number of grids available to sgs_vcycle: 1 + how often every instance's cell count halves. */
 int sgs_max_levels(const sgs_handle* h);
+
+/* Pipelined SGS iterations (on by default). A handle holding one 1-D instance of at least 64
+ * cells (two lane groups of 32), first order, spectral collisions, runs the scans of
+ * sgs_iterate, sgs_dc_step and the finest-level smoothing of sgs_vcycle in segments of 32
+ * cells on a high-priority stream of its own and evaluates the collision step of each group
+ * on the caller's stream as soon as the scan has left that group: the collision step for the
+ * backward scan behind the forward scan and, with SGS_IT_EVAL, the one of the new iterate
+ * behind the backward scan (the groups evaluated before the mass rescale of eq. (32) are then
+ * scaled to the rescaled state: Q and P by lam^2, nu by lam; exact up to rounding). The order
+ * of the method is unchanged: every cell sees the inputs of the sequential iteration. The two
+ * streams are joined again before each call returns (events; also under stream capture).
+ * sgs_dc_step then also evaluates the collision step after each of its iterations (Q and P
+ * hold the last iterate's). sgs_get_overlap: 1 when the bound handle pipelines, else 0. */
+int sgs_set_overlap(sgs_handle* h, int enable);
+int sgs_get_overlap(const sgs_handle* h);
 
 /* Kernel-time profiling. When enabled, every group of launches is bracketed by CUDA events
  * recorded on the launching stream; sgs_profile_read synchronises on them and returns, per
@@ -294,6 +312,22 @@ typedef struct {
  * (reps + 1) symmetric sweeps with the given P per candidate. Synchronises the stream; not
  * graph-capturable (call it before capturing). */
 int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning* out, void* stream);
+
+/* Measurement probes (not part of the method; they supply the denominators of the
+ * benchmark's rooflines and its latency model of the scan).
+ *   sgs_peak_fma: FMA throughput of the CUDA-core pipes of the current device (SGS_FP32:
+ *     FFMA, SGS_FP64: DFMA), independent FMA chains on every SM, iters FMAs per chain; tflops
+ *     = 2 flops per FMA over the CUDA-event time of the launch on stream; sms (nullable) the
+ *     SM count used, ms (nullable) the time. Synchronises the stream; allocates nothing.
+ *   sgs_probe_scan: latency of one building block of the persistent scan, in one cluster of
+ *     `cluster` CTAs of `threads` threads on the nv^3 grid of [-v_max, v_max]^3, in the scan
+ *     arithmetic of a handle of that precision (SGS_FP32: double-float, SGS_FP64: FP64):
+ *     mode 0 a cluster reduction of seven values, mode 1 one Newton iteration of the
+ *     discrete Maxwellian (evaluation, combination, factorisation). us_per_op = (time of reps
+ *     operations - time of an empty launch) / reps in microseconds. Synchronises the stream. */
+int sgs_peak_fma(int precision, long long iters, double* tflops, int* sms, float* ms, void* stream);
+int sgs_probe_scan(int nv, double v_max, int precision, int cluster, int threads, int mode, int reps,
+                   float* us_per_op, void* stream);
 
 /* Synchronises the stream and reads the accumulated status and counters. */
 int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream);

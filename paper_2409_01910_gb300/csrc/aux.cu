@@ -368,6 +368,45 @@ cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Collision results of cells evaluated before the rescale, carried over to the rescaled
+// state: with f -> lam f, Q and P = Q - nu (M - f) scale by lam^2 (Q is quadratic, nu linear
+// and M homogeneous of degree 1 in f), nu by lam and the Maxwellian's exp(alpha) by lam. lam
+// is formed exactly as k_rescale_apply forms it, from the same per-cell masses. Cells
+// [c_lo, c_lo + gridDim.x).
+__global__ void __launch_bounds__(256) k_rescale_fixup(AuxArgs a, const double* mass, int c_lo, double* Q, double* P,
+                                                       double* nu, double* theta) {
+  __shared__ double lam_s;
+  int c = c_lo + blockIdx.x;
+  int q = a.cell_inst[c];
+  const InstDev& I = a.inst[q];
+  if (!(I.total_mass > 0.0) || (a.active && !a.active[q])) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int j = 0; j < I.J; j++) s += mass[I.cell0 + j];
+    lam_s = I.total_mass / (I.dx * I.dy * s);
+  }
+  __syncthreads();
+  const double lam = lam_s, lam2 = lam * lam;
+  const int K = a.N * a.N * a.N;
+  const long long off = a.cell_off[c];
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < K; e += gridDim.y * blockDim.x) {
+    if (Q) Q[off + e] *= lam2;
+    if (P) P[off + e] *= lam2;
+  }
+  if (blockIdx.y == 0 && threadIdx.x == 0) {
+    nu[c] *= lam;
+    theta[5 * (long long)c] += log(lam);
+  }
+}
+
+cudaError_t launch_rescale_fixup(const AuxArgs& a, int c_lo, int c_hi, double* Q, double* P, double* nu,
+                                 double* theta, cudaStream_t st) {
+  if (c_hi <= c_lo) return cudaSuccess;
+  const double* mass = a.scratch + 2 * a.n_inst + a.C;  // written by launch_rescale
+  k_rescale_fixup<<<dim3(c_hi - c_lo, 4), 256, 0, st>>>(a, mass, c_lo, Q, P, nu, theta);
+  return cudaGetLastError();
+}
+
 // Defect-correction right-hand side b = (Q_hi - Q_lo) / eps, in place over Q_lo.
 __global__ void __launch_bounds__(256) k_dc_rhs(AuxArgs a, const double* __restrict__ Qhi, double* Qlo_b) {
   int c = blockIdx.x;

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(128) k_sum(SumArgs<T> a) {
     return;
   }
   if (active) {
-    CT* out = a.partial + ((long long)blockIdx.x * a.G + (g0 + warp)) * n * kLanes;
+    CT* out = a.partial + ((long long)blockIdx.x * a.Gs + (g0 + warp)) * n * kLanes;
 #pragma unroll
     for (int i = 0; i < n; i++) out[i * kLanes + lane] = make_cplx(accr[i], acci[i]);
   }
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(KW * 32, 2) k_sum_df(SumDfArgs a) {
     }
     return;
   }
-  double2* out = a.partial + ((long long)blockIdx.x * a.G + g) * n * kLanes;
+  double2* out = a.partial + ((long long)blockIdx.x * a.Gs + g) * n * kLanes;
 #pragma unroll
   for (int j = 0; j < NJ; j++) {
     const int k3 = -H + warp + KW * j;
@@ -573,14 +573,14 @@ __global__ void k_sum_reduce(RedArgs<T> a) {
     double sr = 0.0, si = 0.0;
     for (int q = u0; q < u1; q++) {
       int u = a.row_units[q];
-      CT v = a.partial[((long long)u * a.G + g) * n * kLanes + t];
+      CT v = a.partial[((long long)u * a.Gs + g) * n * kLanes + t];
       sr += (double)v.x;
       si += (double)v.y;
     }
     if (a.partial2)
       for (int q = u0; q < u1; q++) {
         int u = a.row_units[q];
-        CT v = a.partial2[((long long)u * a.G + g) * n * kLanes + t];
+        CT v = a.partial2[((long long)u * a.Gs + g) * n * kLanes + t];
         sr += (double)v.x;
         si += (double)v.y;
       }

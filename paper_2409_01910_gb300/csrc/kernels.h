@@ -63,8 +63,9 @@ struct SumArgs {
   const T* W;                   // [steps][PW]
   const CT* ahat;
   const CT* bhat;
-  CT* partial;                  // [units][G][n][32]
-  int G;
+  CT* partial;                  // [units][Gs][n][32]
+  int G;                        // groups of this launch (ahat, bhat, partial start at its first group)
+  int Gs;                       // group stride of partial (the handle's group count)
   Counters* cnt;
   long long spin_max;
 };
@@ -87,7 +88,8 @@ struct RedArgs {
   const CT* partial;
   const CT* partial2;     // optional second set of partials, summed after the first
   CT* qhat;
-  int n, G, n_rows;
+  int n, G, n_rows;  // G: groups of this launch
+  int Gs;            // group stride of partial and partial2
 };
 
 // Double-float spectral sum: weights as (FP32 table, FP32 remainder table) in the packed
@@ -99,8 +101,9 @@ struct SumDfArgs {
   const float* Wlo;   // [steps][PW32]
   const float4* ahat;
   const float4* bhat;
-  double2* partial;   // [units][G][n][32]
-  int G;
+  double2* partial;   // [units][Gs][n][32]
+  int G;              // groups of this launch (ahat, bhat, partial start at its first group)
+  int Gs;             // group stride of partial
   Counters* cnt;
   long long spin_max;
 };
@@ -135,6 +138,8 @@ struct SweepArgs {
   int dir;                // +1 forward, -1 backward
   const int* active;      // per instance: 0 = converged, its scans are skipped
   const double* theta;    // per global cell: Maxwellian exponents of the last collision step
+  int s0, s1;             // 1-D: the launch visits scan positions [s0, min(s1, J)) (cells in scan
+                          // order; a whole scan is [0, J)), so that a scan can run in segments
 };
 
 struct AuxArgs {
@@ -149,6 +154,11 @@ struct AuxArgs {
   int nx, ny;
   double* sflux;          // second-order scheme: [2 n_inst] slope fluxes of the walls; null at first order
 };
+
+// Host side (sgs_api.cu): validation of one problem description (SGS_OK, SGS_ERR_ARG or
+// SGS_ERR_UNSUPPORTED, as sgs_setup returns them) and its device description.
+int check_problem(const sgs_problem& p);
+void fill_inst(const sgs_problem& p, int N, double dv, InstDev& I);
 
 // cudaFuncSetAttribute through a per-device cache: the call is made once per (kernel,
 // attribute, value) and device, so launches stay free of it (also during stream capture).
@@ -204,8 +214,15 @@ cudaError_t sweep_max_clusters(const SweepShape& sh, int arith, int* n);
 cudaError_t launch_sweep2d(const SweepArgs& a, const SweepShape& sh, int arith, int ordering, int wf, int ncells,
                            cudaStream_t st);
 cudaError_t launch_sweep(const SweepArgs& a, const SweepShape& sh, int arith, cudaStream_t st);
+// Latency probe of the scan's building blocks in one cluster of the given shape: mode 0
+// cluster reductions, mode 1 Newton iterations of the discrete Maxwellian (reps of each).
+cudaError_t probe_scan(int N, double dv, int arith, int cluster, int threads, int mode, int reps, cudaStream_t st);
 
 cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st);
+// After launch_rescale: Q, P (nullable) *= lam^2, nu *= lam, alpha += ln lam for the cells
+// [c_lo, c_hi) whose collision step was evaluated on the state before the rescale.
+cudaError_t launch_rescale_fixup(const AuxArgs& a, int c_lo, int c_hi, double* Q, double* P, double* nu,
+                                 double* theta, cudaStream_t st);
 cudaError_t launch_dc_rhs(const AuxArgs& a, const double* Qhi, double* Qlo_b, cudaStream_t st);
 cudaError_t launch_residual(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
                             cudaStream_t st);

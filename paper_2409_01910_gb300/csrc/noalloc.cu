@@ -12,12 +12,11 @@
 // share it, so calls whose kernels overlap on the GPU (different streams, or different host
 // threads without ordering) race on it; order such calls on one stream. Every slot a call
 // reads is written earlier in the same call, so no clearing between calls is needed.
-#include <cmath>
 #include <cstdio>
-#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
+#include "kernels.h"
 
 namespace sgs {
 namespace {
@@ -112,41 +111,6 @@ __global__ void k_na_residual_final(int J, double dx, const double* scratch, dou
   res[0] = sqrt(dx * s);
 }
 
-// Instance description for the residual: cell size, Knudsen number and the boundary data.
-bool fill_residual_inst(const sgs_problem& p, InstDev& I) {
-  int N = p.nv;
-  if (p.space_dim != 1 || p.nx < 1 || !(p.x_hi > p.x_lo) || N < 8 || N > kMaxN || N % 4 || !(p.v_max > 0.0) ||
-      !(p.eps > 0.0))
-    return false;
-  memset(&I, 0, sizeof(I));
-  double dv = 2.0 * p.v_max / N, w = dv * dv * dv;
-  I.J = p.nx;
-  I.dx = (p.x_hi - p.x_lo) / p.nx;
-  I.eps = p.eps;
-  for (int s = 0; s < 2; s++) {
-    const sgs_bc& b = p.bc[s];
-    if (!(b.T > 0.0) || (b.kind != SGS_DIFFUSE && b.kind != SGS_INFLOW)) return false;
-    I.bc_kind[s] = b.kind;
-    I.bc_rho[s] = b.rho;
-    double norm = 1.0 / (2.0 * kPi * b.T * std::sqrt(2.0 * kPi * b.T));
-    for (int d = 0; d < 3; d++)
-      for (int i = 0; i < N; i++) {
-        double v = node(i, N, dv);
-        double x = std::exp(-(v - b.u[d]) * (v - b.u[d]) / (2.0 * b.T));
-        if (d == 0) x = (s == 0 ? v > 0.0 : v < 0.0) ? norm * x : 0.0;
-        I.wall[s][d][i] = x;
-      }
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int i = 0; i < N; i++) {
-      s1 += node(i, N, dv) * I.wall[s][0][i];
-      s2 += I.wall[s][1][i];
-      s3 += I.wall[s][2][i];
-    }
-    I.wall_denom[s] = w * s1 * s2 * s3;
-  }
-  return true;
-}
-
 }  // namespace
 }  // namespace sgs
 
@@ -154,14 +118,20 @@ extern "C" int sgs_residual_noalloc(const sgs_problem* p, const double* f, const
                                     double* res, void* stream) {
   using namespace sgs;
   if (!p || !f || !Q || !res) return SGS_ERR_ARG;
+  // the same problems sgs_setup accepts, restricted to what this entry point computes
+  int chk = check_problem(*p);
+  if (chk != SGS_OK) return chk;
+  if (p->space_dim != 1) return SGS_ERR_ARG;      // one 1-D instance
   if (p->order == 2) return SGS_ERR_UNSUPPORTED;  // the first-order residual only
   if (p->nx > kNoAllocMaxCells) {
     fprintf(stderr, "sgs_residual_noalloc: %d cells exceed the static scratch capacity of %d cells\n", p->nx,
             kNoAllocMaxCells);
     return SGS_ERR_ARG;
   }
+  const int N = p->nv;
+  const double dv = 2.0 * p->v_max / N;
   InstDev I;
-  if (!fill_residual_inst(*p, I)) return SGS_ERR_ARG;
+  fill_inst(*p, N, dv, I);  // wall Maxwellians and their zero-flux normalisation, as sgs_setup
   double* scratch = nullptr;
   cudaError_t e = scratch_for_current_device(&scratch);
   if (e != cudaSuccess) {
@@ -169,8 +139,6 @@ extern "C" int sgs_residual_noalloc(const sgs_problem* p, const double* f, const
     return SGS_ERR_CUDA;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  int N = p->nv;
-  double dv = 2.0 * p->v_max / N;
   k_na_wall_flux<<<2, 256, 0, st>>>(I, f, N, dv, scratch);
   k_na_residual_cells<<<p->nx, 256, 0, st>>>(I, f, Q, rhs, N, dv, scratch);
   k_na_residual_final<<<1, 32, 0, st>>>(p->nx, I.dx, scratch, res);

@@ -2,6 +2,7 @@
 // Fourier-weight tables, work planning of the spectral sum, workspace layout and the
 // enqueueing of kernels on the caller's stream.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -133,6 +134,11 @@ struct sgs_handle {
   std::vector<cudaEvent_t> pool;
   unsigned long long launches = 0;
   long long spin_max = 1LL << 26;
+  // pipelined iterations: the scans run on a high-priority stream of the handle while the
+  // collision steps of the groups the scan has left run on the caller's stream
+  bool overlap = true;
+  cudaStream_t scan_st = nullptr;
+  std::vector<cudaEvent_t> ov_ev;
 
   template <typename T>
   T* at(size_t o) const {
@@ -355,7 +361,10 @@ void layout(sgs_handle* h) {
   h->ws_bytes = o;
 }
 
-int check_problem(const sgs_problem& p) {
+}  // namespace
+
+// Problem validation shared by every entry point that takes a problem description.
+int sgs::check_problem(const sgs_problem& p) {
   if (p.space_dim != 1 && p.space_dim != 2) return SGS_ERR_ARG;
   if (p.nx < 1 || !(p.x_hi > p.x_lo)) return SGS_ERR_ARG;
   if (p.space_dim == 2) {
@@ -385,7 +394,9 @@ int check_problem(const sgs_problem& p) {
   return SGS_OK;
 }
 
-void fill_inst(const sgs_problem& p, int N, double dv, InstDev& I) {
+// Device description of one instance: cell sizes, solver controls and the unit wall
+// Maxwellians with their discrete zero-mass-flux normalisation.
+void sgs::fill_inst(const sgs_problem& p, int N, double dv, InstDev& I) {
   memset(&I, 0, sizeof(I));
   const bool two_d = p.space_dim == 2;
   I.space_dim = two_d ? 2 : 1;
@@ -430,6 +441,8 @@ void fill_inst(const sgs_problem& p, int N, double dv, InstDev& I) {
     I.wall_denom[s] = w * sd[0] * sd[1] * sd[2];
   }
 }
+
+namespace {
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -504,42 +517,54 @@ CellTables cell_tables(const sgs_handle* h, int l = 0) {
   return ct;
 }
 
+// Collision context of level l restricted to the lane groups [g_lo, g_hi) (g_hi < 0: all):
+// every per-cell and per-group pointer starts at the range's first cell and group, so the
+// kernels index cells and groups relative to the range; the partial sums keep the level's
+// group stride.
 template <typename T>
-CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0) {
+CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0, int g_lo = 0, int g_hi = -1) {
   typedef typename CplxOf<T>::type CT;
+  const int Gl = h->lev[l].G, Cl = h->lev[l].C;
+  if (g_hi < 0) g_hi = Gl;
+  const int c0 = g_lo * kLanes, c1 = std::min(g_hi * kLanes, Cl);
+  const int N = h->N, n = h->n;
+  const size_t gsz = (size_t)n * n * n * kLanes;
   CollideCtx<T> x;
-  x.N = h->N;
-  x.C = h->lev[l].C;
+  x.N = N;
+  x.C = c1 - c0;
   x.H = h->H;
-  x.NW = h->NW;
+  x.NW = std::min(h->NW, g_hi - g_lo);
   x.n_units = (int)h->units.size();
   x.dv = h->dv;
   x.ct = cell_tables(h, l);
-  x.theta = h->at<double>(h->off.theta);
-  x.nu = h->at<double>(h->off.nu);
+  x.ct.cell_off += c0;
+  x.ct.cell_inst += c0;
+  x.theta = h->at<double>(h->off.theta) + 5 * (size_t)c0;
+  x.nu = h->at<double>(h->off.nu) + c0;
   x.sb.tw_cos = h->at<double>(h->off.tw_cos);
   x.sb.tw_sin = h->at<double>(h->off.tw_sin);
   x.sb.twc = sizeof(T) == 8 ? h->at<T>(h->off.tw_cos) : h->at<T>(h->off.tw_cos32);
   x.sb.tws = sizeof(T) == 8 ? h->at<T>(h->off.tw_sin) : h->at<T>(h->off.tw_sin32);
-  x.efac = h->at<double>(h->off.efac);
-  x.efac_ref = h->at<double>(h->off.efac_ref);
-  x.mom = h->cproj ? h->at<double>(h->off.mom) : nullptr;
+  x.efac = h->at<double>(h->off.efac) + (size_t)3 * kMaxN * c0;
+  x.efac_ref = h->at<double>(h->off.efac_ref) + (size_t)3 * kMaxN * c0;
+  x.mom = h->cproj ? h->at<double>(h->off.mom) + (size_t)5 * N * c0 : nullptr;
   x.cproj = h->cproj == 1 ? h->at<double>(h->off.cproj_A) : nullptr;
   x.cproj_mode = h->cproj;
-  x.sb.st1a = h->at<CT>(h->off.st1a);
-  x.sb.st1b = h->at<CT>(h->off.st1b);
-  x.sb.st2a = h->at<CT>(h->off.st2a);
-  x.sb.st2b = h->at<CT>(h->off.st2b);
-  x.sb.ahat = h->at<CT>(h->off.ahat);
-  x.sb.bhat = h->at<CT>(h->off.bhat);
-  x.sb.qhat = h->at<CT>(h->off.qhat);
+  x.sb.st1a = h->at<CT>(h->off.st1a) + (size_t)c0 * N * N * n;
+  x.sb.st1b = h->at<CT>(h->off.st1b) + (size_t)c0 * N * N * n;
+  x.sb.st2a = h->at<CT>(h->off.st2a) + (size_t)c0 * N * n * n;
+  x.sb.st2b = h->at<CT>(h->off.st2b) + (size_t)c0 * N * n * n;
+  x.sb.ahat = h->at<CT>(h->off.ahat) + g_lo * gsz;
+  x.sb.bhat = h->at<CT>(h->off.bhat) + g_lo * gsz;
+  x.sb.qhat = h->at<CT>(h->off.qhat) + g_lo * gsz;
   x.sum.units = h->at<int4>(h->off.units);
   x.sum.unit_step0 = h->at<long long>(h->off.step0);
   x.sum.W = sizeof(T) == 8 ? h->at<T>(h->off.W64) : h->at<T>(h->off.W32);
   x.sum.ahat = x.sb.ahat;
   x.sum.bhat = x.sb.bhat;
-  x.sum.partial = h->at<CT>(h->off.partial);
-  x.sum.G = h->lev[l].G;
+  x.sum.partial = h->at<CT>(h->off.partial) + (size_t)g_lo * n * kLanes;
+  x.sum.G = g_hi - g_lo;
+  x.sum.Gs = Gl;
   x.sum.cnt = h->at<Counters>(h->off.cnt);
   x.sum.spin_max = h->spin_max;
   x.red.row_k = h->at<int2>(h->off.row_k);
@@ -548,7 +573,8 @@ CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0) {
   x.red.partial = x.sum.partial;
   x.red.qhat = x.sb.qhat;
   x.red.n = h->n;
-  x.red.G = h->lev[l].G;
+  x.red.G = g_hi - g_lo;
+  x.red.Gs = Gl;
   x.red.n_rows = (int)h->row_k.size();
   return x;
 }
@@ -556,12 +582,19 @@ CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0) {
 // Qraw (non-null only with the conservation projection): receives the unprojected operator,
 // the reference of the increment form. The projection of mode 2 depends on f through M, so
 // the increment form adds increments to the unprojected reference and projects the sum.
+//
+// [g_lo, g_hi): the lane groups (32 consecutive cells each) to evaluate; g_hi < 0 means every
+// group of the level. Cells outside the range are neither read nor written.
 int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int precision, cudaStream_t st, int l = 0,
-                 double* Qraw = nullptr) {
+                 double* Qraw = nullptr, int g_lo = 0, int g_hi = -1) {
+  if (g_hi < 0) g_hi = h->lev[l].G;
+  const int c0 = g_lo * kLanes;
   CellTables ct = cell_tables(h, l);
-  const int C = h->lev[l].C;
-  double* theta = h->at<double>(h->off.theta);
-  double* nu = h->at<double>(h->off.nu);
+  ct.cell_off += c0;
+  ct.cell_inst += c0;
+  const int C = std::min(g_hi * kLanes, h->lev[l].C) - c0;
+  double* theta = h->at<double>(h->off.theta) + 5 * (size_t)c0;
+  double* nu = h->at<double>(h->off.nu) + c0;
   const sgs_problem& p0 = h->prob[0];
   cudaError_t e;
   {
@@ -595,9 +628,9 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
   auto run_inc = [&](CollideCtx<float> x) -> int {
     typedef float2 CT;
     const auto& Lv = h->lev[l];
-    DftMode m1{1, h->at<double>(Lv.rf), h->at<double>(Lv.rth)};
+    DftMode m1{1, h->at<double>(Lv.rf), h->at<double>(Lv.rth) + 5 * (size_t)c0};
     DftMode m2{2, m1.f_ref, m1.theta_ref};
-    CT* part2 = h->at<CT>(h->off.partial2);
+    CT* part2 = h->at<CT>(h->off.partial2) + (size_t)g_lo * h->n * kLanes;
     cudaError_t er;
     {
       Scope sc(h, SGS_PROF_DFT, st, 5);
@@ -613,8 +646,9 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
       Scope sc(h, SGS_PROF_DFT, st, 5);
       er = launch_dft(f, x, m2, st);
       if (er == cudaSuccess)
-        er = cudaMemcpyAsync(x.sb.ahat, h->at<CT>(Lv.rah),
-                             (size_t)Lv.G * h->n * h->n * h->n * kLanes * sizeof(CT), cudaMemcpyDeviceToDevice, st);
+        er = cudaMemcpyAsync(x.sb.ahat, h->at<CT>(Lv.rah) + (size_t)g_lo * h->n * h->n * h->n * kLanes,
+                             (size_t)(g_hi - g_lo) * h->n * h->n * h->n * kLanes * sizeof(CT),
+                             cudaMemcpyDeviceToDevice, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
     {
@@ -627,12 +661,12 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
   };
   if (precision == SGS_DF64) {
     if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
-    CollideCtx<double> x = collide_ctx<double>(h, l);
+    CollideCtx<double> x = collide_ctx<double>(h, l, g_lo, g_hi);
     cudaError_t er;
     {
       Scope sc(h, SGS_PROF_DFT, st, 6);
       er = launch_dft(f, x, DftMode{0, nullptr, nullptr}, st);
-      const long long cnt = (long long)h->lev[l].G * h->n * h->n * h->n * kLanes;
+      const long long cnt = (long long)(g_hi - g_lo) * h->n * h->n * h->n * kLanes;
       if (er == cudaSuccess) er = launch_split_spec(x.sb.ahat, cnt, st);
       if (er == cudaSuccess) er = launch_split_spec(x.sb.bhat, cnt, st);
     }
@@ -648,6 +682,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
       d.bhat = reinterpret_cast<const float4*>(x.sb.bhat);
       d.partial = x.sum.partial;
       d.G = x.sum.G;
+      d.Gs = x.sum.Gs;
       d.cnt = x.sum.cnt;
       d.spin_max = x.sum.spin_max;
       er = launch_sum_df(d, h->H, x.n_units, st);
@@ -658,17 +693,21 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
   }
   if (precision == SGS_FP32) {
     if (h->precision != SGS_FP32) return SGS_ERR_ARG;  // FP32 tables not built
-    if (l == 0 ? h->dc_ref : h->lev[l].ref) return run_inc(collide_ctx<float>(h, l));
-    return run(collide_ctx<float>(h, l));
+    if (l == 0 ? h->dc_ref : h->lev[l].ref) return run_inc(collide_ctx<float>(h, l, g_lo, g_hi));
+    return run(collide_ctx<float>(h, l, g_lo, g_hi));
   }
-  return run(collide_ctx<double>(h, l));
+  return run(collide_ctx<double>(h, l, g_lo, g_hi));
 }
 
 // One scan: in 1-D dir +1 / -1 walks the cells forward / backward (ordering 0 / 1); in 2-D
 // the ordering o in 0..3 is launched wavefront by wavefront.
+// In 1-D, [s0, s1) limits the launch to those scan positions (a segment of the scan; first
+// order only: the second-order slope terms are formed once per scan).
 int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int dir, cudaStream_t st, int l = 0,
-               int ordering = -1) {
+               int ordering = -1, int s0 = 0, int s1 = 1 << 30) {
   SweepArgs a;
+  a.s0 = s0;
+  a.s1 = s1;
   a.inst = h->at<InstDev>(h->lev[l].inst);
   a.n_inst = h->n_inst;
   a.f = f;
@@ -722,8 +761,77 @@ int residual_field_impl(sgs_handle* h, const double* f, const double* Q, const d
   return cuda_status(launch_residual_field(aux_args(h, l), f, Q, rhs, R, st));
 }
 
+// Whether an SGS iteration of level l can pipeline its collision steps behind the scans: one
+// 1-D instance of at least two lane groups, first order, spectral collisions, on the finest
+// level, with the handle's scan stream available.
+bool overlap_ok(const sgs_handle* h, int l) {
+  return h->overlap && l == 0 && !h->two_d && h->n_inst == 1 && h->spectral && !h->order2 && h->lev[0].G >= 2 &&
+         h->scan_st != nullptr && (int)h->ov_ev.size() >= 3 * h->lev[0].G + 2;
+}
+
+// One SGS iteration (eq. (29)) whose collision steps overlap the scans. The scans run on the
+// handle's high-priority stream in segments of one lane group (32 cells), the collision
+// steps on the caller's stream st, ordered by events (a fork/join pattern, also under stream
+// capture):
+//   - forward scan, group by group; the collision step of group g (the P^(n+1/2) the
+//     backward scan needs) starts as soon as the forward scan has left group g;
+//   - backward scan, groups G-1 .. 0, each segment after its group's collision step;
+//   - with SGS_IT_EVAL, the collision step of the new iterate for group g >= 1 starts as
+//     soon as the backward scan has left group g, and group 0 follows the mass rescale
+//     (eq. (32)); the earlier groups' Q, P, nu and theta are carried over to the rescaled
+//     state, whose operator they equal up to rounding (Q, P homogeneous of degree 2 in f).
+// Each cell sees the same inputs as in iterate_impl's sequence of whole-grid steps.
+int iterate_overlap(sgs_handle* h, double* f, double* Q, double* P, const double* rhs, int flags, double* res,
+                    cudaStream_t st) {
+  const int G = h->lev[0].G, J = h->inst[0].J, prec = h->precision;
+  const bool eval = (flags & SGS_IT_EVAL) != 0;
+  if (eval && !Q) return SGS_ERR_ARG;
+  cudaStream_t ss = h->scan_st;
+  int k = 0, r;
+  cudaError_t e = cudaSuccess;
+  auto fork = [&](cudaStream_t from, cudaStream_t to) -> cudaEvent_t {
+    cudaEvent_t x = h->ov_ev[k++];
+    if (e == cudaSuccess) e = cudaEventRecord(x, from);
+    if (e == cudaSuccess && to) e = cudaStreamWaitEvent(to, x, 0);
+    return x;
+  };
+  if (!(flags & SGS_IT_P_VALID) && (r = collide_impl(h, f, nullptr, P, prec, st))) return r;
+  fork(st, ss);
+  for (int g = 0; g < G && e == cudaSuccess; g++) {
+    if ((r = sweep_impl(h, f, P, rhs, +1, ss, 0, -1, g * kLanes, std::min((g + 1) * kLanes, J)))) return r;
+    fork(ss, st);
+    if ((r = collide_impl(h, f, nullptr, P, prec, st, 0, nullptr, g, g + 1))) return r;
+  }
+  std::vector<cudaEvent_t> col(G);
+  for (int g = G - 1; g >= 0 && e == cudaSuccess; g--) {
+    // the collision steps of groups < G-1 were enqueued earlier on st; one event covers them
+    if (g == G - 1) fork(st, ss);
+    const int c_lo = g * kLanes, c_hi = std::min((g + 1) * kLanes, J);
+    if ((r = sweep_impl(h, f, P, rhs, -1, ss, 0, -1, J - c_hi, J - c_lo))) return r;
+    if (g > 0 && eval) {
+      fork(ss, st);
+      if ((r = collide_impl(h, f, Q, P, prec, st, 0, nullptr, g, g + 1))) return r;
+    }
+  }
+  fork(ss, st);  // join: every scan segment precedes what follows on st
+  if (e != cudaSuccess) return cuda_status(e);
+  if ((r = rescale_impl(h, f, st))) return r;
+  if (eval) {
+    {
+      Scope sc(h, SGS_PROF_RESCALE, st, 1);
+      e = launch_rescale_fixup(aux_args(h), kLanes, h->C, Q, P, h->at<double>(h->off.nu),
+                               h->at<double>(h->off.theta), st);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    if ((r = collide_impl(h, f, Q, P, prec, st, 0, nullptr, 0, 1))) return r;
+    if (res && (r = residual_impl(h, f, Q, rhs, res, st))) return r;
+  }
+  return SGS_OK;
+}
+
 int iterate_impl(sgs_handle* h, double* f, double* Q, double* P, const double* rhs, int flags, double* res,
                  cudaStream_t st, int l = 0) {
+  if (overlap_ok(h, l)) return iterate_overlap(h, f, Q, P, rhs, flags, res, st);
   int r;
   if (!(flags & SGS_IT_P_VALID)) {
     r = collide_impl(h, f, nullptr, P, h->precision, st, l);
@@ -1040,6 +1148,17 @@ int sgs_bind_workspace(sgs_handle* h, void* device_ptr, size_t bytes) {
                                   h->at<float>(h->off.W32lo), 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  // the scan stream (highest priority) and the events of pipelined iterations
+  if (e == cudaSuccess && !h->two_d && h->n_inst == 1 && h->spectral && h->lev[0].G >= 2 && !h->scan_st) {
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->scan_st, cudaStreamNonBlocking, greatest);
+    for (int i = 0; e == cudaSuccess && i < 3 * h->lev[0].G + 2; i++) {
+      cudaEvent_t x = nullptr;
+      e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+      if (e == cudaSuccess) h->ov_ev.push_back(x);
+    }
+  }
   return cuda_status(e);
 }
 
@@ -1150,8 +1269,14 @@ int sgs_dc_step(sgs_handle* h, double* f, double* Q, double* P, int lo_iters, do
   if (e != cudaSuccess) return cuda_status(e);
   h->dc_ref = true;
   // P from the FP64 collision is P of f_k in the increment form as well (zero increments)
-  for (int it = 0; it < lo_iters; it++)
-    if ((r = iterate_impl(h, f, Q, P, nullptr, it == 0 ? SGS_IT_P_VALID : 0, nullptr, st))) return r;
+  // Pipelined iterations also evaluate the collision step of the iterate they produce (its
+  // P is the next iteration's), so every collision step overlaps a scan; otherwise the next
+  // iteration evaluates it first.
+  const bool ov = overlap_ok(h, 0);
+  for (int it = 0; it < lo_iters; it++) {
+    int fl = ov ? SGS_IT_P_VALID | SGS_IT_EVAL : (it == 0 ? SGS_IT_P_VALID : 0);
+    if ((r = iterate_impl(h, f, Q, P, nullptr, fl, nullptr, st))) return r;
+  }
   return SGS_OK;
 }
 
@@ -1175,6 +1300,14 @@ int sgs_vcycle(sgs_handle* h, double* f, int levels, int pre, int post, int coar
 }
 
 int sgs_max_levels(const sgs_handle* h) { return h ? (int)h->lev.size() : 0; }
+
+int sgs_set_overlap(sgs_handle* h, int enable) {
+  if (!h) return SGS_ERR_ARG;
+  h->overlap = enable != 0;
+  return SGS_OK;
+}
+
+int sgs_get_overlap(const sgs_handle* h) { return h && h->ws ? (overlap_ok(h, 0) ? 1 : 0) : 0; }
 
 int sgs_update_active(sgs_handle* h, const double* res, double tol, void* stream) {
   if (!h || !res || !(tol >= 0.0)) return SGS_ERR_ARG;
@@ -1276,6 +1409,41 @@ int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning
   return SGS_OK;
 }
 
+int sgs_probe_scan(int nv, double v_max, int precision, int cluster, int threads, int mode, int reps,
+                   float* us_per_op, void* stream) {
+  if (!valid_nv(nv) || !(v_max > 0.0) || (mode != 0 && mode != 1) || reps < 1 || !us_per_op) return SGS_ERR_ARG;
+  if (precision != SGS_FP64 && precision != SGS_FP32) return SGS_ERR_ARG;
+  const int arith = precision == SGS_FP32 ? kSweepDF64 : kSweepF64;  // the scan arithmetic of such a handle
+  const double dv = 2.0 * v_max / nv;
+  cudaStream_t st = as_stream(stream);
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; i++)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+      for (int k = 0; k < i; k++) cudaEventDestroy(ev[k]);
+      return SGS_ERR_CUDA;
+    }
+  // warm-up, then an empty launch (launch and set-up cost) and the timed one
+  cudaError_t e = probe_scan(nv, dv, arith, cluster, threads, mode, 1, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = probe_scan(nv, dv, arith, cluster, threads, mode, 0, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+  if (e == cudaSuccess) e = probe_scan(nv, dv, arith, cluster, threads, mode, reps, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+  float t0 = 0.f, t1 = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[2], ev[3]);
+  for (int i = 0; i < 4; i++) cudaEventDestroy(ev[i]);
+  if (e == cudaErrorInvalidConfiguration) {
+    cudaGetLastError();
+    return SGS_ERR_ARG;
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  *us_per_op = (t1 - t0) * 1e3f / reps;
+  return SGS_OK;
+}
+
 int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream) {
   if (!h || !out) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;
@@ -1339,6 +1507,8 @@ void sgs_destroy(sgs_handle* h) {
     h->pool.push_back(rec.b);
   }
   for (auto e : h->pool) cudaEventDestroy(e);
+  for (auto e : h->ov_ev) cudaEventDestroy(e);
+  if (h->scan_st) cudaStreamDestroy(h->scan_st);
   delete h;
 }
 

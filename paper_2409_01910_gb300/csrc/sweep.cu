@@ -427,6 +427,10 @@ __device__ __noinline__ int solve_mg(SweepSmem<E>& sm, int N, E w, const E* mom,
   if (it < 0) {
     status |= SGS_ST_NEWTON_FAIL;
     if (th0 && tid < 5) sm.thg[tid] = keep[tid];
+    // no warm start and no admissible guess (non-positive moments): a fixed theta (the unit
+    // Maxwellian's), so that every CTA of the cluster continues from the same data and takes
+    // the same decisions
+    if (!th0 && !sm.ctl && tid < 5) sm.thg[tid] = tid == 0 ? -1.5 * log(2.0 * kPi) : (tid == 4 ? 0.5 : 0.0);
     __syncthreads();
     if (tid < 5) sm.thE[tid] = cvt<E>(sm.thg[tid]);
     __syncthreads();
@@ -565,7 +569,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   unsigned int status = 0;
   bool have_th = false;
 
-  for (int s = 0; s < J; s++) {
+  const int s_end = min(a.s1, J);
+  for (int s = a.s0; s < s_end; s++) {
     const int j = a.dir > 0 ? s : J - 1 - s;
     const long long cbase = I.f_off + (long long)j * K + e0;
     double* fj = a.f + cbase;
@@ -797,7 +802,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
 
   if (rank == 0 && tid == 0) {
     Counters* c = a.cnt + q;
-    atomicAdd(&c->visits, (unsigned long long)J);
+    atomicAdd(&c->visits, (unsigned long long)max(0, s_end - a.s0));
     atomicAdd(&c->inner_iters, c_inner);
     atomicAdd(&c->newton_iters, c_newton);
     atomicAdd(&c->newton_solves, c_solves);
@@ -1132,6 +1137,100 @@ SweepShape sweep_shape(int N, int arith) {
   s.tpb = ((threads + s.cluster - 1) / s.cluster + 31) / 32 * 32;
   if (s.tpb < 160) s.tpb = 160;
   return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// Latency probe of the scan's two serial building blocks in one cluster of a given launch
+// shape: mode 0 runs `reps` cluster reductions of seven values (cluster_reduce, as in every
+// cell visit); mode 1 runs `reps` dependent Newton iterations of the discrete Maxwellian by
+// the evaluating warps (factors and 1-D sums of each velocity dimension, the barrier among
+// those warps, the combination into moments and Jacobian, the 5x5 factorisation and solve).
+// The results feed a runtime test that never passes (the sentinel), so nothing is stored
+// and nothing allocated.
+// ---------------------------------------------------------------------------------------
+__device__ double g_probe_sink;
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_probe_scan(int N, double dv, int mode, int reps, double sentinel) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  __shared__ SweepSmem<E> sm;
+  const int tid = threadIdx.x;
+  if (tid < kMaxN) {
+    double v = tid < N ? node(tid, N, dv) : 0.0;
+    sm.vv[tid] = cvt<E>(v);
+    sm.vq[tid] = cvt<E>(v * v);
+    sm.c1e[tid] = cvt<E>(fabs(v));
+    sm.c2e[tid] = cvt<E>(0.0);
+  }
+  if (tid == 0) sm.wdims = 1;
+  __syncthreads();
+  double acc = 0.0;
+  if (mode == 0) {
+    int buf = 0;
+    for (int r = 0; r < reps; r++) {
+      E v[7];
+#pragma unroll
+      for (int q = 0; q < 7; q++) v[q] = cvt<E>(1e-3 * (double)(tid + q + r));
+      double t[7];
+      cluster_reduce<7, E>(v, t, sm, buf, cl, CS);
+      acc += t[0];
+    }
+  } else {
+    const int wid = tid >> 5;
+    const int nev = 3 + sm.wdims;
+    if (wid < nev) {
+      // unit Maxwellian exponents and its continuum moments as the target
+      E thE[5] = {cvt<E>(-1.5 * log(2.0 * kPi)), cvt<E>(0.0), cvt<E>(0.0), cvt<E>(0.0), cvt<E>(0.5)};
+      const E target[5] = {cvt<E>(1.0), cvt<E>(0.0), cvt<E>(0.0), cvt<E>(0.0), cvt<E>(3.0)};
+      const E w = cvt<E>(dv * dv * dv);
+      int buf = 0;
+      for (int r = 0; r < reps; r++) {
+        eval_warp<E>(sm, N, thE, wid, buf);
+        eval_bar(nev);
+        E F[5];
+        float A[15], fn;
+        combine_rows<E>(sm.Sb[buf], w, 0, target, F, A, fn);
+        buf ^= 1;
+        float y[5], Ff[5];
+#pragma unroll
+        for (int i = 0; i < 5; i++) Ff[i] = tof(F[i]);
+        chol5_solve(A, Ff, y);
+        acc += (double)y[0] + (double)fn;
+        thE[0] = thE[0] + cvt<E>(1e-9 * (double)y[0]);  // the next evaluation depends on this one
+      }
+    }
+    __syncthreads();
+  }
+  if (acc == sentinel) g_probe_sink = acc;
+}
+
+template <typename E>
+static cudaError_t launch_probe_scan(int N, double dv, int cluster, int threads, int mode, int reps,
+                                     cudaStream_t st) {
+  cudaError_t e = func_attr((const void*)k_probe_scan<E>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(threads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_probe_scan<E>, N, dv, mode, reps, -1.0e300);
+}
+
+cudaError_t probe_scan(int N, double dv, int arith, int cluster, int threads, int mode, int reps, cudaStream_t st) {
+  if (cluster < 1 || cluster > 16 || (cluster & (cluster - 1)) || threads < 160 || threads > 256 || threads % 32 ||
+      threads < 32 * ((kRedMax * cluster + 31) / 32) || N < 8 || N > kMaxN || reps < 0)
+    return cudaErrorInvalidConfiguration;
+  if (arith == kSweepDF64) return launch_probe_scan<dfloat>(N, dv, cluster, threads, mode, reps, st);
+  if (arith == kSweepF32) return launch_probe_scan<float>(N, dv, cluster, threads, mode, reps, st);
+  return launch_probe_scan<double>(N, dv, cluster, threads, mode, reps, st);
 }
 
 template <typename E, int EPT>

@@ -176,6 +176,8 @@ def lib(build: bool = True):
             "sgs_launch_count": (C.c_ulonglong, [vp]),
             "sgs_vcycle": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]),
             "sgs_max_levels": (C.c_int, [vp]),
+            "sgs_set_overlap": (C.c_int, [vp, C.c_int]),
+            "sgs_get_overlap": (C.c_int, [vp]),
             "sgs_residual_noalloc": (C.c_int, [C.POINTER(_Problem), vp, vp, vp, vp, vp]),
             "sgs_update_active": (C.c_int, [vp, vp, C.c_double, vp]),
             "sgs_activate_all": (C.c_int, [vp, vp]),
@@ -188,6 +190,10 @@ def lib(build: bool = True):
             "sgs_destroy": (None, [vp]),
             "sgs_strerror": (C.c_char_p, [C.c_int]),
             "sgs_host_weight": (C.c_double, [C.c_int, C.c_double, C.c_int, C.c_double, C.c_longlong, C.c_longlong]),
+            "sgs_peak_fma": (C.c_int, [C.c_int, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_float), vp]),
+            "sgs_probe_scan": (C.c_int, [C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                         C.POINTER(C.c_float), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -208,6 +214,23 @@ def _check(code: int, what: str):
 
 def host_weight(nv, v_max, collision, b0, a2, b2) -> float:
     return lib().sgs_host_weight(nv, v_max, collision, b0, a2, b2)
+
+
+def peak_fma(precision, iters=1 << 16, stream=None) -> dict:
+    """Measured FMA throughput of the current device's CUDA cores (FP32 or FP64)."""
+    t, n, ms = C.c_double(), C.c_int(), C.c_float()
+    _check(lib().sgs_peak_fma(precision, iters, C.byref(t), C.byref(n), C.byref(ms), _stream(stream)),
+           "sgs_peak_fma")
+    return {"tflops": float(t.value), "sms": int(n.value), "ms": float(ms.value)}
+
+
+def probe_scan(nv, v_max, precision, cluster, threads, mode, reps=2000, stream=None) -> float:
+    """Microseconds per cluster reduction (mode 0) or per Newton iteration (mode 1) of the
+    persistent scan in one cluster of the given shape."""
+    us = C.c_float()
+    _check(lib().sgs_probe_scan(nv, v_max, precision, cluster, threads, mode, reps, C.byref(us), _stream(stream)),
+           "sgs_probe_scan")
+    return float(us.value)
 
 
 def _ptr(t) -> Optional[int]:
@@ -319,6 +342,13 @@ class Solver:
 
     def max_levels(self) -> int:
         return int(lib().sgs_max_levels(self.h))
+
+    def set_overlap(self, enable: bool):
+        """Pipelined iterations (collision steps behind the scans) on or off."""
+        _check(lib().sgs_set_overlap(self.h, 1 if enable else 0), "sgs_set_overlap")
+
+    def overlap(self) -> bool:
+        return bool(lib().sgs_get_overlap(self.h))
 
     def update_active(self, res, tol, stream=None):
         _check(lib().sgs_update_active(self.h, _ptr(res), tol, _stream(stream)), "sgs_update_active")

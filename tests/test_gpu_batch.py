@@ -157,3 +157,54 @@ def test_autotuned_shape_keeps_oracle_parity(oracle):
         s.sweep_forward(f, torch.from_numpy(Po.reshape(-1)).cuda())
         assert rel(f.cpu().numpy().reshape(f0.shape), fo) <= 1e-12, shape
     assert s.read_status()["status"] == 0
+
+
+def uneven_pairs(oracle, precision, inner_fixed):
+    """Four instances of one handle with different cell counts, domains, Knudsen numbers and
+    sides (diffuse walls at different temperatures, inflow Maxwellians), and the oracle's
+    description of each."""
+    specs = [dict(nx=4, eps=0.05, bc_T=(1.0, 1.6), total_mass=1.0),
+             dict(nx=6, x_hi=2.0, eps=0.3, bc_T=(0.9, 2.2), total_mass=2.0),
+             dict(nx=5, x_lo=-1.0, x_hi=1.0, eps=1.0, bc_kind=(sgs.INFLOW, sgs.INFLOW), bc_rho=(1.0, 0.8),
+                  bc_u=((0.4, 0.0, 0.0), (-0.2, 0.1, 0.0)), bc_T=(1.0, 1.3), total_mass=0.0),
+             dict(nx=3, eps=0.1, bc_T=(1.2, 1.2), total_mass=1.0)]
+    g, o = [], []
+    for sp in specs:
+        p = sgs.Problem(nv=8, v_max=6.0, precision=precision, inner_fixed=inner_fixed, **sp)
+        g.append(p)
+        o.append(oracle.Problem(N=8, L=6.0, J=p.nx, x_lo=p.x_lo, x_hi=p.x_hi, eps=p.eps, bc_kind=tuple(p.bc_kind),
+                                bc_rho=tuple(p.bc_rho), bc_u=tuple(tuple(u) for u in p.bc_u), bc_T=tuple(p.bc_T),
+                                total_mass=p.total_mass, inner_fixed=inner_fixed))
+    return g, o
+
+
+@pytest.mark.parametrize("precision,tol", [(sgs.FP64, 1e-12), (sgs.FP32, 1e-7)])
+def test_uneven_batch_matches_oracle_per_instance(oracle, precision, tol):
+    """An uneven batch in one handle (one persistent scan launch, one cluster per instance)
+    against the oracle instance by instance after two SGS iterations with a fixed inner
+    count: FP64 at 1e-12; the mixed form (one high-precision evaluation, then two iterations
+    with FP32 sums in increment form and double-float scans) at 1e-7. The fourth instance is
+    marked converged before the iterations and must come back bit for bit unchanged."""
+    ps, os_ = uneven_pairs(oracle, precision, inner_fixed=5)
+    f0 = [I.initial_state(p.nx, p.nv, p.v_max, T=1.3, seed=40 + q) for q, p in enumerate(ps)]
+    s = sgs.Solver(ps)
+    f, Q, P = s.field(), s.field(), s.field()
+    for q in range(len(ps)):
+        s.view(f, q).copy_(torch.from_numpy(f0[q]))
+    s.update_active(torch.tensor([1.0, 1.0, 1.0, 0.0], dtype=torch.float64, device="cuda"), 1e-8)
+    assert s.read_active() == [1, 1, 1, 0]
+    if precision == sgs.FP64:
+        for it in range(2):
+            s.iterate(f, Q, P, flags=sgs.IT_EVAL | (sgs.IT_P_VALID if it else 0))
+    else:
+        s.dc_step(f, Q, P, 2)
+    st = s.read_status()
+    assert st["status"] == 0
+    assert st["visits"] == 2 * 2 * sum(p.nx for p in ps[:3])
+    for q in range(3):
+        fo = f0[q].copy()
+        for _ in range(2):
+            oracle.sgs_iteration(os_[q], fo)
+        err = rel(s.view(f, q).cpu().numpy(), fo)
+        assert err <= tol, (q, err)
+    assert torch.equal(s.view(f, 3).cpu(), torch.from_numpy(f0[3]))

@@ -7,10 +7,11 @@ benchmark times.
   oracle's scans from the same state with the oracle's P, fixed inner count; 1e-11
   (double-float) and 1e-12 (FP64).
 - Converged solutions (heat: defect correction + 2-level V-cycles; lid-driven cavity,
-  64 x 64 cells, 24^3: defect correction + 3-level V-cycles) reach an FP64 residual of
-  1e-8 on the GPU; the oracle then recomputes, one sampled cell at a time, its own
+  64 x 64 cells, 24^3: defect correction + 3-level V-cycles) are driven to an FP64 residual
+  below 1e-9 on the GPU; the oracle then recomputes, one sampled cell at a time, its own
   collision operator and the cell's share of the residual sqrt(dx dy sum_k w R^2) of the
-  GPU's final state, which must stay below the same 1e-8.
+  GPU's final state. A total of 1e-8 spread evenly over the J cells gives each cell
+  1e-8 / sqrt(J); every sampled share must stay below that.
 """
 import numpy as np
 import pytest
@@ -80,6 +81,34 @@ def test_heat_full_size_scan_parity(oracle, heat_initial, precision, shape, tol,
     assert rel(f.cpu().numpy().reshape(f0.shape), fo) <= tol
 
 
+@pytest.mark.parametrize("form", ["plain", "increment"])
+def test_collide_fp32_full_size_sampled(oracle, form):
+    """The FP32 spectral sum at N = 32 (k_sum<float, 15>, the benchmark's kernel) on 64 cells
+    of 32^3, sampled cells against the oracle at 1e-5: the plain form, and the increment form
+    the mixed solver runs between high-precision evaluations (reference f_k set by a
+    defect-correction step, then f = f_k perturbed by 1e-3 relative)."""
+    from test_gpu_parity import varied_state
+
+    N, J, L = 32, 64, 8.0
+    g = sgs.Problem(nx=J, nv=N, v_max=L, eps=0.01, precision=sgs.FP32)
+    o = oracle.Problem(N=N, L=L, J=J, eps=0.01)
+    fk = varied_state(J, N, L, seed=5)
+    s = sgs.Solver(g)
+    Q, P = s.field(), s.field()
+    f = fk
+    if form == "increment":
+        s.dc_step(dev(fk), Q, P, 0)  # reference: f_k, its high-precision Q and spectra
+        rng = np.random.default_rng(8)
+        f = fk * (1.0 + 1e-3 * rng.uniform(-1.0, 1.0, fk.shape))
+    s.collide(dev(f), Q, P)
+    assert s.read_status()["status"] == 0
+    Qg = Q.cpu().numpy().reshape(f.shape)
+    cells = [0, 21, 45, J - 1]
+    Qo, Po, nuo = oracle.collide(o, f[cells])
+    for k, c in enumerate(cells):
+        assert rel(Qg[c], Qo[k]) <= 1e-5, (form, c, rel(Qg[c], Qo[k]))
+
+
 def sampled_cell_residuals(oracle, residual_fn, o, f, cells, dxdy):
     """The oracle's collision operator at the sampled cells only (zeros elsewhere: the
     residual of a cell uses its own Q) and each sampled cell's share of the residual."""
@@ -98,46 +127,48 @@ def o_L(o):
 
 def test_heat_full_size_converged_residual_sampled(oracle):
     wl, g, o = heat(oracle, sgs.FP32, inner_fixed=0)
+    g.inner_tol = 1e-10  # the cell solves' tolerance bounds the outer residual from below
     s = sgs.Solver(g)
     s.set_sweep_shape(*BENCH_SHAPE)
     f = dev(wl.initial_state())
     Q, P = s.field(), s.field()
     res = torch.zeros(1, dtype=torch.float64, device="cuda")
-    for cycle in range(40):
+    for cycle in range(60):
         s.dc_step(f, Q, P, 0, res=res)
-        if res.item() < 1e-8:
+        if res.item() < 1e-9:
             break
         for _ in range(2):
             s.vcycle(f, 2, 1, 1, 4)
-    assert res.item() < 1e-8 and s.read_status()["status"] == 0
+    assert res.item() < 1e-9 and s.read_status()["status"] == 0
     fh = f.cpu().numpy().reshape(wl.J, wl.N, wl.N, wl.N)
     cells = [0, 1, 21, 42, wl.J - 2, wl.J - 1]
     r = sampled_cell_residuals(oracle, oracle.residual, o, fh, cells, 1.0 / wl.J)
     print("heat: GPU residual", res.item(), "oracle per-cell residuals", r)
-    assert max(r.values()) < 1e-8
+    assert max(r.values()) < 1e-8 / np.sqrt(wl.J)
 
 
 def test_cavity_full_size_converged_residual_sampled(oracle):
     wl = I.cavity_64x64_24v()
     lid = ((0.0, 0.0, 0.0), (wl.lid, 0.0, 0.0))
     g = sgs.Problem(space_dim=2, nx=wl.nx, ny=wl.ny, nv=wl.N, v_max=wl.L, eps=wl.eps, bc_T=(wl.T_wall, wl.T_wall),
-                    bc_T_y=(wl.T_wall, wl.T_wall), bc_u_y=lid, total_mass=wl.total_mass, precision=sgs.FP32)
+                    bc_T_y=(wl.T_wall, wl.T_wall), bc_u_y=lid, total_mass=wl.total_mass, precision=sgs.FP32,
+                    inner_tol=1e-10)  # the cell solves' tolerance bounds the outer residual from below
     base = oracle.Problem(N=wl.N, L=wl.L, J=wl.nx, eps=wl.eps, bc_T=(wl.T_wall, wl.T_wall), total_mass=wl.total_mass)
     o = oracle.Problem2D(base=base, ny=wl.ny, bc_T_y=(wl.T_wall, wl.T_wall), bc_u_y=lid)
     s = sgs.Solver(g)
     f = dev(wl.initial_state())
     Q, P = s.field(), s.field()
     res = torch.zeros(1, dtype=torch.float64, device="cuda")
-    for cycle in range(30):
+    for cycle in range(45):
         s.dc_step(f, Q, P, 0, res=res)
-        if res.item() < 1e-8:
+        if res.item() < 1e-9:
             break
         for _ in range(2):
             s.vcycle(f, 3, 1, 1, 4)
-    assert res.item() < 1e-8 and s.read_status()["status"] == 0
+    assert res.item() < 1e-9 and s.read_status()["status"] == 0
     fh = f.cpu().numpy().reshape(wl.J, wl.N, wl.N, wl.N)
     nx = wl.nx
     cells = [0, nx - 1, (wl.ny - 1) * nx, wl.J - 1, (wl.ny // 2) * nx + nx // 2, (wl.ny - 2) * nx + 7]
     r = sampled_cell_residuals(oracle, oracle.residual2d, o, fh, cells, 1.0 / wl.J)
     print("cavity: GPU residual", res.item(), "oracle per-cell residuals", r)
-    assert max(r.values()) < 1e-8
+    assert max(r.values()) < 1e-8 / np.sqrt(wl.J)

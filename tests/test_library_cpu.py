@@ -61,6 +61,20 @@ def test_problem_validation_on_host(L):
     p2 = sgs.Problem(order=2).c()
     dummy = C.c_void_p(256)
     assert L.sgs_residual_noalloc(C.byref(p2), dummy, dummy, None, dummy, None) == sgs.ERR_UNSUPPORTED
+    # the no-allocation residual refuses what sgs_setup refuses, with the same codes, before
+    # any CUDA call (no GPU is needed to reach these returns)
+    refused = (dict(bc_kind=(sgs.INFLOW, sgs.DIFFUSE), bc_rho=(0.0, 1.0)),
+               dict(bc_u=((0.3, 0.0, 0.0), (0.0, 0.0, 0.0))), dict(nv=10), dict(eps=-1.0), dict(order=5),
+               dict(space_dim=2, nx=4, ny=3), dict(nx=4097))
+    for bad in refused:
+        q = sgs.Problem(**bad)
+        arr = (sgs._Problem * 1)(q.c())
+        hq, wsq = C.c_void_p(), C.c_size_t()
+        want = L.sgs_setup(arr, 1, C.byref(hq), C.byref(wsq))
+        if want == sgs.OK:  # valid for a handle, outside what the no-allocation residual computes
+            L.sgs_destroy(hq)
+            want = sgs.ERR_ARG
+        assert L.sgs_residual_noalloc(C.byref(q.c()), dummy, dummy, None, dummy, None) == want, bad
     # the conservation projection is a handle-wide choice; it enlarges the workspace
     arr = (sgs._Problem * 2)(sgs.Problem().c(), sgs.Problem(conserve_proj=1).c())
     assert L.sgs_setup(arr, 2, C.byref(h), C.byref(ws)) == sgs.ERR_UNSUPPORTED
