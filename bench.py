@@ -55,11 +55,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--dc-every", type=int, default=10)
-    ap.add_argument("--workload", choices=["heat", "shock", "cavity", "batch"], default="heat",
+    ap.add_argument("--workload", choices=["heat", "shock", "cavity", "batch", "paper_bgk_cavity"], default="heat",
                     help="heat: 64-cell heat transfer (default); shock: 128-cell Mach-2 normal shock; "
                          "cavity: 64 x 64 lid-driven cavity (2-D space); batch: 64 independent heat-transfer "
                          "instances of uneven size, grid and eps (one CUDA graph per defect-correction cycle)")
     ap.add_argument("--batch-size", type=int, default=64, help="instances of the batch workload")
+    ap.add_argument("--paper-eps", default="1,0.1,0.01,0.001,0.0001",
+                    help="paper_bgk_cavity: Knudsen numbers to time (comma separated)")
     ap.add_argument("--lo-iters", type=int, default=10, help="SGS iterations per defect-correction cycle (batch)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -69,13 +71,17 @@ def parse():
                     help="sequential iterations (no collision steps pipelined behind the scans)")
     ap.add_argument("--t2tol-all", action="store_true", help="also time the plain FP64 SGS form to 1e-8")
     ap.add_argument("--t2tol-cap", type=float, default=150.0, help="seconds allowed per time-to-residual run")
+    ap.add_argument("--batch-t2tol-cap", type=float, default=0.0,
+                    help="batch: seconds of defect-correction cycles from the initial states to time every "
+                         "instance to residual 1e-8 (0: off)")
     ap.add_argument("--conserve-proj", type=int, choices=[0, 1, 2], default=0,
                     help="conservation projection of Q: 0 the paper's operator, 1 plain, 2 Maxwellian-weighted")
     ap.add_argument("--order", type=int, choices=[1, 2], default=1,
                     help="spatial order of the 1-D scheme (2: linear reconstruction, eq. (slope))")
     ap.add_argument("--pin-mass", action="store_true",
                     help="shock: hold the total mass at the initial state's (eq. (32) rescale), pinning the shock")
-    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d", "dft", "peaks"], default=None,
+    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d", "dft", "peaks", "steps"],
+                    default=None,
                     help="run a small case of one kernel class (for profiler captures) and exit")
     return ap.parse_args()
 
@@ -310,7 +316,7 @@ def run_native(args, rank, world, local):
             step(first + i)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
-        prof = s.profile_read()
+        prof = s.profile_read(with_work=True)
         s.profile(False)
         return [a.elapsed_time(b) for a, b in ev], s.launch_count() - n0, prof
 
@@ -321,16 +327,17 @@ def run_native(args, rank, world, local):
     ms_total = max_over_ranks(sum(ms_steps), world, dev)
     value = whole_job_rate(visits_per_step * args.steps, world, ms_total)
     # the per-class split: the same K steps again with every launch group bracketed by events
-    ms_prof_steps, _, prof = timed_pass(args.warmup + args.steps, True)
+    ms_prof_steps, _, prof_w = timed_pass(args.warmup + args.steps, True)
+    prof = {k: (v[0], v[1]) for k, v in prof_w.items()}
     status = s.read_status()
 
     # dominant kernel class and its roofline
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     dom = max(prof, key=lambda k: prof[k][0])
-    roofs = {k: roofline(k, prof, wl, sm_mhz, peaks, status) for k in ("sweep", "sum", "sum_fp64", "sum_df64")
+    roofs = {k: roofline(k, prof_w, wl, sm_mhz, peaks, status) for k in ("sweep", "sum", "sum_fp64", "sum_df64")
              if prof[k][1] > 0}
-    roof = roofs.get(dom) or roofline(dom, prof, wl, sm_mhz, peaks, status)
+    roof = roofs.get(dom) or roofline(dom, prof_w, wl, sm_mhz, peaks, status)
 
     # end to end through the C ABI with host buffers: H2D of the state (f, P), one step,
     # D2H of the step's residual
@@ -446,18 +453,18 @@ def measure_peaks(wl, shape, local=0):
 
 
 def roofline(cls, prof, wl, sm_mhz, peaks, stats=None):
-    """Roofline of one kernel class over the profiled pass: algorithmic work per launch over
-    the average launch time (CUDA events on the launching stream), against the measured peak
-    of the pipe that bounds it (measure_peaks) or the measured HBM bandwidth."""
-    ms, n = prof[cls]
-    avg = ms / max(1, n)
+    """Roofline of one kernel class over the profiled pass: its algorithmic work (from the
+    cells the library reports each bracketed launch group processed) over its time (CUDA
+    events on the launching stream), against the measured peak of the pipe that bounds it
+    (measure_peaks) or the measured HBM bandwidth. Per launch and over the pass the ratio is
+    the same: both are sums over the same launches."""
+    ms, n, cells = prof[cls]
     hbm, src = measured_peaks()
     K = wl.N ** 3
     if cls in ("sum", "sum_fp64"):
-        # algorithmic work: 10 flops per mode pair over the Hermitian half, every cell of the
-        # workload per launch
-        flops = 10 * 0.5 * pairs_per_cell(wl.N) * wl.J
-        ach = flops / (avg * 1e-3) / 1e12
+        # algorithmic work: 10 flops per mode pair over the Hermitian half, per cell evaluated
+        flops = 10 * 0.5 * pairs_per_cell(wl.N) * cells
+        ach = flops / (ms * 1e-3) / 1e12
         if cls == "sum":
             peak = peaks["fp32_ffma_tflops"]
             return {"kernel": "k_sum<float> (direct spectral sum, FP32)", "bound": "alu", "achieved": ach,
@@ -471,8 +478,8 @@ def roofline(cls, prof, wl, sm_mhz, peaks, stats=None):
         # FP32-pipe operations of one pair in the double-float sum: 8 for w b (two
         # two-products with cross terms) + 4 x 12 for the products with a and their two-sum
         # accumulation; the pipe issues one operation per lane per clock, half the FFMA flop rate
-        ops = 56 * 0.5 * pairs_per_cell(wl.N) * wl.J
-        ach = ops / (avg * 1e-3) / 1e12
+        ops = 56 * 0.5 * pairs_per_cell(wl.N) * cells
+        ach = ops / (ms * 1e-3) / 1e12
         peak = peaks["fp32_ffma_tflops"] / 2.0
         return {"kernel": "k_sum_df (direct spectral sum, double-float on the FP32 pipes)", "bound": "alu",
                 "achieved": ach, "peak": peak, "unit": "T FP32-pipe op/s", "frac": ach / peak, "traffic": None,
@@ -480,18 +487,20 @@ def roofline(cls, prof, wl, sm_mhz, peaks, stats=None):
                                "of measured)"}
     if cls == "sweep":
         # per visit: read the upwind/downwind neighbours, f_j and P_j, write f_j (1-D: 5 K
-        # doubles; 2-D: 7 K doubles); one profiled group = one scan over every cell
-        byts = (7 if is_cavity(wl) else 5) * K * 8 * wl.J
-        ach = byts / (avg * 1e-3) / 1e9
+        # doubles; 2-D: 7 K doubles)
+        byts = (7 if is_cavity(wl) else 5) * K * 8 * cells
+        ach = byts / (ms * 1e-3) / 1e9
         out = {"kernel": "k_sweep<dfloat,8> (persistent SGS scan, one cluster per instance)", "bound": "hbm",
                "achieved": ach, "peak": hbm["hbm_gbs"], "unit": "GB/s", "frac": ach / hbm["hbm_gbs"],
-               "traffic": kernel_traffic("k_sweep<dfloat,8>", wl.J), "peak_source": f"hbm_gbs ({src})",
+               "traffic": kernel_traffic("k_sweep<dfloat,8>", cells / max(1, n)),
+               "traffic_per": f"launch of {cells / max(1, n):.0f} cell visits",
+               "peak_source": f"hbm_gbs ({src})",
                "note": "latency-bound: one visit is a chain of cluster reductions and Newton solves"}
         if stats and stats.get("visits") and not is_cavity(wl):
-            out["latency_model"] = scan_latency_model(avg * 1e3 / wl.J, stats, peaks)
+            out["latency_model"] = scan_latency_model(ms * 1e3 / cells, stats, peaks)
         return out
-    byts = 2 * K * 8 * wl.J
-    ach = byts / (avg * 1e-3) / 1e9
+    byts = 2 * K * 8 * wl.J * n
+    ach = byts / (ms * 1e-3) / 1e9
     return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": hbm["hbm_gbs"], "unit": "GB/s",
             "frac": ach / hbm["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs ({src})"}
 
@@ -753,28 +762,30 @@ def run_batch(args, rank, world, local):
     ms_total = max_over_ranks(sum(a.elapsed_time(c) for a, c in ev), world, torch.device("cuda", local))
     res = b.residuals()
     # per-kernel timings and launch count of one eager cycle (a replay runs exactly the
-    # kernels the captured cycle enqueued; replays themselves are not profiled)
+    # kernels the captured cycle enqueued; replays themselves are not profiled), every
+    # instance active so that every cell is evaluated
     for s in b.solvers.values():
+        s.activate_all()
         s.profile(True)
         s.profile_read()
     launches0 = sum(s.launch_count() for s in b.solvers.values())
-    b._cycle(args.lo_iters, 1e-8)
+    b._cycle(args.lo_iters, 0.0)
     torch.cuda.synchronize()
     launches_per_cycle = sum(s.launch_count() for s in b.solvers.values()) - launches0
     prof = {}
-    for s in b.solvers.values():
-        for k, (ms, n) in s.profile_read().items():
+    flops = 0.0
+    for nv, s in b.solvers.items():
+        for k, (ms, n, cells) in s.profile_read(with_work=True).items():
             a = prof.setdefault(k, [0.0, 0])
             a[0] += ms
             a[1] += n
+            if k == "sum":
+                # FP32 spectral sums: 10 flops per mode pair over the Hermitian half per cell
+                flops += 10 * 0.5 * pairs_per_cell(nv) * cells
         s.profile(False)
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
-    # FP32 spectral sums: 10 flops per mode pair over the Hermitian half, every cell of a
-    # group per launch
-    flops = sum(10 * 0.5 * pairs_per_cell(N) * sum(w.J for w in wls if w.N == N) for N in b.groups)
-    n_sum = prof["sum"][1]
-    ach = flops * (n_sum / max(1, len(b.groups))) / (prof["sum"][0] * 1e-3) / 1e12 if prof["sum"][0] else None
+    ach = flops / (prof["sum"][0] * 1e-3) / 1e12 if prof["sum"][0] else None
     peak = peaks["fp32_ffma_tflops"]
     roof = {"kernel": "k_sum<float> (direct spectral sum, FP32), all groups", "bound": "alu", "achieved": ach,
             "peak": peak, "unit": "TFLOP/s", "frac": ach / peak if ach else None, "traffic": None,
@@ -802,6 +813,29 @@ def run_batch(args, rank, world, local):
     e2e_ms /= args.steps
     h2d = sum(2 * hostf[nv].numel() * 8 for nv in b.groups)
     d2h = sum(hres[nv].numel() * 8 for nv in b.groups)
+    # time from the initial states until each instance's FP64 residual falls below 1e-8
+    t2tol = None
+    if args.batch_t2tol_cap > 0:
+        b.load(states)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reached = [None] * len(probs)
+        cycles = 0
+        while time.perf_counter() - t0 < args.batch_t2tol_cap:
+            b.step()
+            cycles += 1
+            rr = b.residuals()  # the evaluation at the start of this cycle (synchronises)
+            t = time.perf_counter() - t0
+            for i, r in enumerate(rr):
+                if reached[i] is None and r < 1e-8:
+                    reached[i] = round(t, 2)
+            if all(x is not None for x in reached):
+                break
+        done = [x for x in reached if x is not None]
+        t2tol = {"converged": len(done), "of": len(probs), "cycles": cycles, "lo_iters": args.lo_iters,
+                 "seconds_all": max(done) if len(done) == len(probs) else None, "cap_s": args.batch_t2tol_cap,
+                 "per_instance_s": reached,
+                 "per_instance": [{"J": w.J, "N": w.N, "eps": round(w.eps, 5)} for w in wls]}
     out = {
         "metric": METRIC, "value": whole_job_rate(visits_per_step * args.steps, world, ms_total), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
@@ -821,9 +855,88 @@ def run_batch(args, rank, world, local):
                 "note": "every group's (f, P) copied from pinned host memory, one replay, residuals read back"},
         "clocks": clocks, "gpu_launches": int(launches_per_cycle * args.steps), "measured_peaks": peaks,
         "residuals_after": {"max": max(res), "converged_1e-8": int(sum(r < 1e-8 for r in res))},
+        "time_to_residual_1e-8": t2tol,
         "device_status": b.status(),
     }
     return out
+
+
+# The computing times the paper reports for its 2-D BGK cavity (1st and 2nd order; seconds to
+# an outer residual of 1e-5, hardware not stated; None: stopped after 48 hours), for context.
+PAPER_BGK_CAVITY_S = {
+    (1, "sgs_fp"): [2461.28, 18921.84, 162168.90, None, None],
+    (1, "sgs_pfp"): [1876.55, 4684.12, 6144.21, 5490.00, 5502.58],
+    (1, "mg_sgs_pfp"): [425.06, 1030.87, 1090.24, 971.69, 945.81],
+    (2, "sgs_pfp"): [2934.51, 9504.34, 40256.89, 171357.22, None],
+    (2, "mg_sgs_pfp"): [2255.97, 1542.45, 6122.38, 30216.12, 67737.60],
+}
+PAPER_EPS = [1.0, 0.1, 0.01, 1e-3, 1e-4]
+
+
+def run_paper_cavity(args, local):
+    """The paper's 2-D BGK heat-transfer cavity (40 x 40 cells, 20^3 velocities on [-6, 6]^3,
+    top wall at T = 2, nu = 4 pi rho) timed on the GPU in FP64 to an outer residual of 1e-5
+    (inner tolerance 1e-8), for each method and order of the paper's table: SGS-FP,
+    SGS-PFP and MG-SGS-PFP (V-cycles down to 5 x 5 cells, 1 + 1 smoothing iterations at first
+    order, 5 + 1 at second order, 10 iterations on the coarsest grid). Each run is capped at
+    --t2tol-cap seconds. One JSON line with the table and the paper's times beside it."""
+    import torch
+
+    from paper_2409_01910_gb300 import inputs as I
+    from paper_2409_01910_gb300 import sgs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    eps_list = [float(x) for x in args.paper_eps.split(",")]
+    rows = []
+    t_start = time.perf_counter()
+    for order, method in PAPER_BGK_CAVITY_S:
+        for eps in eps_list:
+            wl = I.cavity_heat_bgk_40x40_20v(eps)
+            p = sgs.Problem(space_dim=2, nx=wl.nx, ny=wl.ny, x_lo=-0.5, x_hi=0.5, y_lo=-0.5, y_hi=0.5, nv=wl.N,
+                            v_max=wl.L, collision=sgs.BGK, b0=wl.b0, eps=eps, bc_T=(wl.T_wall, wl.T_wall),
+                            bc_T_y=(wl.T_wall, wl.T_top), total_mass=wl.total_mass, precision=sgs.FP64,
+                            inner_tol=1e-8, order=order, inner_method=sgs.FP if method == "sgs_fp" else sgs.PFP)
+            s = sgs.Solver(p)
+            f = torch.from_numpy(wl.initial_state().reshape(-1)).to(dev)
+            Q, P = s.field(), s.field()
+            res = torch.zeros(1, dtype=torch.float64, device=dev)
+            levels = min(4, s.max_levels())
+            pre = 1 if order == 1 else 5
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r, iters, reached = float("nan"), 0, False
+            while time.perf_counter() - t0 < args.t2tol_cap:
+                if method == "mg_sgs_pfp":
+                    s.collide(f, Q, P)
+                    s.residual(f, Q, res)
+                else:
+                    s.iterate(f, Q, P, flags=sgs.IT_EVAL | (sgs.IT_P_VALID if iters else 0), res=res)
+                    iters += 1
+                r = float(res.item())
+                if r < wl.tol or r != r:
+                    reached = r < wl.tol
+                    break
+                if method == "mg_sgs_pfp":
+                    s.vcycle(f, levels, pre, 1, 10)
+                    iters += 1
+            sec = time.perf_counter() - t0
+            st = s.read_status()
+            paper = PAPER_BGK_CAVITY_S[(order, method)][PAPER_EPS.index(eps)] if eps in PAPER_EPS else None
+            rows.append({"order": order, "method": method, "eps": eps, "seconds": round(sec, 3), "reached": reached,
+                         "residual": r, ("V-cycles" if method.startswith("mg") else "SGS iterations"): iters,
+                         "inner_iters_per_visit": round(st["inner_iters"] / max(1, st["visits"]), 3),
+                         "status": st["status"], "paper_s": paper})
+            s.close()
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return {"metric": "seconds to outer residual 1e-5 (the paper's 2-D BGK cavity)", "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cavity2d_heat_bgk_40x40_N20", "cells": [40, 40], "domain": [[-0.5, 0.5], [-0.5, 0.5]],
+                       "nv": 20, "v_max": 6.0, "collision": "BGK, nu = 4 pi rho", "T_walls": "top 2, others 1",
+                       "tol": 1e-5, "inner_tol": 1e-8, "cap_s": args.t2tol_cap, "multigrid": "4 levels (40^2 .. 5^2)"},
+            "table": rows, "total_s": round(time.perf_counter() - t_start, 1),
+            "paper_note": "paper_s: the paper's computing time for the same problem, method, order and eps "
+                          "(hardware not stated)"}
 
 
 def profile_case(which):
@@ -835,6 +948,21 @@ def profile_case(which):
     from paper_2409_01910_gb300 import inputs as I
     from paper_2409_01910_gb300 import sgs
 
+    if which == "steps":
+        # the benchmark's step on the 64-cell heat workload: one defect-correction evaluation,
+        # then three pipelined SGS iterations with their evaluation (the launch list's case)
+        wl = I.heat_64cells_32v()
+        s = make_solver(wl, sgs.FP32)
+        f = torch.from_numpy(wl.initial_state().reshape(-1)).cuda()
+        Q, P = s.field(), s.field()
+        res = torch.zeros(1, dtype=torch.float64, device="cuda")
+        s.dc_step(f, Q, P, 0, res=res)
+        for _ in range(3):
+            s.iterate(f, Q, P, flags=sgs.IT_P_VALID | sgs.IT_EVAL, res=res)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": which, "status": s.read_status(), "launches": s.launch_count(),
+                          "pipelined": s.overlap()}))
+        return
     if which == "peaks":
         wl = I.heat_64cells_32v()
         s = make_solver(wl, sgs.FP32)
@@ -901,6 +1029,10 @@ def main():
 
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "paper_bgk_cavity":
+        if rank == 0:
+            print(json.dumps(run_paper_cavity(args, local)), flush=True)
+        return
     out = (run_batch if args.workload == "batch" else run_native)(args, rank, world, local)
     if rank == 0:
         if not args.no_cpu_baseline:

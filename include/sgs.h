@@ -103,12 +103,13 @@ typedef struct {
                          far velocity tails). Applied in FP64 in every collision step (all
                          levels and precisions) before P = Q_c - nu (M - f) is formed. Not in
                          the paper; equal in every instance of a handle; ignored for BGK. */
-  int order;          /* spatial order, 1-D only: 1 (or 0): first order (s = 0); 2: linear
-                         reconstruction with the slopes of eq. (slope) (central inside,
-                         one-sided in the end cells, no limiter), explicit in the scans (taken
-                         from the state before each scan, eq. (SGS_BGK)), zero ghost slopes,
-                         diffuse-wall densities from the outgoing face value. Equal in every
-                         instance of a handle; SGS_ERR_UNSUPPORTED with space_dim 2. */
+  int order;          /* spatial order: 1 (or 0): first order (s = 0); 2: linear reconstruction
+                         with the slopes of eq. (slope) (central inside, one-sided in the end
+                         cells, no limiter; in 2-D along x within each row and along y within
+                         each column), explicit in the scans (taken from the state before each
+                         scan or ordering, eq. (SGS_BGK)), zero ghost slopes, diffuse-wall
+                         densities from the outgoing face value. Equal in every instance of a
+                         handle. */
 } sgs_problem;
 
 /* Counters accumulated on the device since setup or the last sgs_reset_stats(). */
@@ -148,9 +149,9 @@ int sgs_collide(sgs_handle* h, const double* f, double* Q, double* P, void* stre
 /* One SGS scan (eq. (29)) over every instance, forward (x_lo -> x_hi) or backward, in a
  * single persistent launch (one thread-block cluster per instance, no host round trip).
  * f (device) is updated in place; P (device) from the preceding sgs_collide; rhs (device,
- * nullable) is the b of R(f) = b (multigrid / defect correction). Second order (order 2,
- * 1-D): the slope terms of eq. (SGS_BGK) and the face-value wall densities are taken from f
- * as it is when the scan starts (explicit slopes). */
+ * nullable) is the b of R(f) = b (multigrid / defect correction). Second order (order 2):
+ * the slope terms of eq. (SGS_BGK) and the face-value wall densities are taken from f as it
+ * is when the scan (in 2-D: the ordering) starts (explicit slopes). */
 int sgs_sweep_forward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream);
 int sgs_sweep_backward(sgs_handle* h, double* f, const double* P, const double* rhs, void* stream);
 /* One scan in a given ordering. 1-D: 0 forward, 1 backward. 2-D (eq. (29) in each
@@ -261,7 +262,9 @@ int sgs_get_overlap(const sgs_handle* h);
 
 /* Kernel-time profiling. When enabled, every group of launches is bracketed by CUDA events
  * recorded on the launching stream; sgs_profile_read synchronises on them and returns, per
- * class, the summed milliseconds and the number of bracketed groups, then clears them.
+ * class, the summed milliseconds, the number of bracketed groups and (work, nullable) the
+ * cells they processed: cells evaluated by the spectral sums, cells visited by the scans
+ * (0 for the other classes), then clears them.
  * sgs_launch_count returns the number of kernels enqueued through the handle so far.
  * Launches enqueued while the stream is being captured into a CUDA graph are not timed. */
 enum sgs_prof_class {
@@ -277,12 +280,14 @@ enum sgs_prof_class {
   SGS_PROF_CLASSES = 9
 };
 int sgs_profile(sgs_handle* h, int enable);
-int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, int n_classes);
+int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, double* work, int n_classes);
 unsigned long long sgs_launch_count(const sgs_handle* h);
 
 /* Batches: per-instance activity. Every instance starts active (at bind). An inactive
  * instance is converged: the scans (and the mass rescale) skip it, so its f stays as it
- * is, while collisions and residuals still cover every cell.
+ * is; in a handle of several instances the collision steps skip its cells as well (their Q,
+ * P and collision frequency from the last evaluation stay valid, f being unchanged), while
+ * residuals still cover every cell.
  *   sgs_update_active: active[q] = !(res[q] < tol) for the device residuals res[n_inst]
  *     (as written by sgs_residual / sgs_dc_step); asynchronous, graph-capturable.
  *   sgs_activate_all: marks every instance active again; asynchronous.
@@ -303,14 +308,22 @@ typedef struct {
   int sweep_ept, sweep_cluster, sweep_threads; /* chosen scan shape */
   float sweep_ms;                              /* its forward + backward scan time, all instances */
   int candidates;                              /* shapes timed */
-  int sum_warps, sum_units, sum_blocks;        /* spectral-sum decomposition (set at setup) */
+  int sum_warps, sum_units, sum_blocks;        /* chosen spectral-sum decomposition: warps (lane
+                                                  groups of 32 cells) per block, work units, blocks */
+  float sum_ms;                                /* its time per sum, all cells (handle's arithmetic) */
+  int sum_candidates;                          /* decompositions timed */
 } sgs_tuning;
 
 /* Autotuner. Times every valid scan shape on the bound instances (reps forward + backward
  * scan pairs each, after one untimed pair, CUDA events on the stream), keeps the fastest
  * for all later scans and reports it. The timed scans are real SGS scans: f advances by
- * (reps + 1) symmetric sweeps with the given P per candidate. Synchronises the stream; not
- * graph-capturable (call it before capturing). */
+ * (reps + 1) symmetric sweeps with the given P per candidate. Then times the spectral sum
+ * (the handle's arithmetic, all cells, two launches after one untimed one) for every
+ * decomposition of 1, 2 or 4 lane groups per block and about 1500, 3000 or 6000 blocks, and
+ * keeps the fastest for all later collision steps (the sums write only workspace buffers;
+ * the reduction order of the partial sums follows the decomposition, so results may differ
+ * in the last bits). Synchronises the stream; not graph-capturable (call it before
+ * capturing). */
 int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning* out, void* stream);
 
 /* Measurement probes (not part of the method; they supply the denominators of the

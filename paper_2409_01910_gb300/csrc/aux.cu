@@ -250,6 +250,149 @@ __global__ void __launch_bounds__(256) k_residual_cells_o2(AuxArgs a, const doub
   if (threadIdx.x == 0) part[c] = w * t;
 }
 
+// ---------------------------------------------------------------------------------------
+// Second-order scheme, 2-D: the slopes of eq. (slope) along x within each row and along y
+// within each column (central inside, one-sided in the end cells, zero when the grid has a
+// single cell in that direction), zero ghost slopes, wall ghosts from the outgoing face
+// value f -/+ s/2 of the slope normal to the side. Cells (i, j) at j nx + i.
+// ---------------------------------------------------------------------------------------
+__device__ inline double slope_x2d(const double* f, long long base, int ci, int nx, int e, int K) {
+  if (nx < 2) return 0.0;
+  if (ci == 0) return f[base + K + e] - f[base + e];
+  if (ci == nx - 1) return f[base + e] - f[base - K + e];
+  return 0.5 * (f[base + K + e] - f[base - K + e]);
+}
+__device__ inline double slope_y2d(const double* f, long long base, int cj, int nx, int ny, int e, int K) {
+  if (ny < 2) return 0.0;
+  const long long r = (long long)nx * K;
+  if (cj == 0) return f[base + r + e] - f[base + e];
+  if (cj == ny - 1) return f[base + e] - f[base - r + e];
+  return 0.5 * (f[base + r + e] - f[base - r + e]);
+}
+
+// Boundary face of index `face` (numbering of k_wall_flux2d): its side and cell.
+__device__ inline void face_cell2d(int face, int nx, int ny, int& side, int& cell) {
+  if (face < ny) {
+    side = 0;
+    cell = face * nx;
+  } else if (face < 2 * ny) {
+    side = 1;
+    cell = (face - ny) * nx + nx - 1;
+  } else if (face < 2 * ny + nx) {
+    side = 2;
+    cell = face - 2 * ny;
+  } else {
+    side = 3;
+    cell = (ny - 1) * nx + (face - 2 * ny - nx);
+  }
+}
+
+// sflux[face] = w sum over the velocities leaving the domain through the face of (v.n) s_n,
+// s_n the slope normal to the face's side in its cell.
+__global__ void __launch_bounds__(256) k_wall_slope_flux2d(AuxArgs a, const double* __restrict__ f, double* sflux) {
+  __shared__ double sh[32];
+  const InstDev& I = a.inst[0];
+  const int nx = a.nx, ny = a.ny, N = a.N, K = N * N * N;
+  int side, cell;
+  face_cell2d(blockIdx.x, nx, ny, side, cell);
+  const int ci = cell % nx, cj = cell / nx;
+  const long long base = I.f_off + (long long)cell * K;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    double vn = node(side < 2 ? e / (N * N) : (e / N) % N, N, a.dv);
+    bool out = side % 2 == 0 ? vn < 0.0 : vn > 0.0;
+    if (out) acc += vn * (side < 2 ? slope_x2d(f, base, ci, nx, e, K) : slope_y2d(f, base, cj, nx, ny, e, K));
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) sflux[blockIdx.x] = a.dv * a.dv * a.dv * t;
+}
+
+// Right-hand side of a second-order 2-D scan ordering from the state f before it (r = ... - out):
+//   out = rhs + (v1^+ sx_W - v1 sx + v1^- sx_E) / (2 dx) + (v2^+ sy_S - v2 sy + v2^- sy_N) / (2 dy)
+// (zero slopes beyond the walls), plus in the wall cells the change of each lagged ghost from
+// the cell value the scan uses to the face value: rho_face - rho_cell = +0.5 sflux / denom on
+// the x_lo / y_lo sides (face f - s/2), -0.5 sflux / denom on the x_hi / y_hi sides; the
+// scan's r holds -v1^+ ghost_W / dx, +v1^- ghost_E / dx, -v2^+ ghost_S / dy, +v2^- ghost_N / dy.
+__global__ void __launch_bounds__(256) k_slope_rhs2d(AuxArgs a, const double* __restrict__ f,
+                                                     const double* __restrict__ rhs,
+                                                     const double* __restrict__ sflux, double* __restrict__ out) {
+  const InstDev& I = a.inst[0];
+  const int nx = a.nx, ny = a.ny, N = a.N, K = N * N * N;
+  const int c = blockIdx.x, ci = c % nx, cj = c / nx;
+  const long long base = I.f_off + (long long)c * K;
+  const double inv_dx = 1.0 / I.dx, inv_dy = 1.0 / I.dy;
+  const int fidx[4] = {cj, ny + cj, 2 * ny + ci, 2 * ny + nx + ci};
+  const bool at[4] = {ci == 0, ci == nx - 1, cj == 0, cj == ny - 1};
+  double drho[4];
+  for (int s = 0; s < 4; s++)
+    drho[s] = (at[s] && I.bc_kind[s] != SGS_INFLOW) ? (s % 2 == 0 ? 0.5 : -0.5) * sflux[fidx[s]] / I.wall_denom[s]
+                                                    : 0.0;
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < K; e += gridDim.y * blockDim.x) {
+    int i1 = e / (N * N), i2 = (e / N) % N, i3 = e % N;
+    double v1 = node(i1, N, a.dv), v2 = node(i2, N, a.dv);
+    double sx = slope_x2d(f, base, ci, nx, e, K), sy = slope_y2d(f, base, cj, nx, ny, e, K);
+    double sw = ci > 0 ? slope_x2d(f, base - K, ci - 1, nx, e, K) : 0.0;
+    double se = ci < nx - 1 ? slope_x2d(f, base + K, ci + 1, nx, e, K) : 0.0;
+    const long long r = (long long)nx * K;
+    double ss = cj > 0 ? slope_y2d(f, base - r, cj - 1, nx, ny, e, K) : 0.0;
+    double sn = cj < ny - 1 ? slope_y2d(f, base + r, cj + 1, nx, ny, e, K) : 0.0;
+    double b = (rhs ? rhs[base + e] : 0.0) + (fmax(v1, 0.0) * sw - v1 * sx + fmin(v1, 0.0) * se) * (0.5 * inv_dx) +
+               (fmax(v2, 0.0) * ss - v2 * sy + fmin(v2, 0.0) * sn) * (0.5 * inv_dy);
+    double Mh[4];
+    for (int s = 0; s < 4; s++) Mh[s] = drho[s] != 0.0 ? drho[s] * I.wall[s][0][i1] * I.wall[s][1][i2] * I.wall[s][2][i3] : 0.0;
+    b += fmax(v1, 0.0) * Mh[0] * inv_dx - fmin(v1, 0.0) * Mh[1] * inv_dx + fmax(v2, 0.0) * Mh[2] * inv_dy -
+         fmin(v2, 0.0) * Mh[3] * inv_dy;
+    out[base + e] = b;
+  }
+}
+
+cudaError_t launch_slope_rhs2d(const AuxArgs& a, const double* f, const double* rhs, double* out, cudaStream_t st) {
+  k_wall_slope_flux2d<<<2 * (a.nx + a.ny), 256, 0, st>>>(a, f, a.sflux);
+  k_slope_rhs2d<<<dim3(a.C, 4), 256, 0, st>>>(a, f, rhs, a.sflux, out);
+  return cudaGetLastError();
+}
+
+// Second-order 2-D residual per cell: the upwind differences of the face values in x and y
+// (eq. (upwind) in each direction), R = (v1^+ ((f + sx/2) - (f_W + sx_W/2)) + v1^- ((f_E - sx_E/2)
+// - (f - sx/2))) / dx + (the same in y) / dy - Q/eps - b, ghosts from the face values of the
+// same f with zero ghost slopes.
+__global__ void __launch_bounds__(256) k_residual_cells2d_o2(AuxArgs a, const double* __restrict__ f,
+                                                              const double* __restrict__ Q,
+                                                              const double* __restrict__ rhs, const double* flux,
+                                                              const double* sflux, double* part, double* Rout) {
+  __shared__ double sh[32];
+  const InstDev& I = a.inst[0];
+  const int nx = a.nx, ny = a.ny, N = a.N, K = N * N * N;
+  const int c = blockIdx.x, ci = c % nx, cj = c / nx;
+  const long long base = I.f_off + (long long)c * K, r = (long long)nx * K;
+  const double w = a.dv * a.dv * a.dv, inv_dx = 1.0 / I.dx, inv_dy = 1.0 / I.dy, inv_eps = 1.0 / I.eps;
+  double rw[4];
+  const int fidx[4] = {cj, ny + cj, 2 * ny + ci, 2 * ny + nx + ci};
+  for (int s = 0; s < 4; s++)
+    rw[s] = I.bc_kind[s] == SGS_INFLOW ? I.bc_rho[s]
+                                       : -(flux[fidx[s]] + (s % 2 == 0 ? -0.5 : 0.5) * sflux[fidx[s]]) / I.wall_denom[s];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    int i1 = e / (N * N), i2 = (e / N) % N, i3 = e % N;
+    double v1 = node(i1, N, a.dv), v2 = node(i2, N, a.dv);
+    double fc = f[base + e];
+    double hx = 0.5 * slope_x2d(f, base, ci, nx, e, K), hy = 0.5 * slope_y2d(f, base, cj, nx, ny, e, K);
+    double gh[4];
+    for (int s = 0; s < 4; s++) gh[s] = rw[s] * I.wall[s][0][i1] * I.wall[s][1][i2] * I.wall[s][2][i3];
+    double xw = ci == 0 ? gh[0] : f[base - K + e] + 0.5 * slope_x2d(f, base - K, ci - 1, nx, e, K);
+    double xe = ci == nx - 1 ? gh[1] : f[base + K + e] - 0.5 * slope_x2d(f, base + K, ci + 1, nx, e, K);
+    double ys = cj == 0 ? gh[2] : f[base - r + e] + 0.5 * slope_y2d(f, base - r, cj - 1, nx, ny, e, K);
+    double yn = cj == ny - 1 ? gh[3] : f[base + r + e] - 0.5 * slope_y2d(f, base + r, cj + 1, nx, ny, e, K);
+    double R = (fmax(v1, 0.0) * ((fc + hx) - xw) + fmin(v1, 0.0) * (xe - (fc - hx))) * inv_dx +
+               (fmax(v2, 0.0) * ((fc + hy) - ys) + fmin(v2, 0.0) * (yn - (fc - hy))) * inv_dy - Q[base + e] * inv_eps;
+    if (rhs) R -= rhs[base + e];
+    if (Rout) Rout[base + e] = R;
+    acc += R * R;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[c] = w * t;
+}
+
 cudaError_t launch_residual_impl(const AuxArgs& a, const double* f, const double* Q, const double* rhs, double* res,
                                  double* R, cudaStream_t st) {
   double* flux = a.scratch;                  // [2 n_inst]
@@ -257,7 +400,12 @@ cudaError_t launch_residual_impl(const AuxArgs& a, const double* f, const double
   if (a.two_d) {
     double* flux2 = a.scratch + 2 * a.n_inst + 2 * a.C;  // [2 (nx + ny)], after the mass slots
     k_wall_flux2d<<<2 * (a.nx + a.ny), 256, 0, st>>>(a, f, flux2);
-    k_residual_cells2d<<<a.C, 256, 0, st>>>(a, f, Q, rhs, flux2, part, R);
+    if (a.sflux) {  // second-order scheme
+      k_wall_slope_flux2d<<<2 * (a.nx + a.ny), 256, 0, st>>>(a, f, a.sflux);
+      k_residual_cells2d_o2<<<a.C, 256, 0, st>>>(a, f, Q, rhs, flux2, a.sflux, part, R);
+    } else {
+      k_residual_cells2d<<<a.C, 256, 0, st>>>(a, f, Q, rhs, flux2, part, R);
+    }
     if (res) k_residual_final<<<1, 32, 0, st>>>(a.inst, 1, part, res);
     return cudaGetLastError();
   }

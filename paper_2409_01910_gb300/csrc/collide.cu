@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ f, C
   __shared__ double vv[kMaxN];
   __shared__ double part[8][5];
   int c = blockIdx.x;
+  if (!cell_active(ct.active, ct.cell_inst, c)) return;
   int K = N * N * N;
   const double* fc = f + ct.cell_off[c];
   if (threadIdx.x < N) vv[threadIdx.x] = node(threadIdx.x, N, dv);
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(256) k_dft_i3(const double* __restrict__ f, Ce
   // M = E1[i1] E2[i2] E3[i3]: E12[i2] = E1[i1] E2[i2] for this block's i1, then one product
   __shared__ double E12[kMaxN], E3[kMaxN], E12r[kMaxN], E3r[kMaxN];
   int c = blockIdx.x, i1 = blockIdx.y;
+  if (!cell_active(ct.active, ct.cell_inst, c)) return;
   if (threadIdx.x < N) {
     const double* e = efac + (long long)c * 3 * kMaxN;
     E12[threadIdx.x] = e[i1] * e[kMaxN + threadIdx.x];
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(256) k_dft_i2(SpecBufs<T> sb, int N) {
   CT* xa = (CT*)(sn + n * N);  // [N][n]
   CT* xb = xa + N * n;
   int c = blockIdx.x, i1 = blockIdx.y;
+  if (!cell_active(sb.active, sb.cell_inst, c)) return;
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
     cs[t] = sb.twc[t];
     sn[t] = sb.tws[t];
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(256) k_dft_i1(SpecBufs<T> sb, int N) {
   CT* xa = (CT*)(sn + n * N);  // [N][n] (i1, k3)
   CT* xb = xa + N * n;
   int c = blockIdx.x, k2 = blockIdx.y;
+  if (!cell_active(sb.active, sb.cell_inst, c)) return;
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
     cs[t] = sb.twc[t];
     sn[t] = sb.tws[t];
@@ -297,6 +301,16 @@ __global__ void __launch_bounds__(128) k_sum(SumArgs<T> a) {
   const uint32_t row_bytes = n * kLanes * sizeof(CT);
   const uint32_t stage_bytes = PW * sizeof(T) + ng * 2 * row_bytes;
 
+  if (a.active) {
+    // a block whose lane groups hold no cell of an active instance has nothing to compute
+    __shared__ int s_any;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    const int c = (g0 + warp) * kLanes + lane;
+    if (warp < ng && c < a.C && a.active[a.cell_inst[c]]) s_any = 1;
+    __syncthreads();
+    if (!s_any) return;
+  }
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -460,6 +474,13 @@ __global__ void __launch_bounds__(KW * 32, 2) k_sum_df(SumDfArgs a) {
   const uint32_t row_bytes = n * kLanes * sizeof(float4);
   const uint32_t stage_bytes = 2 * PW * sizeof(float) + 2 * row_bytes;
 
+  if (a.active) {
+    // a group with no cell of an active instance has nothing to compute (every warp of the
+    // block serves the same group: one warp's vote decides)
+    const int c = g * kLanes + lane;
+    const bool mine = c < a.C && a.active[a.cell_inst[c]];
+    if (!__any_sync(0xffffffffu, mine)) return;
+  }
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -606,6 +627,7 @@ __global__ void __launch_bounds__(256) k_idft_k1(SpecBufs<T> sb, int N) {
   T* sn = cs + n * N;
   CT* x = (CT*)(sn + n * N);  // [k1][k3]
   int c = blockIdx.x, k2 = blockIdx.y;
+  if (!cell_active(sb.active, sb.cell_inst, c)) return;
   int g = c / kLanes, lane = c % kLanes;
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
     cs[t] = sb.twc[t];
@@ -639,6 +661,7 @@ __global__ void __launch_bounds__(256) k_idft_k2(SpecBufs<T> sb, int N) {
   T* sn = cs + n * N;
   CT* x = (CT*)(sn + n * N);  // [k2][k3]
   int c = blockIdx.x, i1 = blockIdx.y;
+  if (!cell_active(sb.active, sb.cell_inst, c)) return;
   for (int t = threadIdx.x; t < n * N; t += blockDim.x) {
     cs[t] = sb.twc[t];
     sn[t] = sb.tws[t];
@@ -674,6 +697,7 @@ __global__ void __launch_bounds__(256) k_idft_k3(SpecBufs<T> sb, const double* _
   CT* x = (CT*)(sn + n * N);  // [i2][k3]
   __shared__ double E12[kMaxN], E3[kMaxN];
   int c = blockIdx.x, i1 = blockIdx.y;
+  if (!cell_active(ct.active, ct.cell_inst, c)) return;
   if (threadIdx.x < N) {
     const double* e = efac + (long long)c * 3 * kMaxN;
     E12[threadIdx.x] = e[i1] * e[kMaxN + threadIdx.x];
@@ -783,6 +807,7 @@ __global__ void __launch_bounds__(256) k_conserve_apply(const double* __restrict
                                                         double* Q, double* P, double* Qraw, int N, double dv) {
   __shared__ double sm[5], lam[5], S[3][5];
   int c = blockIdx.x, i1 = blockIdx.y;
+  if (!cell_active(ct.active, ct.cell_inst, c)) return;
   const double* e = efac + (long long)c * 3 * kMaxN;
   if (threadIdx.x < 5) {
     double a = 0.0;
@@ -846,6 +871,7 @@ __global__ void __launch_bounds__(256) k_collide_bgk(const double* __restrict__ 
                                                       int N, double dv) {
   __shared__ double E[3 * kMaxN];
   int c = blockIdx.x, i1 = blockIdx.y;
+  if (!cell_active(ct.active, ct.cell_inst, c)) return;
   maxwell_factors(theta, c, N, dv, E);
   __syncthreads();
   long long base = ct.cell_off[c] + (long long)i1 * N * N;

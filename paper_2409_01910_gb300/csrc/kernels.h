@@ -40,7 +40,14 @@ struct CellTables {
   const InstDev* inst;
   const long long* cell_off;  // element offset of each cell's distribution
   const int* cell_inst;       // instance of each cell
+  const int* active;          // per instance (nullable): 0 = converged, its cells are skipped
 };
+
+// Whether cell c belongs to an active instance (every cell when active is null). A converged
+// instance's f no longer changes, so its last collision results stay valid.
+__device__ __forceinline__ bool cell_active(const int* active, const int* cell_inst, int c) {
+  return !active || active[cell_inst[c]] != 0;
+}
 
 template <typename T>
 struct SpecBufs {
@@ -53,6 +60,8 @@ struct SpecBufs {
   CT *st2a, *st2b;       // [C][N][n][n]
   CT *ahat, *bhat;       // [G][n][n][n][32]
   CT* qhat;              // [G][n][n][n][32]
+  const int* cell_inst;  // instance of each cell, and the per-instance activity (nullable):
+  const int* active;     // the transforms skip the cells of converged instances
 };
 
 template <typename T>
@@ -68,6 +77,9 @@ struct SumArgs {
   int Gs;                       // group stride of partial (the handle's group count)
   Counters* cnt;
   long long spin_max;
+  const int* cell_inst;         // cells of this launch's groups and the per-instance activity
+  const int* active;            // (nullable): a block whose groups hold no active cell returns
+  int C;                        // cells of this launch
 };
 
 // Inputs of the first DFT pass: mode 0 transforms (f - M, f + M); modes 1 and 2 transform
@@ -106,6 +118,9 @@ struct SumDfArgs {
   int Gs;             // group stride of partial
   Counters* cnt;
   long long spin_max;
+  const int* cell_inst;
+  const int* active;  // as in SumArgs
+  int C;
 };
 
 template <typename T>
@@ -152,7 +167,8 @@ struct AuxArgs {
   const int* active;      // per instance: 0 = converged, its rescale is skipped
   int two_d;              // 2-D space (one instance): grid nx x ny
   int nx, ny;
-  double* sflux;          // second-order scheme: [2 n_inst] slope fluxes of the walls; null at first order
+  double* sflux;          // second-order scheme: slope fluxes of the walls, [2 n_inst] in 1-D, one per
+                          // boundary face [2 (nx + ny)] in 2-D; null at first order
 };
 
 // Host side (sgs_api.cu): validation of one problem description (SGS_OK, SGS_ERR_ARG or
@@ -171,6 +187,8 @@ cudaError_t launch_factors(const double* theta, int C, int N, double dv, double*
 // Second-order scheme (1-D): out = rhs + the explicit slope terms of the scan and the
 // face-value correction of the lagged wall densities, all from the state f before the scan.
 cudaError_t launch_slope_rhs(const AuxArgs& a, const double* f, const double* rhs, double* out, cudaStream_t st);
+// The same for one 2-D instance (slopes along x and y, four wall sides).
+cudaError_t launch_slope_rhs2d(const AuxArgs& a, const double* f, const double* rhs, double* out, cudaStream_t st);
 // Source iteration: wall fluxes of f, then the per-node transport march (1-D problems).
 cudaError_t launch_si_transport(const AuxArgs& a, double* f, const double* P, const double* rhs, const double* efac,
                                 const double* nu, cudaStream_t st);

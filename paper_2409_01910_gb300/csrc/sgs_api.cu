@@ -66,6 +66,12 @@ double weight_G(int N, double L, int collision, double b0, long long a2, long lo
 
 bool valid_nv(int N) { return N >= 8 && N <= 32 && N % 4 == 0; }
 
+// Decompositions of the spectral sum: about kSumBlocks blocks of NW warps (NW lane groups) by
+// default; the autotuner tries every NW in 1, 2, 4 with each block count of kSumBlockChoices.
+constexpr int kSumBlocks = 3000;
+constexpr int kSumBlockChoices[3] = {1500, 3000, 6000};
+constexpr int kSumMaxWarps = 4;
+
 struct Unit {
   int k1, k2, m1lo, m1hi;
   long long step0;
@@ -91,6 +97,9 @@ struct sgs_handle {
   std::vector<int> row_start, row_units;
   long long steps = 0;
   int NW = 1, PW64 = 0, PW32 = 0;
+  long long sum_total = 0;  // steps of the whole sum
+  int U_cap = 0;            // largest unit count of any decomposition (sizes the partial buffers)
+  int sum_blocks = 0;       // block count the current decomposition was planned for
   // tables
   std::vector<double> tw_cos, tw_sin, Gtab, Lo;
   long long na = 0, nb = 0;
@@ -129,6 +138,7 @@ struct sgs_handle {
   struct Rec {
     int cls;
     cudaEvent_t a, b;
+    double work;  // cells the bracketed launches evaluated (sums) or visited (scans)
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -183,53 +193,19 @@ bool gram_inverse(int N, double dv, double* Ainv) {
   return true;
 }
 
-int plan(sgs_handle* h) {
-  int N = h->N, n = N - 1, H = N / 2 - 1;
-  h->n = n;
-  h->H = H;
-  h->G = (h->C + kLanes - 1) / kLanes;
-  h->NW = h->G >= 2 ? 2 : 1;
-  h->PW64 = sum_pad(H, 8);
-  h->PW32 = sum_pad(H, 4);
-  // twiddles: angle 2 pi ((k j) mod N) / N, k in [-H, H], j = i - N/2 + 1
-  h->tw_cos.assign((size_t)n * N, 0.0);
-  h->tw_sin.assign((size_t)n * N, 0.0);
-  for (int k = -H; k <= H; k++)
-    for (int i = 0; i < N; i++) {
-      long long kj = ((long long)k * (i - N / 2 + 1)) % N;
-      if (kj < 0) kj += N;
-      double ang = 2.0 * kPi * (double)kj / N;
-      h->tw_cos[(size_t)(k + H) * N + i] = std::cos(ang);
-      h->tw_sin[(size_t)(k + H) * N + i] = std::sin(ang);
-    }
-  if (!h->spectral) return SGS_OK;
-  const sgs_problem& p0 = h->prob[0];
-  h->na = 3LL * H * H + 1;
-  h->nb = 12LL * H * H + 1;
-  h->Gtab.resize((size_t)(h->na * h->nb));
-  h->Lo.resize((size_t)h->na);
-  for (long long a2 = 0; a2 < h->na; a2++) {
-    for (long long b2 = 0; b2 < h->nb; b2++)
-      h->Gtab[(size_t)(a2 * h->nb + b2)] = weight_G(N, p0.v_max, p0.collision, p0.b0, a2, b2);
-    h->Lo[(size_t)a2] = weight_G(N, p0.v_max, p0.collision, p0.b0, 4 * a2, 0);
-  }
-  // rows of the Hermitian half: k1 > 0, or k1 == 0 and k2 >= 0
+// Work units of the spectral sum: each row (k1, k2) of the Hermitian half split into m1
+// ranges of about `cap` steps. The steps are numbered row by row and m1 by m1 whatever the
+// split, so the weight blocks (built per step) stay valid for every decomposition.
+long long sum_target(const sgs_handle* h, int nw, int blocks) {
+  int blocks_y = (h->G + nw - 1) / nw;
+  return std::max(1LL, (long long)blocks / blocks_y);
+}
+
+int plan_units(sgs_handle* h, long long target_units) {
+  const int n = h->n, H = h->H;
+  const int n_rows = (int)h->row_k.size();
+  long long cap = std::max<long long>(n, h->sum_total / target_units);
   std::vector<Unit> u;
-  long long total = 0;
-  int row = 0;
-  for (int k1 = 0; k1 <= H; k1++)
-    for (int k2 = -H; k2 <= H; k2++) {
-      if (k1 == 0 && k2 < 0) continue;
-      int m1lo = std::max(-H, k1 - H), m1hi = std::min(H, k1 + H);
-      int nm2 = n - std::abs(k2);
-      total += (long long)(m1hi - m1lo + 1) * nm2;
-      h->row_k.push_back(make_int2(k1, k2));
-      row++;
-    }
-  int n_rows = row;
-  int blocks_y = (h->G + h->NW - 1) / h->NW;
-  long long target_units = std::max(1LL, 3000LL / blocks_y);
-  long long cap = std::max<long long>(n, total / target_units);
   long long step = 0;
   for (int r = 0; r < n_rows; r++) {
     int k1 = h->row_k[r].x, k2 = h->row_k[r].y;
@@ -265,6 +241,59 @@ int plan(sgs_handle* h) {
     return u[a].row != u[b].row ? u[a].row < u[b].row : u[a].m1lo < u[b].m1lo;
   });
   for (int i : order) h->row_units[fill[u[i].row]++] = i;
+  return (int)u.size();
+}
+
+int plan(sgs_handle* h) {
+  int N = h->N, n = N - 1, H = N / 2 - 1;
+  h->n = n;
+  h->H = H;
+  h->G = (h->C + kLanes - 1) / kLanes;
+  h->NW = h->G >= 2 ? 2 : 1;
+  h->PW64 = sum_pad(H, 8);
+  h->PW32 = sum_pad(H, 4);
+  // twiddles: angle 2 pi ((k j) mod N) / N, k in [-H, H], j = i - N/2 + 1
+  h->tw_cos.assign((size_t)n * N, 0.0);
+  h->tw_sin.assign((size_t)n * N, 0.0);
+  for (int k = -H; k <= H; k++)
+    for (int i = 0; i < N; i++) {
+      long long kj = ((long long)k * (i - N / 2 + 1)) % N;
+      if (kj < 0) kj += N;
+      double ang = 2.0 * kPi * (double)kj / N;
+      h->tw_cos[(size_t)(k + H) * N + i] = std::cos(ang);
+      h->tw_sin[(size_t)(k + H) * N + i] = std::sin(ang);
+    }
+  if (!h->spectral) return SGS_OK;
+  const sgs_problem& p0 = h->prob[0];
+  h->na = 3LL * H * H + 1;
+  h->nb = 12LL * H * H + 1;
+  h->Gtab.resize((size_t)(h->na * h->nb));
+  h->Lo.resize((size_t)h->na);
+  for (long long a2 = 0; a2 < h->na; a2++) {
+    for (long long b2 = 0; b2 < h->nb; b2++)
+      h->Gtab[(size_t)(a2 * h->nb + b2)] = weight_G(N, p0.v_max, p0.collision, p0.b0, a2, b2);
+    h->Lo[(size_t)a2] = weight_G(N, p0.v_max, p0.collision, p0.b0, 4 * a2, 0);
+  }
+  // rows of the Hermitian half: k1 > 0, or k1 == 0 and k2 >= 0
+  long long total = 0;
+  for (int k1 = 0; k1 <= H; k1++)
+    for (int k2 = -H; k2 <= H; k2++) {
+      if (k1 == 0 && k2 < 0) continue;
+      int m1lo = std::max(-H, k1 - H), m1hi = std::min(H, k1 + H);
+      int nm2 = n - std::abs(k2);
+      total += (long long)(m1hi - m1lo + 1) * nm2;
+      h->row_k.push_back(make_int2(k1, k2));
+    }
+  h->sum_total = total;
+  // default decomposition: about kSumBlocks blocks in the launch; the partial buffers are sized
+  // for the largest unit count the autotuner may try
+  h->U_cap = 0;
+  for (int nw = 1; nw <= kSumMaxWarps; nw *= 2)
+    for (int bl : kSumBlockChoices) h->U_cap = std::max(h->U_cap, plan_units(h, sum_target(h, nw, bl)));
+  h->NW = h->G >= 2 ? 2 : 1;
+  h->sum_blocks = kSumBlocks;
+  plan_units(h, sum_target(h, h->NW, h->sum_blocks));
+  h->U_cap = std::max(h->U_cap, (int)h->units.size());
   return SGS_OK;
 }
 
@@ -295,17 +324,18 @@ void layout(sgs_handle* h) {
   f.efac_ref = take(sizeof(double) * 3 * kMaxN * C);  // is the largest) and those of the reference
   f.cproj_A = take(h->cproj == 1 ? sizeof(double) * 25 : 0);  // inverse Gram matrix of (1, v, |v|^2)
   f.mom = take(h->cproj ? sizeof(double) * 5 * (size_t)C * N : 0);  // moments of Q per (cell, i1) slab
-  f.sflux = take(h->order2 ? sizeof(double) * 2 * h->n_inst : 0);     // second order: wall slope fluxes
+  f.sflux = take(h->order2 ? sizeof(double) * (h->two_d ? 2 * (h->inst[0].nx + h->inst[0].ny) : 2 * h->n_inst)
+                           : 0);                                     // second order: wall slope fluxes
   f.o2rhs = take(h->order2 ? sizeof(double) * h->field : 0);         // second order: scan right-hand side
   bool sp = h->spectral;
-  size_t U = h->units.size();
+  size_t U = (size_t)std::max<int>(h->U_cap, (int)h->units.size());
   f.G = take(sp ? sizeof(double) * h->na * h->nb : 0);
   f.Lo = take(sp ? sizeof(double) * h->na : 0);
   f.units = take(sizeof(int4) * U);
   f.step0 = take(sizeof(long long) * U);
   f.row_k = take(sizeof(int2) * h->row_k.size());
   f.row_start = take(sizeof(int) * h->row_start.size());
-  f.row_units = take(sizeof(int) * h->row_units.size());
+  f.row_units = take(sizeof(int) * U);
   f.W64 = take(sp ? sizeof(double) * h->steps * h->PW64 : 0);
   f.W32 = take(sp && h->precision == SGS_FP32 ? sizeof(float) * h->steps * h->PW32 : 0);
   size_t cpl = sizeof(double2);
@@ -384,7 +414,6 @@ int sgs::check_problem(const sgs_problem& p) {
   if (p.inner_max < 0 || p.inner_fixed < 0 || p.newton_max < 1) return SGS_ERR_ARG;
   if (p.conserve_proj < 0 || p.conserve_proj > 2) return SGS_ERR_ARG;
   if (p.order < 0 || p.order > 2) return SGS_ERR_ARG;
-  if (p.order == 2 && p.space_dim == 2) return SGS_ERR_UNSUPPORTED;
   for (int s = 0; s < 2; s++) {
     if (p.bc[s].kind != SGS_DIFFUSE && p.bc[s].kind != SGS_INFLOW) return SGS_ERR_ARG;
     if (!(p.bc[s].T > 0.0)) return SGS_ERR_ARG;
@@ -470,7 +499,9 @@ struct Scope {
   int cls;
   cudaStream_t st;
   cudaEvent_t a = nullptr, b = nullptr;
-  Scope(sgs_handle* h_, int cls_, cudaStream_t st_, int n_launch) : h(h_), cls(cls_), st(st_) {
+  double work;
+  Scope(sgs_handle* h_, int cls_, cudaStream_t st_, int n_launch, double work_ = 0.0)
+      : h(h_), cls(cls_), st(st_), work(work_) {
     h->launches += n_launch;
     // launches captured into a CUDA graph are not timed: an event recorded during capture
     // becomes a graph node, not a timestamp
@@ -484,7 +515,7 @@ struct Scope {
   ~Scope() {
     if (a && b) {
       cudaEventRecord(b, st);
-      h->recs.push_back({cls, a, b});
+      h->recs.push_back({cls, a, b, work});
     }
   }
 };
@@ -508,12 +539,15 @@ AuxArgs aux_args(const sgs_handle* h, int l = 0) {
   return a;
 }
 
+// The collision step skips the cells of converged (inactive) instances of multi-instance
+// handles: their f no longer changes, so the Q and P of their last evaluation stay valid.
 CellTables cell_tables(const sgs_handle* h, int l = 0) {
   const auto& L = h->lev[l];
   CellTables ct;
   ct.inst = h->at<InstDev>(L.inst);
   ct.cell_off = h->at<long long>(L.cell_off);
   ct.cell_inst = h->at<int>(L.cell_inst);
+  ct.active = h->n_inst > 1 ? h->at<int>(h->off.active) : nullptr;
   return ct;
 }
 
@@ -567,6 +601,11 @@ CollideCtx<T> collide_ctx(const sgs_handle* h, int l = 0, int g_lo = 0, int g_hi
   x.sum.Gs = Gl;
   x.sum.cnt = h->at<Counters>(h->off.cnt);
   x.sum.spin_max = h->spin_max;
+  x.sb.cell_inst = x.ct.cell_inst;
+  x.sb.active = x.ct.active;
+  x.sum.cell_inst = x.ct.cell_inst;
+  x.sum.active = x.ct.active;
+  x.sum.C = x.C;
   x.red.row_k = h->at<int2>(h->off.row_k);
   x.red.row_start = h->at<int>(h->off.row_start);
   x.red.row_units = h->at<int>(h->off.row_units);
@@ -615,7 +654,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     {
-      Scope sc(h, precision == SGS_FP64 ? SGS_PROF_SUM_FP64 : SGS_PROF_SUM, st, 1);
+      Scope sc(h, precision == SGS_FP64 ? SGS_PROF_SUM_FP64 : SGS_PROF_SUM, st, 1, x.C);
       er = launch_spectral_sum(x, nullptr, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
@@ -638,7 +677,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     {
-      Scope sc(h, SGS_PROF_SUM, st, 1);
+      Scope sc(h, SGS_PROF_SUM, st, 1, x.C);
       er = launch_spectral_sum(x, nullptr, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
@@ -652,7 +691,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     {
-      Scope sc(h, SGS_PROF_SUM, st, 1);
+      Scope sc(h, SGS_PROF_SUM, st, 1, x.C);
       er = launch_spectral_sum(x, part2, st);
     }
     if (er != cudaSuccess) return cuda_status(er);
@@ -672,7 +711,7 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
     }
     if (er != cudaSuccess) return cuda_status(er);
     {
-      Scope sc(h, SGS_PROF_SUM_DF64, st, 1);
+      Scope sc(h, SGS_PROF_SUM_DF64, st, 1, x.C);
       SumDfArgs d;
       d.units = x.sum.units;
       d.unit_step0 = x.sum.unit_step0;
@@ -684,6 +723,9 @@ int collide_impl(sgs_handle* h, const double* f, double* Q, double* P, int preci
       d.G = x.sum.G;
       d.Gs = x.sum.Gs;
       d.cnt = x.sum.cnt;
+      d.cell_inst = x.sum.cell_inst;
+      d.active = x.sum.active;
+      d.C = x.sum.C;
       d.spin_max = x.sum.spin_max;
       er = launch_sum_df(d, h->H, x.n_units, st);
     }
@@ -724,7 +766,15 @@ int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int
     const InstDev& I = h->lev[l].hinst0;
     const int o = ordering >= 0 ? ordering : (dir > 0 ? 0 : 1);
     const int nwf = I.nx + I.ny - 1;
-    Scope sc(h, SGS_PROF_SWEEP, st, nwf);
+    Scope sc(h, SGS_PROF_SWEEP, st, nwf + (h->order2 ? 2 : 0), (double)I.nx * I.ny);
+    if (h->order2) {
+      // second order: the slope terms and the face-value wall correction of this ordering
+      // depend only on the state before it, so they join the right-hand side
+      double* b2 = h->at<double>(h->off.o2rhs);
+      cudaError_t e = launch_slope_rhs2d(aux_args(h, l), f, rhs, b2, st);
+      if (e != cudaSuccess) return cuda_status(e);
+      a.rhs = b2;
+    }
     for (int wf = 0; wf < nwf; wf++) {
       int ncells = std::min(I.nx - 1, wf) - std::max(0, wf - (I.ny - 1)) + 1;
       cudaError_t e = launch_sweep2d(a, h->sweep, h->sweep_arith, o, wf, ncells, st);
@@ -732,7 +782,10 @@ int sweep_impl(sgs_handle* h, double* f, const double* P, const double* rhs, int
     }
     return SGS_OK;
   }
-  Scope sc(h, SGS_PROF_SWEEP, st, h->order2 ? 3 : 1);
+  double visits = 0.0;  // cells this launch visits (inactive instances included)
+  for (const auto& I : h->lev[l].hinst.empty() ? h->inst : h->lev[l].hinst)
+    visits += std::max(0, std::min(s1, I.J) - s0);
+  Scope sc(h, SGS_PROF_SWEEP, st, h->order2 ? 3 : 1, visits);
   if (h->order2) {
     // second order: the explicit slope terms (and the face-value wall correction) of this
     // scan depend only on the state before it, so they join the right-hand side
@@ -789,11 +842,12 @@ int iterate_overlap(sgs_handle* h, double* f, double* Q, double* P, const double
   cudaStream_t ss = h->scan_st;
   int k = 0, r;
   cudaError_t e = cudaSuccess;
-  auto fork = [&](cudaStream_t from, cudaStream_t to) -> cudaEvent_t {
+  // `to` waits for everything enqueued on `from` so far (either may be the legacy default
+  // stream, whose handle is null)
+  auto fork = [&](cudaStream_t from, cudaStream_t to) {
     cudaEvent_t x = h->ov_ev[k++];
     if (e == cudaSuccess) e = cudaEventRecord(x, from);
-    if (e == cudaSuccess && to) e = cudaStreamWaitEvent(to, x, 0);
-    return x;
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, x, 0);
   };
   if (!(flags & SGS_IT_P_VALID) && (r = collide_impl(h, f, nullptr, P, prec, st))) return r;
   fork(st, ss);
@@ -802,7 +856,6 @@ int iterate_overlap(sgs_handle* h, double* f, double* Q, double* P, const double
     fork(ss, st);
     if ((r = collide_impl(h, f, nullptr, P, prec, st, 0, nullptr, g, g + 1))) return r;
   }
-  std::vector<cudaEvent_t> col(G);
   for (int g = G - 1; g >= 0 && e == cudaSuccess; g--) {
     // the collision steps of groups < G-1 were enqueued earlier on st; one event covers them
     if (g == G - 1) fork(st, ss);
@@ -956,6 +1009,51 @@ cudaError_t sgs::func_attr(const void* fn, cudaFuncAttribute attr, int value) {
 }
 
 namespace {
+
+// Uploads the work-unit tables of the current spectral-sum decomposition (synchronous).
+cudaError_t upload_sum_plan(sgs_handle* h) {
+  std::vector<int4> u4;
+  std::vector<long long> s0;
+  for (auto& x : h->units) {
+    u4.push_back(make_int4(x.k1, x.k2, x.m1lo, x.m1hi));
+    s0.push_back(x.step0);
+  }
+  cudaError_t e = cudaMemcpy(h->ws + h->off.units, u4.data(), sizeof(int4) * u4.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->ws + h->off.step0, s0.data(), sizeof(long long) * s0.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->ws + h->off.row_start, h->row_start.data(), sizeof(int) * h->row_start.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->ws + h->off.row_units, h->row_units.data(), sizeof(int) * h->row_units.size(),
+                   cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Times `reps` launches of the spectral sum of the handle's arithmetic over every group with
+// the current decomposition (CUDA events on st, after one untimed launch). The sums read the
+// transformed spectra in the workspace and write only the partial sums.
+int time_sum(sgs_handle* h, int reps, cudaStream_t st, float* ms) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return SGS_ERR_CUDA;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return SGS_ERR_CUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i <= reps && e == cudaSuccess; i++) {
+    if (i == 1) e = cudaEventRecord(a, st);
+    if (e != cudaSuccess) break;
+    e = h->precision == SGS_FP32 ? launch_spectral_sum(collide_ctx<float>(h), nullptr, st)
+                                 : launch_spectral_sum(collide_ctx<double>(h), nullptr, st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return cuda_status(e);
+}
 
 // Times `reps` forward + backward scans of the current launch shape (CUDA events on st).
 int time_sweeps(sgs_handle* h, double* f, const double* P, int reps, cudaStream_t st, float* ms) {
@@ -1394,6 +1492,44 @@ int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning
     if (r != SGS_OK) break;
   }
   h->sweep = r == SGS_OK ? best : start;
+  if (r != SGS_OK) {
+    h->prof = prof;
+    return r;
+  }
+  // spectral-sum decomposition: warps (lane groups) per block and block count
+  float sum_best = -1.0f;
+  int sum_tried = 0;
+  if (h->spectral) {
+    const int nw0 = h->NW, bl0 = h->sum_blocks;
+    int best_nw = nw0, best_bl = bl0;
+    for (int nw = 1; nw <= kSumMaxWarps && r == SGS_OK; nw *= 2) {
+      if (nw > 1 && (nw / 2) >= h->G) break;  // more warps than lane groups
+      for (int bl : kSumBlockChoices) {
+        plan_units(h, sum_target(h, nw, bl));
+        if ((int)h->units.size() > h->U_cap) continue;
+        h->NW = nw;
+        cudaError_t e = upload_sum_plan(h);
+        if (e != cudaSuccess) {
+          r = cuda_status(e);
+          break;
+        }
+        float ms = 0.0f;
+        r = time_sum(h, 2, st, &ms);
+        if (r != SGS_OK) break;
+        sum_tried++;
+        if (sum_best < 0.0f || ms < sum_best) {
+          sum_best = ms;
+          best_nw = nw;
+          best_bl = bl;
+        }
+      }
+    }
+    h->NW = best_nw;
+    h->sum_blocks = best_bl;
+    plan_units(h, sum_target(h, best_nw, best_bl));
+    cudaError_t e = upload_sum_plan(h);
+    if (r == SGS_OK && e != cudaSuccess) r = cuda_status(e);
+  }
   h->prof = prof;
   if (r != SGS_OK) return r;
   if (out) {
@@ -1405,6 +1541,8 @@ int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning
     out->sum_warps = h->NW;
     out->sum_units = (int)h->units.size();
     out->sum_blocks = (int)h->units.size() * ((h->G + h->NW - 1) / h->NW);
+    out->sum_ms = sum_best > 0.0f ? sum_best / 2 : 0.0f;
+    out->sum_candidates = sum_tried;
   }
   return SGS_OK;
 }
@@ -1476,11 +1614,12 @@ int sgs_profile(sgs_handle* h, int enable) {
   return SGS_OK;
 }
 
-int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, int n_classes) {
+int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, double* work, int n_classes) {
   if (!h || n_classes < 0) return SGS_ERR_ARG;
   for (int c = 0; c < n_classes; c++) {
     if (ms) ms[c] = 0.0;
     if (launches) launches[c] = 0;
+    if (work) work[c] = 0.0;
   }
   for (auto& rec : h->recs) {
     cudaError_t e = cudaEventSynchronize(rec.b);
@@ -1490,6 +1629,7 @@ int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, in
     if (rec.cls < n_classes) {
       if (ms) ms[rec.cls] += t;
       if (launches) launches[rec.cls] += 1;
+      if (work) work[rec.cls] += rec.work;
     }
     h->pool.push_back(rec.a);
     h->pool.push_back(rec.b);

@@ -184,3 +184,39 @@ def cavity_64x64_24v() -> CavityWorkload:
     """64 x 64 cells, 24^3 velocities on [-6, 6]^3, Maxwell molecules, eps = 0.05, lid speed
     0.5, walls at T = 1."""
     return CavityWorkload("cavity2d_64x64_N24_eps0.05", nx=64, ny=64, N=24, L=6.0, eps=0.05)
+
+
+@dataclass
+class CavityHeatWorkload:
+    """2-D heat transfer in a cavity with the BGK operator: the square (-1/2, 1/2)^2, all
+    walls at rest, the top wall (y = 1/2) at temperature T_top and the others at T_wall,
+    penalty frequency nu = 4 pi rho (b0 = 1), initial state M(1, 0, T_wall) in every cell."""
+
+    name: str
+    nx: int
+    ny: int
+    N: int
+    L: float
+    eps: float
+    T_wall: float = 1.0
+    T_top: float = 2.0
+    b0: float = 1.0
+    tol: float = 1e-5
+
+    @property
+    def J(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def total_mass(self) -> float:
+        return 1.0  # density 1 on the unit square
+
+    def initial_state(self) -> np.ndarray:
+        M = sampled_maxwellian(self.N, self.L, 1.0, (0.0, 0.0, 0.0), self.T_wall)
+        return np.ascontiguousarray(np.repeat(M[None], self.J, 0))
+
+
+def cavity_heat_bgk_40x40_20v(eps: float) -> CavityHeatWorkload:
+    """The BGK heat-transfer cavity of the paper's 2-D BGK example: 40 x 40 cells, 20^3
+    velocities on [-6, 6]^3, top wall at T = 2, the other walls at T = 1."""
+    return CavityHeatWorkload(f"cavity2d_heat_bgk_40x40_N20_eps{eps:g}", nx=40, ny=40, N=20, L=6.0, eps=eps)

@@ -69,6 +69,8 @@ class _Tuning(C.Structure):
         ("sum_warps", C.c_int),
         ("sum_units", C.c_int),
         ("sum_blocks", C.c_int),
+        ("sum_ms", C.c_float),
+        ("sum_candidates", C.c_int),
     ]
 
 
@@ -172,7 +174,8 @@ def lib(build: bool = True):
             "sgs_dc_clear": (C.c_int, [vp]),
             "sgs_set_dc_precision": (C.c_int, [vp, C.c_int]),
             "sgs_profile": (C.c_int, [vp, C.c_int]),
-            "sgs_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_ulonglong), C.c_int]),
+            "sgs_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_ulonglong), C.POINTER(C.c_double),
+                                           C.c_int]),
             "sgs_launch_count": (C.c_ulonglong, [vp]),
             "sgs_vcycle": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]),
             "sgs_max_levels": (C.c_int, [vp]),
@@ -328,10 +331,15 @@ class Solver:
     def profile(self, enable=True):
         _check(lib().sgs_profile(self.h, 1 if enable else 0), "sgs_profile")
 
-    def profile_read(self):
+    def profile_read(self, with_work=False):
+        """Per class: (milliseconds, bracketed launch groups), or with_work (ms, groups, cells
+        processed: evaluated by the sums, visited by the scans)."""
         ms = (C.c_double * PROF_CLASSES)()
         n = (C.c_ulonglong * PROF_CLASSES)()
-        _check(lib().sgs_profile_read(self.h, ms, n, PROF_CLASSES), "sgs_profile_read")
+        wk = (C.c_double * PROF_CLASSES)()
+        _check(lib().sgs_profile_read(self.h, ms, n, wk, PROF_CLASSES), "sgs_profile_read")
+        if with_work:
+            return {PROF_NAMES[i]: (float(ms[i]), int(n[i]), float(wk[i])) for i in range(PROF_CLASSES)}
         return {PROF_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(PROF_CLASSES)}
 
     def launch_count(self) -> int:
@@ -372,7 +380,7 @@ class Solver:
     def autotune(self, f, P, reps=1, stream=None) -> dict:
         t = _Tuning()
         _check(lib().sgs_autotune(self.h, _ptr(f), _ptr(P), reps, C.byref(t), _stream(stream)), "sgs_autotune")
-        return {k: (float(getattr(t, k)) if k == "sweep_ms" else int(getattr(t, k))) for k, _ in _Tuning._fields_}
+        return {k: (float(getattr(t, k)) if k.endswith("_ms") else int(getattr(t, k))) for k, _ in _Tuning._fields_}
 
     def read_status(self, stream=None) -> dict:
         st = _Stats()

@@ -74,8 +74,16 @@ def test_inactive_instance_is_frozen():
     assert not torch.equal(s.view(f, 2), s.view(before, 2))
     st = s.read_status()
     assert st["visits"] == 2 * (6 + 8)
+    # the collision step skips the frozen instance's cells: its Q and P stay as evaluated
+    Pf = s.view(P, 0).clone()
+    Q2, P2 = s.field(), s.field()
+    s.collide(f, Q2, P2)
+    assert torch.count_nonzero(s.view(Q2, 0)).item() == 0 and torch.count_nonzero(s.view(P2, 0)).item() == 0
+    assert torch.count_nonzero(s.view(Q2, 1)).item() > 0
     s.activate_all()
     assert s.read_active() == [1, 1, 1]
+    s.collide(f, Q2, P2)  # active again: evaluated, equal to its evaluation before freezing
+    assert rel(s.view(P2, 0).cpu().numpy(), Pf.cpu().numpy()) <= 1e-14
 
 
 def test_mixed_grid_batch_graph_replay_is_bitwise_eager():
@@ -136,6 +144,8 @@ def test_batch_converges_and_freezes_converged_problems():
 
 
 def test_autotuned_shape_keeps_oracle_parity(oracle):
+    """The scan shape and the spectral-sum decomposition the autotuner picks (and other valid
+    scan shapes) keep parity with the oracle."""
     N, J, L = 8, 5, 6.0
     d = dict(N=N, L=L, J=J, eps=0.1, bc_T=(1.0, 1.7), total_mass=1.0, inner_fixed=5)
     f0 = I.initial_state(J, N, L, T=1.4, seed=11)
@@ -150,6 +160,11 @@ def test_autotuned_shape_keeps_oracle_parity(oracle):
     t = s.autotune(scratch, P, reps=1)
     assert t["candidates"] >= 2 and t["sweep_ms"] > 0
     assert (t["sweep_ept"], t["sweep_cluster"], t["sweep_threads"]) == s.sweep_shape()
+    # the spectral-sum decomposition was tuned too; the collision step keeps oracle parity
+    assert t["sum_candidates"] >= 3 and t["sum_ms"] > 0 and t["sum_warps"] >= 1
+    Qg = s.field()
+    s.collide(torch.from_numpy(f0.reshape(-1)).cuda(), Qg, None)
+    assert rel(Qg.cpu().numpy().reshape(f0.shape), Qo) <= 1e-12
     for shape in (s.sweep_shape(), (2, 2, 160), (4, 1, 160)):
         s.set_sweep_shape(*shape)
         f = torch.from_numpy(f0.reshape(-1)).cuda()

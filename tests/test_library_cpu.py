@@ -51,11 +51,12 @@ def test_problem_validation_on_host(L):
         q = sgs.Problem(**bad)
         arr = (sgs._Problem * 1)(q.c())
         assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.ERR_ARG, bad
-    # the second-order scheme: 1-D only, one order per handle, not in the no-allocation residual
+    # the second-order scheme: one order per handle, not in the no-allocation residual
     arr = (sgs._Problem * 1)(sgs.Problem(order=3).c())
     assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.ERR_ARG
     arr = (sgs._Problem * 1)(sgs.Problem(space_dim=2, nx=4, ny=3, order=2).c())
-    assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.ERR_UNSUPPORTED
+    assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.OK  # 2-D second order
+    L.sgs_destroy(h)
     arr = (sgs._Problem * 2)(sgs.Problem().c(), sgs.Problem(order=2).c())
     assert L.sgs_setup(arr, 2, C.byref(h), C.byref(ws)) == sgs.ERR_UNSUPPORTED
     p2 = sgs.Problem(order=2).c()
