@@ -775,13 +775,13 @@ def run_batch(args, rank, world, local):
     prof = {}
     flops = 0.0
     for nv, s in b.solvers.items():
-        for k, (ms, n, cells) in s.profile_read(with_work=True).items():
+        for k, (ms, n, done) in s.profile_read(with_work=True).items():
             a = prof.setdefault(k, [0.0, 0])
             a[0] += ms
             a[1] += n
             if k == "sum":
                 # FP32 spectral sums: 10 flops per mode pair over the Hermitian half per cell
-                flops += 10 * 0.5 * pairs_per_cell(nv) * cells
+                flops += 10 * 0.5 * pairs_per_cell(nv) * done
         s.profile(False)
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
