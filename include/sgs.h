@@ -277,7 +277,8 @@ enum sgs_prof_class {
   SGS_PROF_RESCALE = 6,     /* mass rescale, grid transfers and other vector updates */
   SGS_PROF_SUM_FP64 = 7,    /* direct spectral sum, FP64 */
   SGS_PROF_SUM_DF64 = 8,    /* direct spectral sum, double-float */
-  SGS_PROF_CLASSES = 9
+  SGS_PROF_FAST = 9,        /* fast spectral operator: tensor-core passes and the final transform */
+  SGS_PROF_CLASSES = 10
 };
 int sgs_profile(sgs_handle* h, int enable);
 int sgs_profile_read(sgs_handle* h, double* ms, unsigned long long* launches, double* work, int n_classes);
@@ -338,9 +339,44 @@ int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning
  *     mode 0 a cluster reduction of seven values, mode 1 one Newton iteration of the
  *     discrete Maxwellian (evaluation, combination, factorisation). us_per_op = (time of reps
  *     operations - time of an empty launch) / reps in microseconds. Synchronises the stream. */
+/*   sgs_tc_selftest: check of the tensor-core path of the fast spectral operator (no
+ *     counterpart in the paper): D = A Bt^T for a 128 x K matrix A and an N x K matrix Bt of
+ *     seeded values in [-1, 1), split into BF16 terms (terms 1: hi only; terms 3: hi hi + lo hi
+ *     + hi lo), computed by tcgen05.mma with FP32 accumulation in TMEM and, from the same BF16
+ *     terms, on the CUDA cores. K in {16, 32, 48, 64}, N a multiple of 16 up to 128; swap
+ *     exchanges the two byte offsets of the operand descriptors. dev_scratch (device, at least
+ *     4 (128 K + N K + 256 N) + 256 bytes) holds the operands. max_err = max |D - Dref| (-1 if
+ *     the completion wait gave up), max_ref = max |Dref|. Synchronises the stream. */
+int sgs_tc_selftest(int K, int N, int terms, int swap, void* dev_scratch, size_t bytes, double* max_err,
+                    double* max_ref, void* stream);
 int sgs_peak_fma(int precision, long long iters, double* tflops, int* sms, float* ms, void* stream);
 int sgs_probe_scan(int nv, double v_max, int precision, int cluster, int threads, int mode, int reps,
                    float* us_per_op, void* stream);
+
+/* The fast (Carleman-form) Fourier spectral operator for hard spheres (the fast methods the
+ * paper cites for its binary-collision runs, Section 2.2): with both Carleman variables
+ * truncated at T = 2R, the gain is a sum over the nodes e_p of a half-sphere rule (m_theta
+ * Gauss-Legendre nodes in cos(theta) x m_phi azimuths) of products of the weighted spectra
+ * phi(k.e_p) fhat and Psi(|k - (k.e_p) e_p|) fhat, phi(s) = 2 int_0^T r cos(pi r s / L) dr,
+ * Psi(t) = 2 T L J1(pi T t / L) / t; the loss uses the same rule for beta(m, m). Each product
+ * is formed on a zero-padded P^3 grid (P = 32 for N <= 16, else 48: no wrap-around) through
+ * three separable DFT passes computed as tcgen05 matrix products (BF16 operands split from FP32,
+ * FP32 accumulation in TMEM; terms 3: hi hi + lo hi + hi lo, about 1e-4 relative on Q; terms
+ * 1: one BF16 product, about 2e-2), the node sum accumulated in FP32, the final transform to
+ * the modes |k_i| <= N/2 - 1 and to the velocity grid in FP64.
+ *   sgs_fast_setup: for a hard-sphere handle (SGS_ERR_UNSUPPORTED otherwise); the nodes are
+ *     processed `chunk` at a time (the workspace scales with chunk x cells); reports the
+ *     workspace size of the operator (its own, besides the handle's).
+ *   sgs_fast_bind: binds the caller's device buffer (256-byte aligned) and uploads the tables
+ *     (synchronous).
+ *   sgs_fast_collide: Q (device field of the handle) = the fast operator Q[f, f] of every cell
+ *     of f; uses the handle's transform buffers (same stream as the handle's other calls).
+ *     Asynchronous on the stream. */
+typedef struct sgs_fast sgs_fast;
+int sgs_fast_setup(const sgs_handle* h, int m_theta, int m_phi, int chunk, sgs_fast** out, size_t* workspace_bytes);
+int sgs_fast_bind(sgs_fast* x, void* device_ptr, size_t bytes);
+int sgs_fast_collide(sgs_fast* x, sgs_handle* h, const double* f, double* Q, int terms, void* stream);
+void sgs_fast_destroy(sgs_fast* x);
 
 /* Synchronises the stream and reads the accumulated status and counters. */
 int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream);

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsgs.so")
-SOURCES = ["sgs_api.cu", "collide.cu", "sweep.cu", "aux.cu", "noalloc.cu", "peaks.cu"]
+SOURCES = ["sgs_api.cu", "collide.cu", "sweep.cu", "aux.cu", "noalloc.cu", "peaks.cu", "fast.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1045,7 +1045,8 @@ cudaError_t launch_reduce_idft(const double* f, double* Q, double* P, const Coll
   cudaError_t e;
   RedArgs<T> ra = x.red;
   ra.partial2 = partial2;
-  k_sum_reduce<T><<<dim3(x.red.n_rows, x.red.G), 256, 0, st>>>(ra);
+  // n_rows = 0: qhat is already complete (the fast operator writes it directly)
+  if (x.red.n_rows > 0) k_sum_reduce<T><<<dim3(x.red.n_rows, x.red.G), 256, 0, st>>>(ra);
   size_t sm3 = dft_smem<T>(N, n * n, 0);
   e = func_attr((const void*)k_idft_k1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
   if (e != cudaSuccess) return e;

@@ -232,6 +232,33 @@ cudaError_t sweep_max_clusters(const SweepShape& sh, int arith, int* n);
 cudaError_t launch_sweep2d(const SweepArgs& a, const SweepShape& sh, int arith, int ordering, int wf, int ncells,
                            cudaStream_t st);
 cudaError_t launch_sweep(const SweepArgs& a, const SweepShape& sh, int arith, cudaStream_t st);
+// Fast (Carleman-form) spectral operator on the tensor cores (fast.cu): one chunk of S slots
+// (half-sphere nodes, the loss slot last) for every cell.
+struct FastArgs {
+  int n, npad, P, C, S;         // modes per dimension, padded K modes, grid, cells, slots of the chunk
+  int s0;                       // first global slot of the chunk
+  int terms;
+  const float* fhat;            // [C][n][npad][npad][2]
+  const float* wtab;            // [slots][2][n][npad][npad]
+  const float* wslot;           // [slots] weight of each slot's product
+  const float* bt12;            // [2P][2 npad]: passes 1 and 2
+  const float* bt3;             // [P][2 npad]: pass 3 (real part)
+  float* Y1;                    // [B][P][n][npad][2]
+  float* Y2;                    // [B][P][P][npad][2]
+  float* G;                     // [C][P][P][P]
+  long long spin_max;
+  unsigned int* status;         // TIMEOUT bit
+};
+
+cudaError_t launch_fast_fhat(const double2* ahat, const double2* bhat, int C, int n, int npad, float* out,
+                             cudaStream_t st);
+cudaError_t launch_fast_pass(int pass, const FastArgs& a, cudaStream_t st);
+cudaError_t launch_fast_final(const float* G, const double2* tw, int C, int n, int P, double2* T1, double2* T2,
+                              double2* qhat, cudaStream_t st);
+
+// Tensor-core self-test (fast.cu): D = A Bt^T on tcgen05 and on the CUDA cores.
+cudaError_t tc_selftest(const float* A, const float* Bt, float* D, float* Dref, int K, int N, int terms, int swap,
+                        int* err, cudaStream_t st);
 // Latency probe of the scan's building blocks in one cluster of the given shape: mode 0
 // cluster reductions, mode 1 Newton iterations of the discrete Maxwellian (reps of each).
 cudaError_t probe_scan(int N, double dv, int arith, int cluster, int threads, int mode, int reps, cudaStream_t st);

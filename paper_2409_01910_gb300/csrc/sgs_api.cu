@@ -1582,6 +1582,264 @@ int sgs_probe_scan(int nv, double v_max, int precision, int cluster, int threads
   return SGS_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// The fast (Carleman-form) spectral operator, hard spheres, on the tensor cores.
+// ---------------------------------------------------------------------------------------
+}  // extern "C"
+
+struct sgs_fast {
+  int N = 0, n = 0, h = 0, npad = 0, P = 0, C = 0, M = 0, slots = 0, chunk = 0;
+  double L = 0.0, b0 = 0.0;
+  std::vector<float> wtab, wslot, bt12, bt3;
+  std::vector<double2> tw;
+  struct {
+    size_t fhat, wtab, wslot, bt12, bt3, tw, Y1, Y2, G, T1, T2, end;
+  } off;
+  size_t ws_bytes = 0;
+  char* ws = nullptr;
+  template <typename T>
+  T* at(size_t o) const {
+    return reinterpret_cast<T*>(ws + o);
+  }
+};
+
+namespace {
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on the Legendre polynomial
+// from the Chebyshev-like initial guesses).
+void gauss_legendre(int m, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(m, 0.0);
+  w.assign(m, 0.0);
+  for (int i = 0; i < m; i++) {
+    double z = std::cos(kPi * (i + 0.75) / (m + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; it++) {
+      double p0 = 1.0, p1 = 0.0;
+      for (int j = 1; j <= m; j++) {
+        double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+      }
+      dp = m * (z * p0 - p1) / (z * z - 1.0);
+      double dz = p0 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// The radial factors of the Carleman weights with both variables truncated at T:
+// phi(s) = 2 int_0^T rho cos(pi rho s / L) drho, psi(t) = 2 pi int_0^T rho J0(pi rho t / L) drho.
+double fast_phi(double s, double T, double L) {
+  const double a = kPi * s / L;
+  if (std::fabs(a) <= 1e-12) return T * T;
+  return 2.0 * (T * std::sin(a * T) / a + (std::cos(a * T) - 1.0) / (a * a));
+}
+double fast_psi(double t, double T, double L) {
+  if (t <= 1e-12) return kPi * T * T;
+  return 2.0 * T * L * std::cyl_bessel_j(1.0, kPi * T * t / L) / t;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sgs_fast_setup(const sgs_handle* h, int m_theta, int m_phi, int chunk, sgs_fast** out, size_t* workspace_bytes) {
+  if (!h || !out || m_theta < 1 || m_phi < 1 || chunk < 1 || m_theta * m_phi > 4096) return SGS_ERR_ARG;
+  *out = nullptr;
+  if (!h->spectral || h->prob[0].collision != SGS_HARD_SPHERE) return SGS_ERR_UNSUPPORTED;
+  sgs_fast* x = new (std::nothrow) sgs_fast();
+  if (!x) return SGS_ERR_NOMEM;
+  x->N = h->N;
+  x->n = h->n;
+  x->h = h->H;
+  x->npad = x->n <= 16 ? 16 : 32;
+  x->P = 3 * x->h + 1 <= 32 ? 32 : 48;  // zero padding that keeps the linear convolutions free of wrap-around
+  x->C = h->C;
+  x->M = m_theta * m_phi;
+  x->slots = x->M + 1;  // the nodes, then the loss term
+  x->chunk = std::min(chunk, x->slots);
+  x->L = h->L;
+  x->b0 = h->prob[0].b0;
+  const int n = x->n, np = x->npad, P = x->P, H = x->h;
+  const double R = 2.0 * x->L / (3.0 * std::sqrt(2.0) + 1.0), T = 2.0 * R;
+  // half-sphere rule: Gauss-Legendre in cos(theta) on [0, 1], uniform azimuths
+  std::vector<double> gx, gw;
+  gauss_legendre(m_theta, gx, gw);
+  std::vector<double> e(3 * x->M), wp(x->M);
+  for (int i = 0; i < m_theta; i++)
+    for (int j = 0; j < m_phi; j++) {
+      const double mu = 0.5 * (gx[i] + 1.0), st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+      const double az = 2.0 * kPi * j / m_phi;
+      const int p = i * m_phi + j;
+      e[3 * p] = st * std::cos(az);
+      e[3 * p + 1] = st * std::sin(az);
+      e[3 * p + 2] = mu;
+      wp[p] = 0.5 * gw[i] * 2.0 * kPi / m_phi;
+    }
+  const size_t per = (size_t)n * np * np;
+  x->wtab.assign((size_t)x->slots * 2 * per, 0.0f);
+  x->wslot.assign(x->slots, 0.0f);
+  std::vector<double> bmm((size_t)n * n * n, 0.0);
+  for (int p = 0; p < x->M; p++) {
+    float* wa = &x->wtab[((size_t)p * 2) * per];
+    float* wb = wa + per;
+    for (int k1 = 0; k1 < n; k1++)
+      for (int k2 = 0; k2 < n; k2++)
+        for (int k3 = 0; k3 < n; k3++) {
+          const double kv[3] = {(double)(k1 - H), (double)(k2 - H), (double)(k3 - H)};
+          const double ke = kv[0] * e[3 * p] + kv[1] * e[3 * p + 1] + kv[2] * e[3 * p + 2];
+          const double kk = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+          const double ph = fast_phi(ke, T, x->L), ps = fast_psi(std::sqrt(std::max(kk - ke * ke, 0.0)), T, x->L);
+          const size_t o = ((size_t)k1 * np + k2) * np + k3;
+          wa[o] = (float)ph;
+          wb[o] = (float)ps;
+          bmm[((size_t)k1 * n + k2) * n + k3] += wp[p] * ph * ps;
+        }
+    x->wslot[p] = (float)(4.0 * x->b0 * wp[p]);
+  }
+  {  // the loss term: -fhat * (beta(m, m) fhat) as the last slot
+    float* wa = &x->wtab[((size_t)x->M * 2) * per];
+    float* wb = wa + per;
+    for (int k1 = 0; k1 < n; k1++)
+      for (int k2 = 0; k2 < n; k2++)
+        for (int k3 = 0; k3 < n; k3++) {
+          const size_t o = ((size_t)k1 * np + k2) * np + k3;
+          wa[o] = 1.0f;
+          wb[o] = (float)(4.0 * x->b0 * bmm[((size_t)k1 * n + k2) * n + k3]);
+        }
+    x->wslot[x->M] = -1.0f;
+  }
+  // DFT matrices E[x, k] = exp(2 pi i x (k - h) / P) as real 2 x 2 blocks, K index 2 k + (re, im)
+  x->bt12.assign((size_t)2 * P * 2 * np, 0.0f);
+  x->bt3.assign((size_t)P * 2 * np, 0.0f);
+  for (int xx = 0; xx < P; xx++)
+    for (int k = 0; k < n; k++) {
+      const double ang = 2.0 * kPi * (double)(((long long)xx * (k - H)) % P) / P;
+      const float er = (float)std::cos(ang), ei = (float)std::sin(ang);
+      float* r0 = &x->bt12[(size_t)(2 * xx) * 2 * np];
+      float* r1 = &x->bt12[(size_t)(2 * xx + 1) * 2 * np];
+      r0[2 * k] = er;
+      r0[2 * k + 1] = -ei;
+      r1[2 * k] = ei;
+      r1[2 * k + 1] = er;
+      float* r3 = &x->bt3[(size_t)xx * 2 * np];
+      r3[2 * k] = er;
+      r3[2 * k + 1] = -ei;
+    }
+  x->tw.resize((size_t)n * P);
+  for (int k = 0; k < n; k++)
+    for (int xx = 0; xx < P; xx++) {
+      const double ang = -2.0 * kPi * (double)(((long long)xx * (k - H)) % P) / P;
+      x->tw[(size_t)k * P + xx] = make_double2(std::cos(ang), std::sin(ang));
+    }
+  // workspace
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  const size_t Bc = (size_t)x->C * x->chunk * 2;
+  x->off.fhat = take(sizeof(float) * x->C * per * 2);
+  x->off.wtab = take(sizeof(float) * x->wtab.size());
+  x->off.wslot = take(sizeof(float) * x->wslot.size());
+  x->off.bt12 = take(sizeof(float) * x->bt12.size());
+  x->off.bt3 = take(sizeof(float) * x->bt3.size());
+  x->off.tw = take(sizeof(double2) * x->tw.size());
+  x->off.Y1 = take(sizeof(float) * Bc * P * n * np * 2);
+  x->off.Y2 = take(sizeof(float) * Bc * P * P * np * 2);
+  x->off.G = take(sizeof(float) * (size_t)x->C * P * P * P);
+  x->off.T1 = take(sizeof(double2) * (size_t)x->C * P * P * n);
+  x->off.T2 = take(sizeof(double2) * (size_t)x->C * P * n * n);
+  x->off.end = o;
+  x->ws_bytes = o;
+  *out = x;
+  if (workspace_bytes) *workspace_bytes = o;
+  return SGS_OK;
+}
+
+int sgs_fast_bind(sgs_fast* x, void* device_ptr, size_t bytes) {
+  if (!x || !device_ptr) return SGS_ERR_ARG;
+  if (bytes < x->ws_bytes) return SGS_ERR_WORKSPACE;
+  if (((uintptr_t)device_ptr) % kAlign) return SGS_ERR_ARG;
+  x->ws = (char*)device_ptr;
+  cudaError_t e = cudaMemcpy(x->ws + x->off.wtab, x->wtab.data(), sizeof(float) * x->wtab.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(x->ws + x->off.wslot, x->wslot.data(), sizeof(float) * x->wslot.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(x->ws + x->off.bt12, x->bt12.data(), sizeof(float) * x->bt12.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(x->ws + x->off.bt3, x->bt3.data(), sizeof(float) * x->bt3.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(x->ws + x->off.tw, x->tw.data(), sizeof(double2) * x->tw.size(), cudaMemcpyHostToDevice);
+  // the padded entries of the pass-2 output (k1 >= n) are never written: zero them once
+  if (e == cudaSuccess) e = cudaMemset(x->ws + x->off.Y2, 0, x->off.G - x->off.Y2);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return cuda_status(e);
+}
+
+int sgs_fast_collide(sgs_fast* x, sgs_handle* h, const double* f, double* Q, int terms, void* stream) {
+  if (!x || !h || !f || !Q || (terms != 1 && terms != 3)) return SGS_ERR_ARG;
+  if (!x->ws || !h->ws) return SGS_ERR_WORKSPACE;
+  if (x->N != h->N || x->C != h->C || x->L != h->L) return SGS_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  // moments and discrete Maxwellians (the transforms of f - M and f + M give fhat)
+  CollideCtx<double> cx = collide_ctx<double>(h);
+  cudaError_t e;
+  {
+    Scope sc(h, SGS_PROF_MOMENTS, st, 1);
+    const sgs_problem& p0 = h->prob[0];
+    e = launch_moments(f, cx.ct, h->C, h->N, h->dv, p0.newton_tol, p0.newton_max, h->at<double>(h->off.theta),
+                       h->at<double>(h->off.nu), h->at<Counters>(h->off.cnt), st);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  {
+    Scope sc(h, SGS_PROF_DFT, st, 5);
+    e = launch_dft(f, cx, DftMode{0, nullptr, nullptr}, st);
+    if (e == cudaSuccess)
+      e = launch_fast_fhat(cx.sb.ahat, cx.sb.bhat, x->C, x->n, x->npad, x->at<float>(x->off.fhat), st);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  {
+    Scope sc(h, SGS_PROF_FAST, st, 3 * ((x->slots + x->chunk - 1) / x->chunk) + 4, (double)x->C);
+    e = cudaMemsetAsync(x->ws + x->off.G, 0, sizeof(float) * (size_t)x->C * x->P * x->P * x->P, st);
+    FastArgs a;
+    a.n = x->n;
+    a.npad = x->npad;
+    a.P = x->P;
+    a.C = x->C;
+    a.terms = terms;
+    a.fhat = x->at<float>(x->off.fhat);
+    a.wtab = x->at<float>(x->off.wtab);
+    a.wslot = x->at<float>(x->off.wslot);
+    a.bt12 = x->at<float>(x->off.bt12);
+    a.bt3 = x->at<float>(x->off.bt3);
+    a.Y1 = x->at<float>(x->off.Y1);
+    a.Y2 = x->at<float>(x->off.Y2);
+    a.G = x->at<float>(x->off.G);
+    a.spin_max = h->spin_max;
+    a.status = &h->at<Counters>(h->off.cnt)[0].status;
+    for (int s0 = 0; s0 < x->slots && e == cudaSuccess; s0 += x->chunk) {
+      a.s0 = s0;
+      a.S = std::min(x->chunk, x->slots - s0);
+      for (int pass = 1; pass <= 3 && e == cudaSuccess; pass++) e = launch_fast_pass(pass, a, st);
+    }
+    if (e == cudaSuccess)
+      e = launch_fast_final(a.G, x->at<double2>(x->off.tw), x->C, x->n, x->P, x->at<double2>(x->off.T1),
+                            x->at<double2>(x->off.T2), cx.sb.qhat, st);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  // inverse transform of the modes to the velocity grid (no partial sums to reduce)
+  Scope sc(h, SGS_PROF_REDUCE_IDFT, st, 3);
+  cx.red.n_rows = 0;
+  cx.mom = nullptr;
+  return cuda_status(launch_reduce_idft(f, Q, nullptr, cx, nullptr, nullptr, st));
+}
+
+void sgs_fast_destroy(sgs_fast* x) { delete x; }
+
 int sgs_read_status(sgs_handle* h, sgs_stats* out, void* stream) {
   if (!h || !out) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;

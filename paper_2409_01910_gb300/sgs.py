@@ -23,7 +23,7 @@ DIFFUSE, INFLOW = 0, 1
 FP64, FP32, DF64 = 0, 1, 2
 PFP, FP, PFP_RELAX = 0, 1, 2
 IT_P_VALID, IT_EVAL = 1, 2
-PROF_NAMES = ("moments", "dft", "sum", "reduce_idft", "sweep", "residual", "rescale", "sum_fp64", "sum_df64")
+PROF_NAMES = ("moments", "dft", "sum", "reduce_idft", "sweep", "residual", "rescale", "sum_fp64", "sum_df64", "fast")
 PROF_CLASSES = len(PROF_NAMES)
 
 
@@ -197,6 +197,12 @@ def lib(build: bool = True):
                                        C.POINTER(C.c_float), vp]),
             "sgs_probe_scan": (C.c_int, [C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                          C.POINTER(C.c_float), vp]),
+            "sgs_fast_setup": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.POINTER(vp), C.POINTER(C.c_size_t)]),
+            "sgs_fast_bind": (C.c_int, [vp, vp, C.c_size_t]),
+            "sgs_fast_collide": (C.c_int, [vp, vp, vp, vp, C.c_int, vp]),
+            "sgs_fast_destroy": (None, [vp]),
+            "sgs_tc_selftest": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_size_t, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -234,6 +240,18 @@ def probe_scan(nv, v_max, precision, cluster, threads, mode, reps=2000, stream=N
     _check(lib().sgs_probe_scan(nv, v_max, precision, cluster, threads, mode, reps, C.byref(us), _stream(stream)),
            "sgs_probe_scan")
     return float(us.value)
+
+
+def tc_selftest(K, N, terms=3, swap=0, stream=None):
+    """Tensor-core check: (max |D_tcgen05 - D_cuda_cores|, max |D|) for a 128 x K by K x N
+    product of seeded BF16-split values."""
+    import torch
+
+    scratch = torch.empty(4 * (128 * K + N * K + 256 * N) + 1024, dtype=torch.uint8, device="cuda")
+    me, mr = C.c_double(), C.c_double()
+    _check(lib().sgs_tc_selftest(K, N, terms, swap, scratch.data_ptr(), scratch.numel(), C.byref(me), C.byref(mr),
+                                 _stream(stream)), "sgs_tc_selftest")
+    return float(me.value), float(mr.value)
 
 
 def _ptr(t) -> Optional[int]:
@@ -393,6 +411,37 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             lib().sgs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FastOperator:
+    """The fast (Carleman-form) spectral operator of a hard-sphere Solver on the tensor cores:
+    Q[f, f] of every cell (see sgs_fast_collide)."""
+
+    def __init__(self, solver: "Solver", m_theta: int = 8, m_phi: int = 16, chunk: int = 8):
+        import torch
+
+        h = C.c_void_p()
+        ws = C.c_size_t()
+        _check(lib().sgs_fast_setup(solver.h, m_theta, m_phi, chunk, C.byref(h), C.byref(ws)), "sgs_fast_setup")
+        self.h = h
+        self.solver = solver
+        self.workspace = torch.empty(max(int(ws.value), 256), dtype=torch.uint8, device=solver.device)
+        _check(lib().sgs_fast_bind(self.h, self.workspace.data_ptr(), self.workspace.numel()), "sgs_fast_bind")
+
+    def collide(self, f, Q, terms: int = 3, stream=None):
+        _check(lib().sgs_fast_collide(self.h, self.solver.h, _ptr(f), _ptr(Q), terms, _stream(stream)),
+               "sgs_fast_collide")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sgs_fast_destroy(self.h)
             self.h = None
 
     def __del__(self):
