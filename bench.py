@@ -80,7 +80,7 @@ def parse():
                     help="spatial order of the 1-D scheme (2: linear reconstruction, eq. (slope))")
     ap.add_argument("--pin-mass", action="store_true",
                     help="shock: hold the total mass at the initial state's (eq. (32) rescale), pinning the shock")
-    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d", "dft", "peaks", "steps"],
+    ap.add_argument("--case", choices=["sweep", "sum", "sum64", "sumdf", "sweep2d", "dft", "peaks", "steps", "fast"],
                     default=None,
                     help="run a small case of one kernel class (for profiler captures) and exit")
     return ap.parse_args()
@@ -948,6 +948,19 @@ def profile_case(which):
     from paper_2409_01910_gb300 import inputs as I
     from paper_2409_01910_gb300 import sgs
 
+    if which == "fast":
+        # the fast spectral operator (hard spheres, tensor cores) on 64 cells of the shock's
+        # 32^3 grid on [-10, 10]^3: one evaluation after a warm-up one
+        J, N, L = 64, 32, 10.0
+        s = sgs.Solver(sgs.Problem(nx=J, nv=N, v_max=L, collision=sgs.HARD_SPHERE, eps=0.1))
+        fast = sgs.FastOperator(s, 8, 16, chunk=8)
+        f = torch.from_numpy(I.initial_state(J, N, L, T=1.5).reshape(-1)).cuda()
+        Q = s.field()
+        for _ in range(2):
+            fast.collide(f, Q, terms=3)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": which, "status": s.read_status()}))
+        return
     if which == "steps":
         # the benchmark's step on the 64-cell heat workload: one defect-correction evaluation,
         # then three pipelined SGS iterations with their evaluation (the launch list's case)

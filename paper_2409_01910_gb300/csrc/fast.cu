@@ -126,13 +126,42 @@ __global__ void __launch_bounds__(kTcRows) k_tc_selftest(const float* __restrict
 // memory (terms 3: hi hi + lo hi + hi lo; terms 1: hi hi), accumulated in FP32 in TMEM.
 // ---------------------------------------------------------------------------------------
 
-// Loads rows of an operand into the two BF16 tiles (hi, lo) of K-major shared memory.
-__device__ inline void put_row(uint16_t* hi, uint16_t* lo, int row, int K, int k, float x, int terms) {
-  uint16_t h, l;
-  tc::split_bf16(x, h, l);
+// Four consecutive values (k % 4 == 0) of one row: one 8-byte shared store per BF16 tile.
+__device__ inline void put4(uint16_t* hi, uint16_t* lo, int row, int k, int K, float4 v, int terms) {
+  uint16_t h[4], l[4];
+  tc::split_bf16(v.x, h[0], l[0]);
+  tc::split_bf16(v.y, h[1], l[1]);
+  tc::split_bf16(v.z, h[2], l[2]);
+  tc::split_bf16(v.w, h[3], l[3]);
   const uint32_t o = tc::kmajor_offset(row, k, K) / 2;
-  hi[o] = h;
-  if (terms == 3) lo[o] = l;
+  *reinterpret_cast<uint2*>(hi + o) =
+      make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16));
+  if (terms == 3)
+    *reinterpret_cast<uint2*>(lo + o) =
+        make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16), (uint32_t)l[2] | ((uint32_t)l[3] << 16));
+}
+
+// A contiguous tile of ROWS rows x K floats (rows from `valid` on read as zero) into the BF16
+// hi / lo tiles: 16-byte loads, eight in flight per thread before they are converted.
+template <int K, int ROWS>
+__device__ inline void load_tile(const float* __restrict__ src, int valid, uint16_t* hi, uint16_t* lo, int terms) {
+  static_assert(ROWS % 8 == 0 && K % 8 == 0, "whole core matrices");
+  constexpr int kChunks = ROWS * K / 4;
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll 1
+  for (int c0 = threadIdx.x; c0 < kChunks; c0 += kTcRows * 8) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int c = c0 + u * kTcRows;
+      v[u] = c < kChunks && (c * 4) / K < valid ? s4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int c = c0 + u * kTcRows;
+      if (c < kChunks) put4(hi, lo, (c * 4) / K, (c * 4) % K, K, v[u], terms);
+    }
+  }
 }
 
 // Issues the MMAs of one product (K / 16 steps, 1 or 3 terms) into TMEM column `col`.
@@ -164,15 +193,16 @@ __device__ inline bool wait_mma(uint64_t* bar, uint32_t par, const FastArgs& a) 
   return ok;
 }
 
-template <int PASS>
+// NP: padded mode count along K (16 or 32, K = 2 NP); PP: the padded grid P (32 or 48).
+template <int PASS, int NP, int PP>
 __global__ void __launch_bounds__(kTcRows) k_fast_pass(FastArgs a) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  const int K = 2 * a.npad, P = a.P, n = a.n, np = a.npad;
-  const int NB = PASS == 3 ? P : 2 * P;          // columns of one product
-  const int nA = PASS == 3 ? 2 : 1;              // A operands per tile (pass 3: a = 0 and a = 1)
+  constexpr int K = 2 * NP, P = PP, np = NP;
+  constexpr int NB = PASS == 3 ? P : 2 * P;  // columns of one product
+  const int n = a.n;
   uint16_t* Bhi = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Blo = Bhi + NB * K;
-  uint16_t* Abuf = Blo + NB * K;                 // [nA][hi, lo][128][K]
+  uint16_t* Abuf = Blo + NB * K;              // [nA][hi, lo][128][K]
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tslot;
   const int t = threadIdx.x, warp = t >> 5;
@@ -181,9 +211,8 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass(FastArgs a) {
     mbar_init(&bar, 1);
     fence_mbar_init();
   }
-  // the DFT matrix of this pass, split once per CTA
-  const float* bt = PASS == 3 ? a.bt3 : a.bt12;
-  for (int i = t; i < NB * K; i += kTcRows) put_row(Bhi, Blo, i / K, K, i % K, bt[i], 3);
+  // the DFT matrix of this pass (NB rows of K floats, contiguous), split once per CTA
+  load_tile<K, NB>(PASS == 3 ? a.bt3 : a.bt12, NB, Bhi, Blo, 3);
   const int B = a.C * a.S * 2;
   long long rows;
   if (PASS == 1) rows = (long long)B * n * np;
@@ -205,6 +234,8 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass(FastArgs a) {
       uint16_t* Ahi = Abuf;
       uint16_t* Alo = Abuf + kTcRows * K;
       if (PASS == 1) {
+        // row (b, k1, k2): the weights of slot s and side ab times the cell's spectrum,
+        // both rows contiguous; every load of the row is issued before the first use
         int b = 0, k1 = 0, k2 = 0;
         if (live) {
           b = (int)(r / (n * np));
@@ -213,22 +244,24 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass(FastArgs a) {
           k2 = rem % np;
         }
         const int ab = b & 1, sl = (b >> 1) % a.S, c = (b >> 1) / a.S;
-        const float* fr = a.fhat + (((long long)c * n + k1) * np + k2) * np * 2;
-        const float* wr = a.wtab + ((((long long)(a.s0 + sl) * 2 + ab) * n + k1) * np + k2) * np;
-        for (int k3 = 0; k3 < np; k3++) {
-          const float w = live ? wr[k3] : 0.0f;
-          const float xr = live ? w * fr[2 * k3] : 0.0f, xi = live ? w * fr[2 * k3 + 1] : 0.0f;
-          put_row(Ahi, Alo, t, K, 2 * k3, xr, a.terms);
-          put_row(Ahi, Alo, t, K, 2 * k3 + 1, xi, a.terms);
+        const float4* fr = reinterpret_cast<const float4*>(a.fhat + (((long long)c * n + k1) * np + k2) * np * 2);
+        const float4* wr =
+            reinterpret_cast<const float4*>(a.wtab + ((((long long)(a.s0 + sl) * 2 + ab) * n + k1) * np + k2) * np);
+        float4 fv[NP / 2], wv[NP / 4];
+#pragma unroll
+        for (int i = 0; i < NP / 2; i++) fv[i] = live ? fr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < NP / 4; i++) wv[i] = live ? wr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < NP / 2; i++) {  // K elements 4 i .. 4 i + 3: modes k3 = 2 i, 2 i + 1
+          const float4 w4 = wv[i / 2];
+          const float w0 = (i & 1) ? w4.z : w4.x, w1 = (i & 1) ? w4.w : w4.y;
+          put4(Ahi, Alo, t, 4 * i, K, make_float4(w0 * fv[i].x, w0 * fv[i].y, w1 * fv[i].z, w1 * fv[i].w), a.terms);
         }
       } else {
-        // rows of Y1 are consecutive blocks of K floats: one coalesced sweep over the tile
-        const long long base = tile * kTcRows * K;
-        for (int i = t; i < kTcRows * K; i += kTcRows) {
-          const int row = i / K, k = i % K;
-          const float x = tile * kTcRows + row < rows ? a.Y1[base + i] : 0.0f;
-          put_row(Ahi, Alo, row, K, k, x, a.terms);
-        }
+        // rows of Y1 are consecutive blocks of K floats
+        load_tile<K, kTcRows>(a.Y1 + tile * kTcRows * K, (int)(rows - tile * kTcRows < kTcRows ? rows - tile * kTcRows : kTcRows), Ahi, Alo,
+                     a.terms);
       }
       tc::fence_async_smem();
       tc::fence_before_sync();
@@ -270,16 +303,15 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass(FastArgs a) {
       // ---- pass 3: rows (c, x2, x3) of one cell (P^2 is a multiple of 128)
       const int c = (int)(tile * kTcRows / ((long long)P * P));
       const int row0 = (int)(tile * kTcRows % ((long long)P * P));
-      float g[48];
+      float g[P];
 #pragma unroll
-      for (int i = 0; i < 48; i++) g[i] = 0.0f;
+      for (int i = 0; i < P; i++) g[i] = 0.0f;
       for (int sl = 0; sl < a.S && ok; sl++) {
         for (int ab = 0; ab < 2; ab++) {
           uint16_t* Ahi = Abuf + (size_t)ab * 2 * kTcRows * K;
           uint16_t* Alo = Ahi + kTcRows * K;
           const long long b = ((long long)c * a.S + sl) * 2 + ab;
-          const float* src = a.Y2 + (b * P * P + row0) * K;
-          for (int i = t; i < kTcRows * K; i += kTcRows) put_row(Ahi, Alo, i / K, K, i % K, src[i], a.terms);
+          load_tile<K, kTcRows>(a.Y2 + (b * P * P + row0) * K, kTcRows, Ahi, Alo, a.terms);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -297,22 +329,28 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass(FastArgs a) {
         phase ^= 1u;
         if (!ok) break;
         const float ws = a.wslot[a.s0 + sl];
+#pragma unroll
         for (int c0 = 0; c0 < P; c0 += 16) {
           float va[16], vb[16];
           tc::tmem_ld16(taddr + lane_base + (uint32_t)c0, va);
           tc::tmem_ld16(taddr + lane_base + (uint32_t)(P + c0), vb);
 #pragma unroll
-          for (int i = 0; i < 16; i++)
-            if (c0 + i < 48) g[c0 + i] = fmaf(ws * va[i], vb[i], g[c0 + i]);
+          for (int i = 0; i < 16; i++) g[c0 + i] = fmaf(ws * va[i], vb[i], g[c0 + i]);
         }
         tc::fence_before_sync();
         __syncthreads();
       }
       if (ok && live) {
-        float* o = a.G + ((long long)c * P * P + row0 + t) * P;
+        float4* o = reinterpret_cast<float4*>(a.G + ((long long)c * P * P + row0 + t) * P);
 #pragma unroll
-        for (int i = 0; i < 48; i++)
-          if (i < P) o[i] += g[i];
+        for (int i = 0; i < P / 4; i++) {
+          float4 v = o[i];
+          v.x += g[4 * i];
+          v.y += g[4 * i + 1];
+          v.z += g[4 * i + 2];
+          v.w += g[4 * i + 3];
+          o[i] = v;
+        }
       }
     }
   }
@@ -403,32 +441,39 @@ cudaError_t launch_fast_fhat(const double2* ahat, const double2* bhat, int C, in
   return cudaGetLastError();
 }
 
-template <int PASS>
+template <int PASS, int NP, int PP>
 static cudaError_t launch_pass_t(const FastArgs& a, cudaStream_t st) {
-  const int K = 2 * a.npad, NB = PASS == 3 ? a.P : 2 * a.P, nA = PASS == 3 ? 2 : 1;
-  const size_t smem = (size_t)2 * NB * K * sizeof(uint16_t) + (size_t)nA * 2 * kTcRows * K * sizeof(uint16_t);
-  cudaError_t e = func_attr((const void*)k_fast_pass<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr int K = 2 * NP, NB = PASS == 3 ? PP : 2 * PP, nA = PASS == 3 ? 2 : 1;
+  constexpr size_t smem = (size_t)2 * NB * K * sizeof(uint16_t) + (size_t)nA * 2 * kTcRows * K * sizeof(uint16_t);
+  auto kern = k_fast_pass<PASS, NP, PP>;
+  cudaError_t e = func_attr((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long B = (long long)a.C * a.S * 2;
-  long long rows = PASS == 1 ? B * a.n * a.npad : (PASS == 2 ? B * a.P * a.n : (long long)a.C * a.P * a.P);
+  long long rows = PASS == 1 ? B * a.n * NP : (PASS == 2 ? B * PP * a.n : (long long)a.C * PP * PP);
   const long long tiles = (rows + kTcRows - 1) / kTcRows;
   int dev = 0, sms = 0, per = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fast_pass<PASS>, kTcRows, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTcRows, smem);
   if (e != cudaSuccess) return e;
   per = std::max(1, std::min(per, 4));  // 128 TMEM columns per CTA: at most 4 CTAs share an SM's 512
   const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sms * per));
-  k_fast_pass<PASS><<<grid, kTcRows, smem, st>>>(a);
+  kern<<<grid, kTcRows, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+template <int PASS>
+static cudaError_t launch_pass_p(const FastArgs& a, cudaStream_t st) {
+  if (a.npad == 16 && a.P == 32) return launch_pass_t<PASS, 16, 32>(a, st);
+  if (a.npad == 32 && a.P == 32) return launch_pass_t<PASS, 32, 32>(a, st);
+  if (a.npad == 32 && a.P == 48) return launch_pass_t<PASS, 32, 48>(a, st);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_fast_pass(int pass, const FastArgs& a, cudaStream_t st) {
-  if (a.P != 32 && a.P != 48) return cudaErrorInvalidValue;
-  if (a.npad != 16 && a.npad != 32) return cudaErrorInvalidValue;
-  if (pass == 1) return launch_pass_t<1>(a, st);
-  if (pass == 2) return launch_pass_t<2>(a, st);
-  if (pass == 3) return launch_pass_t<3>(a, st);
+  if (pass == 1) return launch_pass_p<1>(a, st);
+  if (pass == 2) return launch_pass_p<2>(a, st);
+  if (pass == 3) return launch_pass_p<3>(a, st);
   return cudaErrorInvalidValue;
 }
 
