@@ -439,12 +439,15 @@ def measure_peaks(wl, shape, local=0):
         while time.perf_counter() < t_end:  # about a second of FFMA load for the clock samples
             fp32.append(sgs.peak_fma(sgs.FP32, iters=1 << 20))
     fp64 = max((sgs.peak_fma(sgs.FP64, iters=1 << 14) for _ in range(3)), key=lambda x: x["tflops"])
+    packed = max((sgs.peak_fma(sgs.FP32 | sgs.PEAK_PACKED, iters=1 << 19) for _ in range(3)),
+                 key=lambda x: x["tflops"])
     best32 = max(fp32, key=lambda x: x["tflops"])
     ept, cluster, threads = shape
     precision = sgs.FP32  # the mixed solver's scans run in double-float
     red = sgs.probe_scan(wl.N, wl.L, precision, cluster, threads, 0, reps=4000)
     newt = sgs.probe_scan(wl.N, wl.L, precision, cluster, threads, 1, reps=4000)
     return {"fp32_ffma_tflops": round(best32["tflops"], 3), "fp64_dfma_tflops": round(fp64["tflops"], 4),
+            "fp32_packed_ffma2_tflops": round(packed["tflops"], 3),
             "sms": best32["sms"], "sm_mhz_during_probe": clk.summary().get("sm_mhz"),
             "scan_cluster_reduce_us": round(red, 3), "scan_newton_iteration_us": round(newt, 3),
             "scan_probe_shape": {"ctas_per_cluster": cluster, "threads_per_cta": threads, "arith": "double-float"},

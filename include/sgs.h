@@ -164,6 +164,16 @@ int sgs_sweep_ordering(sgs_handle* h, double* f, const double* P, const double* 
 /* Uniform rescale of each instance to its total mass (eq. (32)); no-op where <= 0. */
 int sgs_rescale(sgs_handle* h, double* f, void* stream);
 
+/* Macroscopic quantities of every cell of f (device, the handle's field layout): density,
+ * bulk velocity and temperature as defined with the moments (eq. (6) and the definitions
+ * beside it, d = 3: rho T = (1/3) int |v - U|^2 f) and the heat flux of the lid-driven cavity
+ * study (Section 4.2.2), q = 1/2 int (v - U)|v - U|^2 f dv, all by the velocity quadrature
+ * (eq. (10)). out (device, caller-owned): 8 doubles per cell in the handle's cell order,
+ * (rho, U1, U2, U3, T, q1, q2, q3). FP64 throughout; f is only read. Cells of zero density
+ * give non-finite U, T, q. Needs a bound workspace (its cell tables); SGS_ERR_ARG for null
+ * pointers. */
+int sgs_macroscopic(const sgs_handle* h, const double* f, double* out, void* stream);
+
 /* One source iteration (eq. (SI)), 1-D problems: the collision step of f (P = Q - nu (M - f),
  * eq. (28), written to P), then for every velocity node the upwind transport with
  * absorption (|v1|/dx + nu_j/eps) f_j = (|v1|/dx) f_upwind + P_j/eps + (nu_j/eps) M[f_j] + b_j,
@@ -330,9 +340,11 @@ int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning
 /* Measurement probes (not part of the method; they supply the denominators of the
  * benchmark's rooflines and its latency model of the scan).
  *   sgs_peak_fma: FMA throughput of the CUDA-core pipes of the current device (SGS_FP32:
- *     FFMA, SGS_FP64: DFMA), independent FMA chains on every SM, iters FMAs per chain; tflops
- *     = 2 flops per FMA over the CUDA-event time of the launch on stream; sms (nullable) the
- *     SM count used, ms (nullable) the time. Synchronises the stream; allocates nothing.
+ *     FFMA, SGS_FP64: DFMA, SGS_FP32 | SGS_PEAK_PACKED: the packed FP32 pair FMA
+ *     fma.rn.f32x2, two FMAs per instruction), independent FMA chains on every SM, iters
+ *     instructions per chain; tflops = 2 flops per FMA over the CUDA-event time of the launch
+ *     on stream; sms (nullable) the SM count used, ms (nullable) the time. Synchronises the
+ *     stream; allocates nothing.
  *   sgs_probe_scan: latency of one building block of the persistent scan, in one cluster of
  *     `cluster` CTAs of `threads` threads on the nv^3 grid of [-v_max, v_max]^3, in the scan
  *     arithmetic of a handle of that precision (SGS_FP32: double-float, SGS_FP64: FP64):
@@ -349,6 +361,7 @@ int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning
  *     the completion wait gave up), max_ref = max |Dref|. Synchronises the stream. */
 int sgs_tc_selftest(int K, int N, int terms, int swap, void* dev_scratch, size_t bytes, double* max_err,
                     double* max_ref, void* stream);
+#define SGS_PEAK_PACKED 256
 int sgs_peak_fma(int precision, long long iters, double* tflops, int* sms, float* ms, void* stream);
 int sgs_probe_scan(int nv, double v_max, int precision, int cluster, int threads, int mode, int reps,
                    float* us_per_op, void* stream);

@@ -193,6 +193,7 @@ def lib():
             "or_qhat_direct": (None, [C.c_int, C.c_double, C.c_int, C.c_double, d, d, d]),
             "or_qfsm": (None, [C.c_int, C.c_double, C.c_int, C.c_double, d, d]),
             "or_moments": (None, [C.c_int, C.c_double, d, d]),
+            "or_macroscopic": (None, [C.c_int, C.c_double, d, d]),
             "or_conserve_project": (C.c_int, [C.c_int, C.c_double, d]),
             "or_conserve_project_w": (C.c_int, [C.c_int, C.c_double, d, d]),
             "or_discrete_maxwellian": (C.c_int, [C.c_int, C.c_double, d, d, d, C.c_int, C.c_double, C.c_int]),
@@ -287,6 +288,14 @@ def moments(f, L):
     m = np.empty(5)
     lib().or_moments(f.shape[0], L, _p(_arr(f)), _p(m))
     return m
+
+
+def macroscopic(f, L):
+    """(rho, U1, U2, U3, T, q1, q2, q3) of one cell (N, N, N): the moments' definitions with
+    d = 3 and the heat flux q = 1/2 int (v - U)|v - U|^2 f dv of Section 4.2.2."""
+    out = np.empty(8)
+    lib().or_macroscopic(f.shape[0], L, _p(_arr(f)), _p(out))
+    return out
 
 
 def conserve_project(q, L):

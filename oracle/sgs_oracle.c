@@ -382,6 +382,44 @@ void or_moments(int N, double L, const double* f, double* m5) {
 }
 
 /* ------------------------------------------------------------------------------------
+ * Macroscopic quantities of one cell by the velocity quadrature: rho, U and T as defined
+ * with the moments (eq. (6) and the definitions beside it, d = 3), and the heat flux of the
+ * lid-driven cavity study (Section 4.2.2), q = 1/2 int (v - U) |v - U|^2 f dv.
+ * out = (rho, U1, U2, U3, T, q1, q2, q3). U first, then the central sums about it.
+ * ---------------------------------------------------------------------------------- */
+void or_macroscopic(int N, double L, const double* f, double* out) {
+  double* v = (double*)malloc(sizeof(double) * N);
+  or_velocity_nodes(N, L, v);
+  double w = weight(N, L);
+  double rho = 0.0, mom[3] = {0.0, 0.0, 0.0};
+  for (int i1 = 0; i1 < N; i1++)
+    for (int i2 = 0; i2 < N; i2++)
+      for (int i3 = 0; i3 < N; i3++) {
+        double x = w * f[((long)i1 * N + i2) * N + i3];
+        rho += x;
+        mom[0] += x * v[i1];
+        mom[1] += x * v[i2];
+        mom[2] += x * v[i3];
+      }
+  double U[3] = {mom[0] / rho, mom[1] / rho, mom[2] / rho};
+  double e2 = 0.0, q[3] = {0.0, 0.0, 0.0};
+  for (int i1 = 0; i1 < N; i1++)
+    for (int i2 = 0; i2 < N; i2++)
+      for (int i3 = 0; i3 < N; i3++) {
+        double x = w * f[((long)i1 * N + i2) * N + i3];
+        double c[3] = {v[i1] - U[0], v[i2] - U[1], v[i3] - U[2]};
+        double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+        e2 += x * c2;
+        for (int d = 0; d < 3; d++) q[d] += 0.5 * x * c[d] * c2;
+      }
+  out[0] = rho;
+  for (int d = 0; d < 3; d++) out[1 + d] = U[d];
+  out[4] = e2 / (3.0 * rho);
+  for (int d = 0; d < 3; d++) out[5 + d] = q[d];
+  free(v);
+}
+
+/* ------------------------------------------------------------------------------------
  * Discrete Maxwellian (eqs. (13)-(14)): M_k = exp(alpha + beta.v_k - gamma |v_k|^2)
  * whose weighted moments sum_k wk_k phi(v_k) M_k equal a target. Newton's method on
  * theta = (alpha, beta, gamma): F(theta) = sum wk phi M - target, Jacobian A D with

@@ -75,6 +75,8 @@ int or_conserve_project(int N, double L, double* q);
 int or_conserve_project_w(int N, double L, const double* M, double* q);
 /* Moments (rho, rho*U, sum w|v|^2 f) with weights w. */
 void or_moments(int N, double L, const double* f, double* m5);
+/* rho, U1..3, T (eq. (6), d = 3) and the heat flux q1..3 of Section 4.2.2 of one cell */
+void or_macroscopic(int N, double L, const double* f, double* out8);
 /* Discrete Maxwellian exp(alpha + beta.v - gamma|v|^2) matching weighted moments.
  * wk: per-node weights (NULL -> w). theta in: initial guess (used if use_guess),
  * out: solution. Returns Newton iterations, or -1 on failure. */

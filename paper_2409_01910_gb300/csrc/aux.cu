@@ -509,6 +509,71 @@ __global__ void __launch_bounds__(256) k_rescale_apply(AuxArgs a, double* f, con
   for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < K; e += gridDim.y * blockDim.x) fc[e] *= lam;
 }
 
+// Macroscopic quantities of every cell: rho, U and T as the moments define them (d = 3) and
+// the heat flux q = 1/2 sum w (v - U)|v - U|^2 f of the lid-driven cavity study (Section
+// 4.2.2). out[8 c ..] = (rho, U1, U2, U3, T, q1, q2, q3). Raw sums give rho and U, a second
+// pass over the cell's nodes (from L2) forms the central sums about U, so T and q carry no
+// cancellation between raw moments.
+__global__ void __launch_bounds__(256) k_macroscopic(AuxArgs a, const double* __restrict__ f, double* __restrict__ out) {
+  __shared__ double sh[4][32];
+  __shared__ double tot[4];
+  const int c = blockIdx.x, N = a.N, K = N * N * N;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* fc = f + a.cell_off[c];
+  const double dv = a.dv, w = dv * dv * dv;
+  auto block_sums = [&](double (&x)[4]) {
+    warp_allsum<4>(x);
+    if (lane == 0)
+      for (int k = 0; k < 4; k++) sh[k][wid] = x[k];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      double t = 0.0;
+      for (int k = 0; k < nw; k++) t += sh[threadIdx.x][k];
+      tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+  };
+  double x[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    const double fe = fc[e];
+    x[0] += fe;
+    x[1] += node(e / (N * N), N, dv) * fe;
+    x[2] += node((e / N) % N, N, dv) * fe;
+    x[3] += node(e % N, N, dv) * fe;
+  }
+  block_sums(x);
+  const double s0 = tot[0], U1 = tot[1] / s0, U2 = tot[2] / s0, U3 = tot[3] / s0;
+  __syncthreads();
+  double y[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    const double fe = fc[e];
+    const double c1 = node(e / (N * N), N, dv) - U1, c2 = node((e / N) % N, N, dv) - U2, c3 = node(e % N, N, dv) - U3;
+    const double cc = c1 * c1 + c2 * c2 + c3 * c3, fcc = fe * cc;
+    y[0] += fcc;
+    y[1] += c1 * fcc;
+    y[2] += c2 * fcc;
+    y[3] += c3 * fcc;
+  }
+  block_sums(y);
+  if (threadIdx.x == 0) {
+    double* o = out + 8 * (long long)c;
+    o[0] = w * s0;
+    o[1] = U1;
+    o[2] = U2;
+    o[3] = U3;
+    o[4] = tot[0] / (3.0 * s0);
+    o[5] = 0.5 * w * tot[1];
+    o[6] = 0.5 * w * tot[2];
+    o[7] = 0.5 * w * tot[3];
+  }
+}
+
+cudaError_t launch_macroscopic(const AuxArgs& a, const double* f, double* out, cudaStream_t st) {
+  if (a.C <= 0) return cudaSuccess;
+  k_macroscopic<<<a.C, 256, 0, st>>>(a, f, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st) {
   double* mass = a.scratch + 2 * a.n_inst + a.C;  // [C]
   k_cell_mass<<<a.C, 256, 0, st>>>(a, f, mass);

@@ -447,16 +447,23 @@ static cudaError_t launch_pass_t(const FastArgs& a, cudaStream_t st) {
   constexpr size_t smem = (size_t)2 * NB * K * sizeof(uint16_t) + (size_t)nA * 2 * kTcRows * K * sizeof(uint16_t);
   auto kern = k_fast_pass<PASS, NP, PP>;
   cudaError_t e = func_attr((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the whole unified L1 as shared memory, so that several CTAs share an SM
+  if (e == cudaSuccess) e = func_attr((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   const long long B = (long long)a.C * a.S * 2;
   long long rows = PASS == 1 ? B * a.n * NP : (PASS == 2 ? B * PP * a.n : (long long)a.C * PP * PP);
   const long long tiles = (rows + kTcRows - 1) / kTcRows;
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0, per = 0, sm_bytes = 0, reserved = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTcRows, smem);
   if (e != cudaSuccess) return e;
-  per = std::max(1, std::min(per, 4));  // 128 TMEM columns per CTA: at most 4 CTAs share an SM's 512
+  // CTAs an SM's shared memory holds (the occupancy query can assume a smaller carveout); the
+  // tile loop is strided, so CTAs beyond the resident ones only wait for a slot
+  const int by_smem = sm_bytes / (int)(smem + 256 + (size_t)reserved);
+  per = std::max(1, std::min(std::max(per, by_smem), 4));  // 128 TMEM columns per CTA: at most 4 CTAs share 512
   const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sms * per));
   kern<<<grid, kTcRows, smem, st>>>(a);
   return cudaGetLastError();

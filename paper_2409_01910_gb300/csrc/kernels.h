@@ -264,6 +264,8 @@ cudaError_t tc_selftest(const float* A, const float* Bt, float* D, float* Dref, 
 cudaError_t probe_scan(int N, double dv, int arith, int cluster, int threads, int mode, int reps, cudaStream_t st);
 
 cudaError_t launch_rescale(const AuxArgs& a, double* f, cudaStream_t st);
+// rho, U, T and the heat flux q of every cell: out[8 c + (0..7)]
+cudaError_t launch_macroscopic(const AuxArgs& a, const double* f, double* out, cudaStream_t st);
 // After launch_rescale: Q, P (nullable) *= lam^2, nu *= lam, alpha += ln lam for the cells
 // [c_lo, c_hi) whose collision step was evaluated on the state before the rescale.
 cudaError_t launch_rescale_fixup(const AuxArgs& a, int c_lo, int c_hi, double* Q, double* P, double* nu,

@@ -1307,6 +1307,12 @@ int sgs_rescale(sgs_handle* h, double* f, void* stream) {
   return rescale_impl(h, f, as_stream(stream));
 }
 
+int sgs_macroscopic(const sgs_handle* h, const double* f, double* out, void* stream) {
+  if (!h || !f || !out) return SGS_ERR_ARG;
+  if (!h->ws) return SGS_ERR_WORKSPACE;
+  return cuda_status(launch_macroscopic(aux_args(h), f, out, as_stream(stream)));
+}
+
 int sgs_si_iteration(sgs_handle* h, double* f, double* P, const double* rhs, void* stream) {
   if (!h || !f || !P) return SGS_ERR_ARG;
   if (!h->ws) return SGS_ERR_WORKSPACE;

@@ -23,6 +23,7 @@ DIFFUSE, INFLOW = 0, 1
 FP64, FP32, DF64 = 0, 1, 2
 PFP, FP, PFP_RELAX = 0, 1, 2
 IT_P_VALID, IT_EVAL = 1, 2
+PEAK_PACKED = 256  # sgs_peak_fma: the packed FP32 pair FMA (fma.rn.f32x2)
 PROF_NAMES = ("moments", "dft", "sum", "reduce_idft", "sweep", "residual", "rescale", "sum_fp64", "sum_df64", "fast")
 PROF_CLASSES = len(PROF_NAMES)
 
@@ -168,6 +169,7 @@ def lib(build: bool = True):
             "sgs_sweep_backward": (C.c_int, [vp, vp, vp, vp, vp]),
             "sgs_sweep_ordering": (C.c_int, [vp, vp, vp, vp, C.c_int, vp]),
             "sgs_rescale": (C.c_int, [vp, vp, vp]),
+            "sgs_macroscopic": (C.c_int, [vp, vp, vp, vp]),
             "sgs_residual": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "sgs_iterate": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, vp, vp]),
             "sgs_dc_step": (C.c_int, [vp, vp, vp, vp, C.c_int, vp, vp]),
@@ -226,7 +228,8 @@ def host_weight(nv, v_max, collision, b0, a2, b2) -> float:
 
 
 def peak_fma(precision, iters=1 << 16, stream=None) -> dict:
-    """Measured FMA throughput of the current device's CUDA cores (FP32 or FP64)."""
+    """Measured FMA throughput of the current device's CUDA cores (FP32, FP64, or
+    FP32 | PEAK_PACKED for the packed pair instruction)."""
     t, n, ms = C.c_double(), C.c_int(), C.c_float()
     _check(lib().sgs_peak_fma(precision, iters, C.byref(t), C.byref(n), C.byref(ms), _stream(stream)),
            "sgs_peak_fma")
@@ -328,6 +331,16 @@ class Solver:
 
     def rescale(self, f, stream=None):
         _check(lib().sgs_rescale(self.h, _ptr(f), _stream(stream)), "sgs_rescale")
+
+    def macroscopic(self, f, out=None, stream=None):
+        """(cells, 8) FP64 device tensor: rho, U1, U2, U3, T, q1, q2, q3 of every cell."""
+        import torch
+
+        if out is None:
+            cells = self.field_elems // self.problems[0].nv ** 3
+            out = torch.empty((cells, 8), dtype=torch.float64, device=f.device)
+        _check(lib().sgs_macroscopic(self.h, _ptr(f), _ptr(out), _stream(stream)), "sgs_macroscopic")
+        return out
 
     def residual(self, f, Q, res, rhs=None, stream=None):
         _check(lib().sgs_residual(self.h, _ptr(f), _ptr(Q), _ptr(rhs), _ptr(res), _stream(stream)), "sgs_residual")
