@@ -375,8 +375,10 @@ int sgs_probe_scan(int nv, double v_max, int precision, int cluster, int threads
  * is formed on a zero-padded P^3 grid (P = 32 for N <= 16, else 48: no wrap-around) through
  * three separable DFT passes computed as tcgen05 matrix products (BF16 operands split from FP32,
  * FP32 accumulation in TMEM; terms 3: hi hi + lo hi + hi lo, about 1e-4 relative on Q; terms
- * 1: one BF16 product, about 2e-2), the node sum accumulated in FP32, the final transform to
- * the modes |k_i| <= N/2 - 1 and to the velocity grid in FP64.
+ * 1: one BF16 product, about 2e-2); the intermediate operands between the passes are stored
+ * as BF16 tiles in the tensor core's shared-memory layout and streamed by bulk copies; the
+ * node sum is accumulated in FP32; the transforms of f, the final transform to the modes
+ * |k_i| <= N/2 - 1 and the transform to the velocity grid run in FP32 (moments in FP64).
  *   sgs_fast_setup: for a hard-sphere handle (SGS_ERR_UNSUPPORTED otherwise); the nodes are
  *     processed `chunk` at a time (the workspace scales with chunk x cells); reports the
  *     workspace size of the operator (its own, besides the handle's).

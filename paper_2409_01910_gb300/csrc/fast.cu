@@ -180,29 +180,48 @@ __device__ inline void issue_product(uint32_t tmem, uint32_t ahi, uint32_t alo, 
   }
 }
 
-// Waits for the MMAs committed to `bar` (phase parity `par`), uniformly over the CTA. On a
-// time-out it reports, waits once more (bounded) so that nothing still writes TMEM, and
-// returns false.
-__device__ inline bool wait_mma(uint64_t* bar, uint32_t par, const FastArgs& a) {
-  bool ok = __syncthreads_and(mbar_wait(bar, par, a.spin_max) ? 1 : 0) != 0;
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(a.status, SGS_ST_TIMEOUT);
-    __syncthreads_and(mbar_wait(bar, par, a.spin_max) ? 1 : 0);
-  }
+// Bounded wait on phase `par` of `bar`, uniform over the CTA (every thread polls; the result
+// is the AND), so that the warp-wide TMEM instructions after it run in all threads or none.
+__device__ inline bool wait_uniform(uint64_t* bar, uint32_t par, long long spin_max) {
+  const bool ok = __syncthreads_and(mbar_wait(bar, par, spin_max) ? 1 : 0) != 0;
   tc::fence_after_sync();
   return ok;
 }
 
-// NP: padded mode count along K (16 or 32, K = 2 NP); PP: the padded grid P (32 or 48).
-template <int PASS, int NP, int PP>
-__global__ void __launch_bounds__(kTcRows) k_fast_pass(FastArgs a) {
+// After a wait gave up: report, then wait (bounded) for every copy and MMA still in flight
+// (uses next .. issued - 1 of each double-buffered barrier pair), so that nothing writes this
+// CTA's shared memory or TMEM when it is released.
+__device__ inline void drain(uint64_t* bar, int next, int issued, long long spin_max) {
+  for (int q = next; q < issued; q++) mbar_wait(&bar[q & 1], (uint32_t)((q >> 1) & 1), spin_max);
+}
+
+// Intermediate operands (the outputs of passes 1 and 2) are stored as the next pass's A
+// tiles: BF16 planes hi (and lo for 3 terms) of 128-row tiles in the K-major core-matrix
+// layout of shared memory, tile t at element t * 128 * K, so that the next pass copies a
+// tile into shared memory with one bulk copy per plane and hands it to the tensor core.
+// (re, im) of one complex entry are adjacent along K: one 32-bit store per plane.
+__device__ inline void store_pair(uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, long long row, int k, int K,
+                                  float re, float im, int terms) {
+  uint16_t h0, l0, h1, l1;
+  tc::split_bf16(re, h0, l0);
+  tc::split_bf16(im, h1, l1);
+  const long long o = (row >> 7) * (kTcRows * (long long)K) + tc::kmajor_offset((int)(row & 127), k, K) / 2;
+  *reinterpret_cast<uint32_t*>(hi + o) = (uint32_t)h0 | ((uint32_t)h1 << 16);
+  if (terms == 3) *reinterpret_cast<uint32_t*>(lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+}
+
+// ---- pass 1 (k3 -> x3): rows (b, k1, k2), A = w_{s,a} fhat_c formed by the threads (both
+// rows contiguous in memory, every load issued before the first use), one product per tile
+// into TMEM; the epilogue writes the pass-2 operand Y1 (rows (b, x3, k1), K = (k2, re/im)).
+template <int NP, int PP>
+__global__ void __launch_bounds__(kTcRows) k_fast_pass1(FastArgs a) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  constexpr int K = 2 * NP, P = PP, np = NP;
-  constexpr int NB = PASS == 3 ? P : 2 * P;  // columns of one product
+  constexpr int K = 2 * NP, P = PP, np = NP, NB = 2 * P;
   const int n = a.n;
   uint16_t* Bhi = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Blo = Bhi + NB * K;
-  uint16_t* Abuf = Blo + NB * K;              // [nA][hi, lo][128][K]
+  uint16_t* Ahi = Blo + NB * K;
+  uint16_t* Alo = Ahi + kTcRows * K;
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tslot;
   const int t = threadIdx.x, warp = t >> 5;
@@ -211,13 +230,8 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass(FastArgs a) {
     mbar_init(&bar, 1);
     fence_mbar_init();
   }
-  // the DFT matrix of this pass (NB rows of K floats, contiguous), split once per CTA
-  load_tile<K, NB>(PASS == 3 ? a.bt3 : a.bt12, NB, Bhi, Blo, 3);
-  const int B = a.C * a.S * 2;
-  long long rows;
-  if (PASS == 1) rows = (long long)B * n * np;
-  else if (PASS == 2) rows = (long long)B * P * n;
-  else rows = (long long)a.C * P * P;
+  load_tile<K, NB>(a.bt12, NB, Bhi, Blo, 3);  // the DFT matrix, split once per CTA
+  const long long rows = (long long)a.C * a.S * 2 * n * np;
   const long long tiles = (rows + kTcRows - 1) / kTcRows;
   tc::fence_before_sync();
   __syncthreads();
@@ -225,144 +239,315 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass(FastArgs a) {
   const uint32_t taddr = tslot;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   uint32_t phase = 0;
+  int mma_next = 0, mma_wait = 0;
   bool ok = true;
-  for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long r = tile * kTcRows + t;  // this thread's row
     const bool live = r < rows;
-    if (PASS != 3) {
-      // ---- A tile: 128 rows of K values
-      uint16_t* Ahi = Abuf;
-      uint16_t* Alo = Abuf + kTcRows * K;
-      if (PASS == 1) {
-        // row (b, k1, k2): the weights of slot s and side ab times the cell's spectrum,
-        // both rows contiguous; every load of the row is issued before the first use
-        int b = 0, k1 = 0, k2 = 0;
-        if (live) {
-          b = (int)(r / (n * np));
-          const int rem = (int)(r % (n * np));
-          k1 = rem / np;
-          k2 = rem % np;
-        }
-        const int ab = b & 1, sl = (b >> 1) % a.S, c = (b >> 1) / a.S;
-        const float4* fr = reinterpret_cast<const float4*>(a.fhat + (((long long)c * n + k1) * np + k2) * np * 2);
-        const float4* wr =
-            reinterpret_cast<const float4*>(a.wtab + ((((long long)(a.s0 + sl) * 2 + ab) * n + k1) * np + k2) * np);
-        float4 fv[NP / 2], wv[NP / 4];
+    int b = 0, k1 = 0, k2 = 0;
+    if (live) {
+      b = (int)(r / (n * np));
+      const int rem = (int)(r % (n * np));
+      k1 = rem / np;
+      k2 = rem % np;
+    }
+    const int ab = b & 1, sl = (b >> 1) % a.S, c = (b >> 1) / a.S;
+    const float4* fr = reinterpret_cast<const float4*>(a.fhat + (((long long)c * n + k1) * np + k2) * np * 2);
+    const float4* wr =
+        reinterpret_cast<const float4*>(a.wtab + ((((long long)(a.s0 + sl) * 2 + ab) * n + k1) * np + k2) * np);
+    float4 fv[NP / 2], wv[NP / 4];
 #pragma unroll
-        for (int i = 0; i < NP / 2; i++) fv[i] = live ? fr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < NP / 2; i++) fv[i] = live ? fr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < NP / 4; i++) wv[i] = live ? wr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < NP / 4; i++) wv[i] = live ? wr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < NP / 2; i++) {  // K elements 4 i .. 4 i + 3: modes k3 = 2 i, 2 i + 1
-          const float4 w4 = wv[i / 2];
-          const float w0 = (i & 1) ? w4.z : w4.x, w1 = (i & 1) ? w4.w : w4.y;
-          put4(Ahi, Alo, t, 4 * i, K, make_float4(w0 * fv[i].x, w0 * fv[i].y, w1 * fv[i].z, w1 * fv[i].w), a.terms);
-        }
-      } else {
-        // rows of Y1 are consecutive blocks of K floats
-        load_tile<K, kTcRows>(a.Y1 + tile * kTcRows * K, (int)(rows - tile * kTcRows < kTcRows ? rows - tile * kTcRows : kTcRows), Ahi, Alo,
-                     a.terms);
-      }
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
-      if (t == 0) {
-        issue_product(taddr, smem_addr(Ahi), smem_addr(Alo), smem_addr(Bhi), smem_addr(Blo), K, NB, a.terms);
-        tc::mma_commit(&bar);
-      }
-      ok = wait_mma(&bar, phase, a);
-      phase ^= 1u;
-      if (!ok) break;
-      // ---- epilogue: 2P columns (x, re/im) of this thread's row
-      for (int c0 = 0; c0 < NB; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + lane_base + (uint32_t)c0, v);
-        if (!live) continue;
-        if (PASS == 1) {
-          const int b = (int)(r / (n * np)), rem = (int)(r % (n * np)), k1 = rem / np, k2 = rem % np;
+    for (int i = 0; i < NP / 2; i++) {  // K elements 4 i .. 4 i + 3: modes k3 = 2 i, 2 i + 1
+      const float4 w4 = wv[i / 2];
+      const float w0 = (i & 1) ? w4.z : w4.x, w1 = (i & 1) ? w4.w : w4.y;
+      put4(Ahi, Alo, t, 4 * i, K, make_float4(w0 * fv[i].x, w0 * fv[i].y, w1 * fv[i].z, w1 * fv[i].w), a.terms);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) {
+      issue_product(taddr, smem_addr(Ahi), smem_addr(Alo), smem_addr(Bhi), smem_addr(Blo), K, NB, a.terms);
+      tc::mma_commit(&bar);
+    }
+    mma_next++;
+    ok = wait_uniform(&bar, phase, a.spin_max);
+    if (!ok) break;
+    mma_wait++;
+    phase ^= 1u;
+    // epilogue: (x3, re/im) of this thread's row into the pass-2 operand
 #pragma unroll
-          for (int i = 0; i < 16; i += 2) {
-            const int x3 = (c0 + i) >> 1;
-            float2* o = reinterpret_cast<float2*>(a.Y1 + ((((long long)b * P + x3) * n + k1) * np + k2) * 2);
-            *o = make_float2(v[i], v[i + 1]);
-          }
-        } else {
-          const int b = (int)(r / (P * n)), rem = (int)(r % (P * n)), x3 = rem / n, k1 = rem % n;
+    for (int c0 = 0; c0 < NB; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(taddr + lane_base + (uint32_t)c0, v);
+      if (live) {
 #pragma unroll
-          for (int i = 0; i < 16; i += 2) {
-            const int x2 = (c0 + i) >> 1;
-            float2* o = reinterpret_cast<float2*>(a.Y2 + ((((long long)b * P + x2) * P + x3) * np + k1) * 2);
-            *o = make_float2(v[i], v[i + 1]);
-          }
-        }
-      }
-      tc::fence_before_sync();
-      __syncthreads();
-    } else {
-      // ---- pass 3: rows (c, x2, x3) of one cell (P^2 is a multiple of 128)
-      const int c = (int)(tile * kTcRows / ((long long)P * P));
-      const int row0 = (int)(tile * kTcRows % ((long long)P * P));
-      float g[P];
-#pragma unroll
-      for (int i = 0; i < P; i++) g[i] = 0.0f;
-      for (int sl = 0; sl < a.S && ok; sl++) {
-        for (int ab = 0; ab < 2; ab++) {
-          uint16_t* Ahi = Abuf + (size_t)ab * 2 * kTcRows * K;
-          uint16_t* Alo = Ahi + kTcRows * K;
-          const long long b = ((long long)c * a.S + sl) * 2 + ab;
-          load_tile<K, kTcRows>(a.Y2 + (b * P * P + row0) * K, kTcRows, Ahi, Alo, a.terms);
-        }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (t == 0) {
-          for (int ab = 0; ab < 2; ab++) {
-            uint16_t* Ahi = Abuf + (size_t)ab * 2 * kTcRows * K;
-            issue_product(taddr + (uint32_t)(ab * P), smem_addr(Ahi), smem_addr(Ahi + kTcRows * K), smem_addr(Bhi),
-                          smem_addr(Blo), K, NB, a.terms);
-          }
-          tc::mma_commit(&bar);
-        }
-        ok = wait_mma(&bar, phase, a);
-        phase ^= 1u;
-        if (!ok) break;
-        const float ws = a.wslot[a.s0 + sl];
-#pragma unroll
-        for (int c0 = 0; c0 < P; c0 += 16) {
-          float va[16], vb[16];
-          tc::tmem_ld16(taddr + lane_base + (uint32_t)c0, va);
-          tc::tmem_ld16(taddr + lane_base + (uint32_t)(P + c0), vb);
-#pragma unroll
-          for (int i = 0; i < 16; i++) g[c0 + i] = fmaf(ws * va[i], vb[i], g[c0 + i]);
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-      }
-      if (ok && live) {
-        float4* o = reinterpret_cast<float4*>(a.G + ((long long)c * P * P + row0 + t) * P);
-#pragma unroll
-        for (int i = 0; i < P / 4; i++) {
-          float4 v = o[i];
-          v.x += g[4 * i];
-          v.y += g[4 * i + 1];
-          v.z += g[4 * i + 2];
-          v.w += g[4 * i + 3];
-          o[i] = v;
+        for (int i = 0; i < 16; i += 2) {
+          const int x3 = (c0 + i) >> 1;
+          store_pair(a.Y1h, a.Y1l, ((long long)b * P + x3) * n + k1, 2 * k2, K, v[i], v[i + 1], a.terms);
         }
       }
     }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (!ok) {
+    if (t == 0) atomicOr(a.status, SGS_ST_TIMEOUT);
+    for (int q = mma_wait; q < mma_next; q++) mbar_wait(&bar, phase, a.spin_max);
   }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_free(taddr, 128);
 }
 
+// ---- pass 2 (k2 -> x2): A tiles of Y1 (rows (b, x3, k1)) streamed by bulk copies into
+// double-buffered operand buffers; two TMEM accumulators, so that the copy of tile i + 1 and
+// the MMAs of tile i run while the epilogue of tile i - 1 writes the pass-3 operand Y2 (rows
+// (b, x2, x3), K = (k1, re/im)).
+template <int NP, int PP>
+__global__ void __launch_bounds__(kTcRows) k_fast_pass2(FastArgs a) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  constexpr int K = 2 * NP, P = PP, NB = 2 * P;
+  constexpr int TILE = kTcRows * K;  // elements of one operand plane tile
+  const int n = a.n;
+  uint16_t* Bhi = reinterpret_cast<uint16_t*>(smraw);
+  uint16_t* Blo = Bhi + NB * K;
+  uint16_t* Abuf = Blo + NB * K;  // [2 buffers][hi, lo][TILE]
+  __shared__ __align__(8) uint64_t bar_ld[2], bar_mma[2];
+  __shared__ uint32_t tslot;
+  const int t = threadIdx.x, warp = t >> 5;
+  if (warp == 0) tc::tmem_alloc(&tslot, 256);  // two accumulators of NB columns, 128 apart
+  if (t == 0) {
+    for (int j = 0; j < 2; j++) {
+      mbar_init(&bar_ld[j], 1);
+      mbar_init(&bar_mma[j], 1);
+    }
+    fence_mbar_init();
+  }
+  load_tile<K, NB>(a.bt12, NB, Bhi, Blo, 3);
+  const long long rows = (long long)a.C * a.S * 2 * P * n;
+  const long long tiles = (rows + kTcRows - 1) / kTcRows;
+  const int nt = tiles > blockIdx.x ? (int)((tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;  // this CTA's tiles
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tslot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t plane_bytes = TILE * sizeof(uint16_t);
+  auto issue_ld = [&](int i) {  // thread 0: the operand planes of this CTA's i-th tile
+    const long long tile = blockIdx.x + (long long)i * gridDim.x;
+    uint16_t* dst = Abuf + (size_t)(i & 1) * 2 * TILE;
+    mbar_arrive_expect_tx(&bar_ld[i & 1], plane_bytes * (a.terms == 3 ? 2 : 1));
+    bulk_g2s(dst, a.Y1h + tile * TILE, plane_bytes, &bar_ld[i & 1]);
+    if (a.terms == 3) bulk_g2s(dst + TILE, a.Y1l + tile * TILE, plane_bytes, &bar_ld[i & 1]);
+  };
+  auto epilogue = [&](int i) {
+    const long long r = (blockIdx.x + (long long)i * gridDim.x) * kTcRows + t;
+    const bool live = r < rows;
+    int b = 0, x3 = 0, k1 = 0;
+    if (live) {
+      b = (int)(r / (P * n));
+      const int rem = (int)(r % (P * n));
+      x3 = rem / n;
+      k1 = rem % n;
+    }
+    const uint32_t acc = taddr + lane_base + (uint32_t)((i & 1) * 128);
+#pragma unroll
+    for (int c0 = 0; c0 < NB; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(acc + (uint32_t)c0, v);
+      if (live) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+          const int x2 = (c0 + q) >> 1;
+          store_pair(a.Y2h, a.Y2l, ((long long)b * P + x2) * P + x3, 2 * k1, K, v[q], v[q + 1], a.terms);
+        }
+      }
+    }
+  };
+  int ld_next = 0, ld_wait = 0, mma_next = 0, mma_wait = 0;
+  if (t == 0)
+    for (int i = 0; i < 2 && i < nt; i++) issue_ld(i);
+  ld_next = nt < 2 ? nt : 2;
+  bool ok = true;
+  for (int i = 0; i < nt; i++) {
+    ok = wait_uniform(&bar_ld[i & 1], (uint32_t)((i >> 1) & 1), a.spin_max);
+    if (!ok) break;
+    ld_wait = i + 1;
+    if (t == 0) {
+      uint16_t* A = Abuf + (size_t)(i & 1) * 2 * TILE;
+      issue_product(taddr + (uint32_t)((i & 1) * 128), smem_addr(A), smem_addr(A + TILE), smem_addr(Bhi),
+                    smem_addr(Blo), K, NB, a.terms);
+      tc::mma_commit(&bar_mma[i & 1]);
+    }
+    mma_next = i + 1;
+    if (i >= 1) {
+      ok = wait_uniform(&bar_mma[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1), a.spin_max);
+      if (!ok) break;
+      mma_wait = i;
+      // MMA i - 1 has read its operand buffer: the copy of tile i + 1 goes there
+      if (i + 1 < nt) {
+        if (t == 0) issue_ld(i + 1);
+        ld_next = i + 2;
+      }
+      epilogue(i - 1);
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+  }
+  if (ok && nt > 0) {
+    ok = wait_uniform(&bar_mma[(nt - 1) & 1], (uint32_t)(((nt - 1) >> 1) & 1), a.spin_max);
+    if (ok) {
+      mma_wait = nt;
+      epilogue(nt - 1);
+    }
+  }
+  if (!ok) {
+    if (t == 0) atomicOr(a.status, SGS_ST_TIMEOUT);
+    drain(bar_ld, ld_wait, ld_next, a.spin_max);
+    drain(bar_mma, mma_wait, mma_next, a.spin_max);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(taddr, 256);
+}
+
+// ---- pass 3 (k1 -> x1): units (tile of rows (c, x2, x3), slot s); a unit's two operands
+// (sides a = 0, 1 of b = (c, s, a)) are Y2 tiles, streamed by bulk copies into
+// double-buffered operand buffers; its two products (real part of the transform) go to a
+// TMEM accumulator pair, double-buffered like pass 2; the epilogue multiplies the two sides,
+// weights the slot and sums the slots of the tile in registers, then adds the sum to G.
+template <int NP, int PP>
+__global__ void __launch_bounds__(kTcRows) k_fast_pass3(FastArgs a) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  constexpr int K = 2 * NP, P = PP, NB = P;
+  constexpr int TILE = kTcRows * K;
+  constexpr int TPC = P * P / kTcRows;  // tiles per cell (P^2 is a multiple of 128)
+  uint16_t* Bhi = reinterpret_cast<uint16_t*>(smraw);
+  uint16_t* Blo = Bhi + NB * K;
+  uint16_t* Abuf = Blo + NB * K;  // [2 buffers][side 2][hi, lo][TILE]
+  __shared__ __align__(8) uint64_t bar_ld[2], bar_mma[2];
+  __shared__ uint32_t tslot;
+  const int t = threadIdx.x, warp = t >> 5;
+  if (warp == 0) tc::tmem_alloc(&tslot, 256);  // two accumulator pairs (sides at +0, +P), 128 apart
+  if (t == 0) {
+    for (int j = 0; j < 2; j++) {
+      mbar_init(&bar_ld[j], 1);
+      mbar_init(&bar_mma[j], 1);
+    }
+    fence_mbar_init();
+  }
+  load_tile<K, NB>(a.bt3, NB, Bhi, Blo, 3);
+  const int S = a.S;
+  const long long tiles = (long long)a.C * TPC;
+  const int nt = tiles > blockIdx.x ? (int)((tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int nu = nt * S;  // units of this CTA: tile-major, slots inner
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tslot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t plane_bytes = TILE * sizeof(uint16_t);
+  auto issue_ld = [&](int u) {  // thread 0
+    const long long tile = blockIdx.x + (long long)(u / S) * gridDim.x;
+    const int s = u % S;
+    const long long c = tile / TPC, tin = tile % TPC;
+    uint16_t* dst = Abuf + (size_t)(u & 1) * 4 * TILE;
+    mbar_arrive_expect_tx(&bar_ld[u & 1], plane_bytes * (a.terms == 3 ? 4 : 2));
+    for (int ab = 0; ab < 2; ab++) {
+      const long long src = ((c * S + s) * 2 + ab) * TPC + tin;  // tile of b = (c, s, ab)
+      bulk_g2s(dst + (size_t)ab * 2 * TILE, a.Y2h + src * TILE, plane_bytes, &bar_ld[u & 1]);
+      if (a.terms == 3) bulk_g2s(dst + (size_t)ab * 2 * TILE + TILE, a.Y2l + src * TILE, plane_bytes, &bar_ld[u & 1]);
+    }
+  };
+  float g[P];
+#pragma unroll
+  for (int q = 0; q < P; q++) g[q] = 0.0f;
+  auto epilogue = [&](int u) {
+    const int s = u % S;
+    const float ws = a.wslot[a.s0 + s];
+    const uint32_t acc = taddr + lane_base + (uint32_t)((u & 1) * 128);
+#pragma unroll
+    for (int c0 = 0; c0 < P; c0 += 16) {
+      float va[16], vb[16];
+      tc::tmem_ld16(acc + (uint32_t)c0, va);
+      tc::tmem_ld16(acc + (uint32_t)(P + c0), vb);
+#pragma unroll
+      for (int q = 0; q < 16; q++) g[c0 + q] = fmaf(ws * va[q], vb[q], g[c0 + q]);
+    }
+    if (s == S - 1) {  // the tile's last slot: add the slot sum to G and start the next tile
+      const long long tile = blockIdx.x + (long long)(u / S) * gridDim.x;
+      float4* o = reinterpret_cast<float4*>(a.G + (tile * kTcRows + t) * P);
+#pragma unroll
+      for (int q = 0; q < P / 4; q++) {
+        float4 v = o[q];
+        v.x += g[4 * q];
+        v.y += g[4 * q + 1];
+        v.z += g[4 * q + 2];
+        v.w += g[4 * q + 3];
+        o[q] = v;
+      }
+#pragma unroll
+      for (int q = 0; q < P; q++) g[q] = 0.0f;
+    }
+  };
+  int ld_next = 0, ld_wait = 0, mma_next = 0, mma_wait = 0;
+  if (t == 0)
+    for (int u = 0; u < 2 && u < nu; u++) issue_ld(u);
+  ld_next = nu < 2 ? nu : 2;
+  bool ok = true;
+  for (int u = 0; u < nu; u++) {
+    ok = wait_uniform(&bar_ld[u & 1], (uint32_t)((u >> 1) & 1), a.spin_max);
+    if (!ok) break;
+    ld_wait = u + 1;
+    if (t == 0) {
+      uint16_t* A = Abuf + (size_t)(u & 1) * 4 * TILE;
+      for (int ab = 0; ab < 2; ab++)
+        issue_product(taddr + (uint32_t)((u & 1) * 128 + ab * P), smem_addr(A + (size_t)ab * 2 * TILE),
+                      smem_addr(A + (size_t)ab * 2 * TILE + TILE), smem_addr(Bhi), smem_addr(Blo), K, NB, a.terms);
+      tc::mma_commit(&bar_mma[u & 1]);
+    }
+    mma_next = u + 1;
+    if (u >= 1) {
+      ok = wait_uniform(&bar_mma[(u - 1) & 1], (uint32_t)(((u - 1) >> 1) & 1), a.spin_max);
+      if (!ok) break;
+      mma_wait = u;
+      if (u + 1 < nu) {
+        if (t == 0) issue_ld(u + 1);
+        ld_next = u + 2;
+      }
+      epilogue(u - 1);
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+  }
+  if (ok && nu > 0) {
+    ok = wait_uniform(&bar_mma[(nu - 1) & 1], (uint32_t)(((nu - 1) >> 1) & 1), a.spin_max);
+    if (ok) {
+      mma_wait = nu;
+      epilogue(nu - 1);
+    }
+  }
+  if (!ok) {
+    if (t == 0) atomicOr(a.status, SGS_ST_TIMEOUT);
+    drain(bar_ld, ld_wait, ld_next, a.spin_max);
+    drain(bar_mma, mma_wait, mma_next, a.spin_max);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(taddr, 256);
+}
+
 // Compact FP32 spectrum of every cell, fhat = (ahat + bhat) / 2 (the transforms of f - M and
 // f + M), zero-padded to npad along k2 and k3: out[c][k1][k2][k3][re, im].
-__global__ void k_fast_fhat(const double2* __restrict__ ahat, const double2* __restrict__ bhat, int C, int n,
-                            int npad, float* __restrict__ out) {
+__global__ void k_fast_fhat(const float2* __restrict__ ahat, const float2* __restrict__ bhat, int C, int n, int npad,
+                            float* __restrict__ out) {
   const long long total = (long long)C * n * npad * npad;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const int k3 = (int)(i % npad), k2 = (int)((i / npad) % npad), k1 = (int)((i / ((long long)npad * npad)) % n);
@@ -370,63 +555,68 @@ __global__ void k_fast_fhat(const double2* __restrict__ ahat, const double2* __r
     float2 v = make_float2(0.0f, 0.0f);
     if (k2 < n && k3 < n) {
       const long long o = ((((long long)(c / kLanes) * n + k1) * n + k2) * n + k3) * kLanes + (c % kLanes);
-      v = make_float2((float)(0.5 * (ahat[o].x + bhat[o].x)), (float)(0.5 * (ahat[o].y + bhat[o].y)));
+      v = make_float2(0.5f * (ahat[o].x + bhat[o].x), 0.5f * (ahat[o].y + bhat[o].y));
     }
     reinterpret_cast<float2*>(out)[i] = v;
   }
 }
 
 // Forward transform of G (real, [c][x2][x3][x1]) to the modes |k_i| <= h, times P^-3, in three
-// passes with FP64 accumulation; tw[k][x] = exp(-2 pi i (k - h) x / P).
-// pass A: T1[c][x2][x3][k1] = sum_x1 G e^{..k1 x1}
-__global__ void k_fast_final_a(const float* __restrict__ G, const double2* __restrict__ tw, int n, int P,
-                               double2* __restrict__ T1) {
-  const long long cx = blockIdx.x;  // (c, x2, x3)
+// separable passes in FP32 (G itself carries FP32 sums of BF16 products);
+// tw[k][x] = exp(-2 pi i (k - h) x / P).
+// pass A: T1[c][x2][x3][k1] = sum_x1 G e^{..k1 x1}; one warp per row (c, x2, x3)
+__global__ void k_fast_final_a(const float* __restrict__ G, const float2* __restrict__ tw, int n, int P,
+                               long long rows, float2* __restrict__ T1) {
+  const long long cx = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (cx >= rows) return;
   const float* g = G + cx * P;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    double re = 0.0, im = 0.0;
+  for (int k = lane; k < n; k += 32) {
+    float re = 0.0f, im = 0.0f;
     for (int x = 0; x < P; x++) {
-      const double2 w = tw[k * P + x];
-      re += w.x * g[x];
-      im += w.y * g[x];
+      const float2 w = tw[k * P + x];
+      const float gv = g[x];
+      re = fmaf(w.x, gv, re);
+      im = fmaf(w.y, gv, im);
     }
-    T1[cx * n + k] = make_double2(re, im);
+    T1[cx * n + k] = make_float2(re, im);
   }
 }
 
 // pass B: T2[c][x2][k3][k1] = sum_x3 T1[c][x2][x3][k1] e^{..k3 x3}
-__global__ void k_fast_final_b(const double2* __restrict__ T1, const double2* __restrict__ tw, int n, int P,
-                               double2* __restrict__ T2) {
+__global__ void k_fast_final_b(const float2* __restrict__ T1, const float2* __restrict__ tw, int n, int P,
+                               float2* __restrict__ T2) {
   const long long cx2 = blockIdx.x;  // (c, x2)
-  const double2* src = T1 + cx2 * P * n;
+  const float2* src = T1 + cx2 * P * n;
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
     const int k3 = i / n, k1 = i % n;
-    double re = 0.0, im = 0.0;
+    float re = 0.0f, im = 0.0f;
     for (int x3 = 0; x3 < P; x3++) {
-      const double2 w = tw[k3 * P + x3], v = src[x3 * n + k1];
-      re += w.x * v.x - w.y * v.y;
-      im += w.x * v.y + w.y * v.x;
+      const float2 w = tw[k3 * P + x3], v = src[x3 * n + k1];
+      re = fmaf(w.x, v.x, fmaf(-w.y, v.y, re));
+      im = fmaf(w.x, v.y, fmaf(w.y, v.x, im));
     }
-    T2[cx2 * n * n + i] = make_double2(re, im);
+    T2[cx2 * n * n + i] = make_float2(re, im);
   }
 }
 
-// pass C: qhat[g][k1][k2][k3][lane] = P^-3 sum_x2 T2[c][x2][k3][k1] e^{..k2 x2}
-__global__ void k_fast_final_c(const double2* __restrict__ T2, const double2* __restrict__ tw, int n, int P,
-                               double2* __restrict__ qhat) {
+// pass C: qhat[g][k1][k2][k3][lane] = P^-3 sum_x2 T2[c][x2][k3][k1] e^{..k2 x2}; grid (C, blocks
+// over the n^3 modes)
+__global__ void k_fast_final_c(const float2* __restrict__ T2, const float2* __restrict__ tw, int n, int P,
+                               float2* __restrict__ qhat) {
   const int c = blockIdx.x;
-  const double scale = 1.0 / ((double)P * P * P);
-  for (int i = threadIdx.x; i < n * n * n; i += blockDim.x) {
-    const int k1 = i / (n * n), k2 = (i / n) % n, k3 = i % n;
-    double re = 0.0, im = 0.0;
-    for (int x2 = 0; x2 < P; x2++) {
-      const double2 w = tw[k2 * P + x2], v = T2[(((long long)c * P + x2) * n + k3) * n + k1];
-      re += w.x * v.x - w.y * v.y;
-      im += w.x * v.y + w.y * v.x;
-    }
-    const long long o = ((((long long)(c / kLanes) * n + k1) * n + k2) * n + k3) * kLanes + (c % kLanes);
-    qhat[o] = make_double2(re * scale, im * scale);
+  const float scale = 1.0f / ((float)P * P * P);
+  const int i = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i >= n * n * n) return;
+  const int k1 = i / (n * n), k2 = (i / n) % n, k3 = i % n;
+  float re = 0.0f, im = 0.0f;
+  for (int x2 = 0; x2 < P; x2++) {
+    const float2 w = tw[k2 * P + x2], v = T2[(((long long)c * P + x2) * n + k3) * n + k1];
+    re = fmaf(w.x, v.x, fmaf(-w.y, v.y, re));
+    im = fmaf(w.x, v.y, fmaf(w.y, v.x, im));
   }
+  const long long o = ((((long long)(c / kLanes) * n + k1) * n + k2) * n + k3) * kLanes + (c % kLanes);
+  qhat[o] = make_float2(re * scale, im * scale);
 }
 
 }  // namespace
@@ -434,61 +624,72 @@ __global__ void k_fast_final_c(const double2* __restrict__ T2, const double2* __
 // ---------------------------------------------------------------------------------------
 // Launchers of the fast operator.
 // ---------------------------------------------------------------------------------------
-cudaError_t launch_fast_fhat(const double2* ahat, const double2* bhat, int C, int n, int npad, float* out,
+cudaError_t launch_fast_fhat(const float2* ahat, const float2* bhat, int C, int n, int npad, float* out,
                              cudaStream_t st) {
   const long long total = (long long)C * n * npad * npad;
   k_fast_fhat<<<(int)std::min<long long>((total + 255) / 256, 152 * 8), 256, 0, st>>>(ahat, bhat, C, n, npad, out);
   return cudaGetLastError();
 }
 
-template <int PASS, int NP, int PP>
-static cudaError_t launch_pass_t(const FastArgs& a, cudaStream_t st) {
-  constexpr int K = 2 * NP, NB = PASS == 3 ? PP : 2 * PP, nA = PASS == 3 ? 2 : 1;
-  constexpr size_t smem = (size_t)2 * NB * K * sizeof(uint16_t) + (size_t)nA * 2 * kTcRows * K * sizeof(uint16_t);
-  auto kern = k_fast_pass<PASS, NP, PP>;
-  cudaError_t e = func_attr((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  // the whole unified L1 as shared memory, so that several CTAs share an SM
-  if (e == cudaSuccess) e = func_attr((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e != cudaSuccess) return e;
-  const long long B = (long long)a.C * a.S * 2;
-  long long rows = PASS == 1 ? B * a.n * NP : (PASS == 2 ? B * PP * a.n : (long long)a.C * PP * PP);
-  const long long tiles = (rows + kTcRows - 1) / kTcRows;
+// CTAs per SM for a pass kernel: what its shared memory allows (the occupancy query can
+// assume a smaller carveout) and what its TMEM columns allow (512 per SM); the tile loops are
+// strided, so CTAs beyond the resident ones only wait for a slot.
+static cudaError_t pass_grid(const void* kern, size_t smem, int tmem_cols, long long work, int* grid) {
+  cudaError_t e = func_attr(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = func_attr(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   int dev = 0, sms = 0, per = 0, sm_bytes = 0, reserved = 0;
-  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTcRows, smem);
   if (e != cudaSuccess) return e;
-  // CTAs an SM's shared memory holds (the occupancy query can assume a smaller carveout); the
-  // tile loop is strided, so CTAs beyond the resident ones only wait for a slot
   const int by_smem = sm_bytes / (int)(smem + 256 + (size_t)reserved);
-  per = std::max(1, std::min(std::max(per, by_smem), 4));  // 128 TMEM columns per CTA: at most 4 CTAs share 512
-  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sms * per));
-  kern<<<grid, kTcRows, smem, st>>>(a);
+  per = std::max(1, std::min(std::max(per, by_smem), 512 / tmem_cols));
+  *grid = (int)std::max<long long>(1, std::min<long long>(work, (long long)sms * per));
+  return cudaSuccess;
+}
+
+template <int NP, int PP>
+static cudaError_t launch_passes_t(int pass, const FastArgs& a, cudaStream_t st) {
+  constexpr int K = 2 * NP, TILE = kTcRows * K;
+  const long long B = (long long)a.C * a.S * 2;
+  int grid = 0;
+  cudaError_t e;
+  if (pass == 1) {
+    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * 2 * PP * K + (size_t)2 * TILE);
+    const long long tiles = (B * a.n * NP + kTcRows - 1) / kTcRows;
+    e = pass_grid((const void*)k_fast_pass1<NP, PP>, smem, 128, tiles, &grid);
+    if (e == cudaSuccess) k_fast_pass1<NP, PP><<<grid, kTcRows, smem, st>>>(a);
+  } else if (pass == 2) {
+    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * 2 * PP * K + (size_t)2 * 2 * TILE);
+    const long long tiles = (B * PP * a.n + kTcRows - 1) / kTcRows;
+    e = pass_grid((const void*)k_fast_pass2<NP, PP>, smem, 256, tiles, &grid);
+    if (e == cudaSuccess) k_fast_pass2<NP, PP><<<grid, kTcRows, smem, st>>>(a);
+  } else {
+    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * PP * K + (size_t)2 * 4 * TILE);
+    const long long tiles = (long long)a.C * PP * PP / kTcRows;
+    e = pass_grid((const void*)k_fast_pass3<NP, PP>, smem, 256, tiles, &grid);
+    if (e == cudaSuccess) k_fast_pass3<NP, PP><<<grid, kTcRows, smem, st>>>(a);
+  }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-template <int PASS>
-static cudaError_t launch_pass_p(const FastArgs& a, cudaStream_t st) {
-  if (a.npad == 16 && a.P == 32) return launch_pass_t<PASS, 16, 32>(a, st);
-  if (a.npad == 32 && a.P == 32) return launch_pass_t<PASS, 32, 32>(a, st);
-  if (a.npad == 32 && a.P == 48) return launch_pass_t<PASS, 32, 48>(a, st);
-  return cudaErrorInvalidValue;
-}
-
 cudaError_t launch_fast_pass(int pass, const FastArgs& a, cudaStream_t st) {
-  if (pass == 1) return launch_pass_p<1>(a, st);
-  if (pass == 2) return launch_pass_p<2>(a, st);
-  if (pass == 3) return launch_pass_p<3>(a, st);
+  if (pass < 1 || pass > 3) return cudaErrorInvalidValue;
+  if (a.npad == 16 && a.P == 32) return launch_passes_t<16, 32>(pass, a, st);
+  if (a.npad == 32 && a.P == 32) return launch_passes_t<32, 32>(pass, a, st);
+  if (a.npad == 32 && a.P == 48) return launch_passes_t<32, 48>(pass, a, st);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_fast_final(const float* G, const double2* tw, int C, int n, int P, double2* T1, double2* T2,
-                              double2* qhat, cudaStream_t st) {
-  k_fast_final_a<<<C * P * P, 32, 0, st>>>(G, tw, n, P, T1);
+cudaError_t launch_fast_final(const float* G, const float2* tw, int C, int n, int P, float2* T1, float2* T2,
+                              float2* qhat, cudaStream_t st) {
+  const long long rows = (long long)C * P * P;
+  k_fast_final_a<<<(int)((rows + 7) / 8), 256, 0, st>>>(G, tw, n, P, rows, T1);
   k_fast_final_b<<<C * P, 256, 0, st>>>(T1, tw, n, P, T2);
-  k_fast_final_c<<<C, 256, 0, st>>>(T2, tw, n, P, qhat);
+  k_fast_final_c<<<dim3(C, (n * n * n + 255) / 256), 256, 0, st>>>(T2, tw, n, P, qhat);
   return cudaGetLastError();
 }
 

@@ -243,18 +243,23 @@ struct FastArgs {
   const float* wslot;           // [slots] weight of each slot's product
   const float* bt12;            // [2P][2 npad]: passes 1 and 2
   const float* bt3;             // [P][2 npad]: pass 3 (real part)
-  float* Y1;                    // [B][P][n][npad][2]
-  float* Y2;                    // [B][P][P][npad][2]
+  // the pass-2 and pass-3 operands as BF16 planes (hi; lo for 3 terms) of 128-row tiles in the
+  // K-major core-matrix layout (K = 2 npad): Y1 rows (b, x3, k1), K (k2, re/im); Y2 rows
+  // (b, x2, x3), K (k1, re/im); the last Y1 tile padded to 128 rows
+  uint16_t* Y1h;
+  uint16_t* Y1l;
+  uint16_t* Y2h;
+  uint16_t* Y2l;
   float* G;                     // [C][P][P][P]
   long long spin_max;
   unsigned int* status;         // TIMEOUT bit
 };
 
-cudaError_t launch_fast_fhat(const double2* ahat, const double2* bhat, int C, int n, int npad, float* out,
+cudaError_t launch_fast_fhat(const float2* ahat, const float2* bhat, int C, int n, int npad, float* out,
                              cudaStream_t st);
 cudaError_t launch_fast_pass(int pass, const FastArgs& a, cudaStream_t st);
-cudaError_t launch_fast_final(const float* G, const double2* tw, int C, int n, int P, double2* T1, double2* T2,
-                              double2* qhat, cudaStream_t st);
+cudaError_t launch_fast_final(const float* G, const float2* tw, int C, int n, int P, float2* T1, float2* T2,
+                              float2* qhat, cudaStream_t st);
 
 // Tensor-core self-test (fast.cu): D = A Bt^T on tcgen05 and on the CUDA cores.
 cudaError_t tc_selftest(const float* A, const float* Bt, float* D, float* Dref, int K, int N, int terms, int swap,

@@ -1597,9 +1597,9 @@ struct sgs_fast {
   int N = 0, n = 0, h = 0, npad = 0, P = 0, C = 0, M = 0, slots = 0, chunk = 0;
   double L = 0.0, b0 = 0.0;
   std::vector<float> wtab, wslot, bt12, bt3;
-  std::vector<double2> tw;
+  std::vector<float2> tw;
   struct {
-    size_t fhat, wtab, wslot, bt12, bt3, tw, Y1, Y2, G, T1, T2, end;
+    size_t fhat, wtab, wslot, bt12, bt3, tw, Y1h, Y1l, Y2h, Y2l, G, T1, T2, end;
   } off;
   size_t ws_bytes = 0;
   char* ws = nullptr;
@@ -1738,7 +1738,7 @@ int sgs_fast_setup(const sgs_handle* h, int m_theta, int m_phi, int chunk, sgs_f
   for (int k = 0; k < n; k++)
     for (int xx = 0; xx < P; xx++) {
       const double ang = -2.0 * kPi * (double)(((long long)xx * (k - H)) % P) / P;
-      x->tw[(size_t)k * P + xx] = make_double2(std::cos(ang), std::sin(ang));
+      x->tw[(size_t)k * P + xx] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
   // workspace
   size_t o = 0;
@@ -1753,12 +1753,17 @@ int sgs_fast_setup(const sgs_handle* h, int m_theta, int m_phi, int chunk, sgs_f
   x->off.wslot = take(sizeof(float) * x->wslot.size());
   x->off.bt12 = take(sizeof(float) * x->bt12.size());
   x->off.bt3 = take(sizeof(float) * x->bt3.size());
-  x->off.tw = take(sizeof(double2) * x->tw.size());
-  x->off.Y1 = take(sizeof(float) * Bc * P * n * np * 2);
-  x->off.Y2 = take(sizeof(float) * Bc * P * P * np * 2);
+  x->off.tw = take(sizeof(float2) * x->tw.size());
+  // BF16 operand planes of 128-row tiles (K = 2 np); Y1's last tile padded
+  const size_t tile = (size_t)128 * 2 * np;
+  const size_t y1_tiles = (Bc * P * n + 127) / 128, y2_tiles = Bc * P * P / 128;
+  x->off.Y1h = take(sizeof(uint16_t) * y1_tiles * tile);
+  x->off.Y1l = take(sizeof(uint16_t) * y1_tiles * tile);
+  x->off.Y2h = take(sizeof(uint16_t) * y2_tiles * tile);
+  x->off.Y2l = take(sizeof(uint16_t) * y2_tiles * tile);
   x->off.G = take(sizeof(float) * (size_t)x->C * P * P * P);
-  x->off.T1 = take(sizeof(double2) * (size_t)x->C * P * P * n);
-  x->off.T2 = take(sizeof(double2) * (size_t)x->C * P * n * n);
+  x->off.T1 = take(sizeof(float2) * (size_t)x->C * P * P * n);
+  x->off.T2 = take(sizeof(float2) * (size_t)x->C * P * n * n);
   x->off.end = o;
   x->ws_bytes = o;
   *out = x;
@@ -1779,9 +1784,10 @@ int sgs_fast_bind(sgs_fast* x, void* device_ptr, size_t bytes) {
   if (e == cudaSuccess)
     e = cudaMemcpy(x->ws + x->off.bt3, x->bt3.data(), sizeof(float) * x->bt3.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(x->ws + x->off.tw, x->tw.data(), sizeof(double2) * x->tw.size(), cudaMemcpyHostToDevice);
-  // the padded entries of the pass-2 output (k1 >= n) are never written: zero them once
-  if (e == cudaSuccess) e = cudaMemset(x->ws + x->off.Y2, 0, x->off.G - x->off.Y2);
+    e = cudaMemcpy(x->ws + x->off.tw, x->tw.data(), sizeof(float2) * x->tw.size(), cudaMemcpyHostToDevice);
+  // the padded entries of the pass-3 operand (k1 >= n) and the rows past the last pass-2 row
+  // are never written: zero them once
+  if (e == cudaSuccess) e = cudaMemset(x->ws + x->off.Y1h, 0, x->off.G - x->off.Y1h);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   return cuda_status(e);
 }
@@ -1791,8 +1797,9 @@ int sgs_fast_collide(sgs_fast* x, sgs_handle* h, const double* f, double* Q, int
   if (!x->ws || !h->ws) return SGS_ERR_WORKSPACE;
   if (x->N != h->N || x->C != h->C || x->L != h->L) return SGS_ERR_ARG;
   cudaStream_t st = as_stream(stream);
-  // moments and discrete Maxwellians (the transforms of f - M and f + M give fhat)
-  CollideCtx<double> cx = collide_ctx<double>(h);
+  // moments and discrete Maxwellians (the transforms of f - M and f + M give fhat); the
+  // transforms run in FP32 (the passes take FP32 spectra and BF16 products)
+  CollideCtx<float> cx = collide_ctx<float>(h);
   cudaError_t e;
   {
     Scope sc(h, SGS_PROF_MOMENTS, st, 1);
@@ -1822,8 +1829,10 @@ int sgs_fast_collide(sgs_fast* x, sgs_handle* h, const double* f, double* Q, int
     a.wslot = x->at<float>(x->off.wslot);
     a.bt12 = x->at<float>(x->off.bt12);
     a.bt3 = x->at<float>(x->off.bt3);
-    a.Y1 = x->at<float>(x->off.Y1);
-    a.Y2 = x->at<float>(x->off.Y2);
+    a.Y1h = x->at<uint16_t>(x->off.Y1h);
+    a.Y1l = x->at<uint16_t>(x->off.Y1l);
+    a.Y2h = x->at<uint16_t>(x->off.Y2h);
+    a.Y2l = x->at<uint16_t>(x->off.Y2l);
     a.G = x->at<float>(x->off.G);
     a.spin_max = h->spin_max;
     a.status = &h->at<Counters>(h->off.cnt)[0].status;
@@ -1833,8 +1842,8 @@ int sgs_fast_collide(sgs_fast* x, sgs_handle* h, const double* f, double* Q, int
       for (int pass = 1; pass <= 3 && e == cudaSuccess; pass++) e = launch_fast_pass(pass, a, st);
     }
     if (e == cudaSuccess)
-      e = launch_fast_final(a.G, x->at<double2>(x->off.tw), x->C, x->n, x->P, x->at<double2>(x->off.T1),
-                            x->at<double2>(x->off.T2), cx.sb.qhat, st);
+      e = launch_fast_final(a.G, x->at<float2>(x->off.tw), x->C, x->n, x->P, x->at<float2>(x->off.T1),
+                            x->at<float2>(x->off.T2), cx.sb.qhat, st);
   }
   if (e != cudaSuccess) return cuda_status(e);
   // inverse transform of the modes to the velocity grid (no partial sums to reduce)
