@@ -958,11 +958,27 @@ def profile_case(which):
         s = sgs.Solver(sgs.Problem(nx=J, nv=N, v_max=L, collision=sgs.HARD_SPHERE, eps=0.1))
         fast = sgs.FastOperator(s, 8, 16, chunk=8)
         f = torch.from_numpy(I.initial_state(J, N, L, T=1.5).reshape(-1)).cuda()
-        Q = s.field()
-        for _ in range(2):
-            fast.collide(f, Q, terms=3)
-        torch.cuda.synchronize()
-        print(json.dumps({"case": which, "status": s.read_status()}))
+        Q, P = s.field(), s.field()
+        out = {"case": which, "cells": J, "nv": N, "v_max": L, "nodes": "8 x 16 + loss slot", "chunk": 8}
+        runs = (("fast_terms3", lambda: fast.collide(f, Q, terms=3)), ("fast_terms1", lambda: fast.collide(f, Q, terms=1)),
+                ("direct_fp32", lambda: s.collide(f, Q, P)))
+        for name, fn in runs:
+            fn()  # warm-up (the first fast evaluation is the one ncu skips past)
+            torch.cuda.synchronize()
+            s.profile(True)
+            s.profile_read()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            prof = s.profile_read()
+            s.profile(False)
+            out[name] = {"ms": round(e0.elapsed_time(e1) / 3, 3),
+                         "classes_ms": {k: round(v[0] / 3, 3) for k, v in prof.items() if v[0] > 0}}
+        out["status"] = s.read_status()["status"]
+        print(json.dumps(out))
         return
     if which == "steps":
         # the benchmark's step on the 64-cell heat workload: one defect-correction evaluation,
