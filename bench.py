@@ -446,10 +446,12 @@ def measure_peaks(wl, shape, local=0):
     precision = sgs.FP32  # the mixed solver's scans run in double-float
     red = sgs.probe_scan(wl.N, wl.L, precision, cluster, threads, 0, reps=4000)
     newt = sgs.probe_scan(wl.N, wl.L, precision, cluster, threads, 1, reps=4000)
+    cbar = sgs.probe_scan(wl.N, wl.L, precision, cluster, threads, 2, reps=4000)
     return {"fp32_ffma_tflops": round(best32["tflops"], 3), "fp64_dfma_tflops": round(fp64["tflops"], 4),
             "fp32_packed_ffma2_tflops": round(packed["tflops"], 3),
             "sms": best32["sms"], "sm_mhz_during_probe": clk.summary().get("sm_mhz"),
             "scan_cluster_reduce_us": round(red, 3), "scan_newton_iteration_us": round(newt, 3),
+            "scan_cluster_barrier_us": round(cbar, 3),
             "scan_probe_shape": {"ctas_per_cluster": cluster, "threads_per_cta": threads, "arith": "double-float"},
             "how": ("sgs_peak_fma: 8 independent FMA chains per thread, every SM fully occupied, CUDA events; "
                     "sgs_probe_scan: 4000 dependent operations in one cluster minus an empty launch")}

@@ -349,7 +349,8 @@ int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning
  *     `cluster` CTAs of `threads` threads on the nv^3 grid of [-v_max, v_max]^3, in the scan
  *     arithmetic of a handle of that precision (SGS_FP32: double-float, SGS_FP64: FP64):
  *     mode 0 a cluster reduction of seven values, mode 1 one Newton iteration of the
- *     discrete Maxwellian (evaluation, combination, factorisation). us_per_op = (time of reps
+ *     discrete Maxwellian (evaluation, combination, factorisation), mode 2 the hardware
+ *     cluster barrier alone (one step of the reduction). us_per_op = (time of reps
  *     operations - time of an empty launch) / reps in microseconds. Synchronises the stream. */
 /*   sgs_tc_selftest: check of the tensor-core path of the fast spectral operator (no
  *     counterpart in the paper): D = A Bt^T for a 128 x K matrix A and an N x K matrix Bt of

@@ -1555,7 +1555,7 @@ int sgs_autotune(sgs_handle* h, double* f, const double* P, int reps, sgs_tuning
 
 int sgs_probe_scan(int nv, double v_max, int precision, int cluster, int threads, int mode, int reps,
                    float* us_per_op, void* stream) {
-  if (!valid_nv(nv) || !(v_max > 0.0) || (mode != 0 && mode != 1) || reps < 1 || !us_per_op) return SGS_ERR_ARG;
+  if (!valid_nv(nv) || !(v_max > 0.0) || (mode < 0 || mode > 2) || reps < 1 || !us_per_op) return SGS_ERR_ARG;
   if (precision != SGS_FP64 && precision != SGS_FP32) return SGS_ERR_ARG;
   const int arith = precision == SGS_FP32 ? kSweepDF64 : kSweepF64;  // the scan arithmetic of such a handle
   const double dv = 2.0 * v_max / nv;

@@ -799,6 +799,9 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     // cell before any reads of the next one's neighbours (each thread reads only its own
     // nodes, so no cross-thread ordering is needed beyond program order)
   }
+  // no CTA leaves while another may still read its shared memory (the last reduction's
+  // distributed-shared-memory loads)
+  cl.sync();
 
   if (rank == 0 && tid == 0) {
     Counters* c = a.cnt + q;
@@ -1113,6 +1116,7 @@ __global__ void __launch_bounds__(256) k_sweep2d(SweepArgs a, int ordering, int 
 #pragma unroll
     for (int t = 0; t < EPT; t++) fj[t] = tod(g[t]);
   }
+  cl.sync();  // the last reduction's remote loads are done before any CTA leaves
   if (rank == 0 && tid == 0) {
     Counters* c = a.cnt;
     atomicAdd(&c->visits, 1ULL);
@@ -1167,14 +1171,27 @@ __global__ void __launch_bounds__(256) k_probe_scan(int N, double dv, int mode, 
   __syncthreads();
   double acc = 0.0;
   if (mode == 0) {
+    // inputs formed once (FP64 is scarce: forming them per repetition would time FP64
+    // conversions, not the reduction); each repetition reduces a fresh copy
     int buf = 0;
+    E v0[7];
+#pragma unroll
+    for (int q = 0; q < 7; q++) v0[q] = cvt<E>(1e-3 * (double)(tid + q));
+    E accE = cvt<E>(0.0);
     for (int r = 0; r < reps; r++) {
       E v[7];
 #pragma unroll
-      for (int q = 0; q < 7; q++) v[q] = cvt<E>(1e-3 * (double)(tid + q + r));
+      for (int q = 0; q < 7; q++) v[q] = v0[q];
       double t[7];
       cluster_reduce<7, E>(v, t, sm, buf, cl, CS);
-      acc += t[0];
+      accE = accE + sm.red_tote[0];
+    }
+    acc = tod(accE);
+  } else if (mode == 2) {
+    // the hardware cluster barrier alone (one of the reduction's steps)
+    for (int r = 0; r < reps; r++) {
+      cl.sync();
+      acc += (double)(tid + r);
     }
   } else {
     const int wid = tid >> 5;
@@ -1185,6 +1202,7 @@ __global__ void __launch_bounds__(256) k_probe_scan(int N, double dv, int mode, 
       const E target[5] = {cvt<E>(1.0), cvt<E>(0.0), cvt<E>(0.0), cvt<E>(0.0), cvt<E>(3.0)};
       const E w = cvt<E>(dv * dv * dv);
       int buf = 0;
+      float accf = 0.0f;
       for (int r = 0; r < reps; r++) {
         eval_warp<E>(sm, N, thE, wid, buf);
         eval_bar(nev);
@@ -1196,12 +1214,14 @@ __global__ void __launch_bounds__(256) k_probe_scan(int N, double dv, int mode, 
 #pragma unroll
         for (int i = 0; i < 5; i++) Ff[i] = tof(F[i]);
         chol5_solve(A, Ff, y);
-        acc += (double)y[0] + (double)fn;
+        accf += y[0] + fn;  // FP32: the probe times the iteration, not FP64 adds
         thE[0] = thE[0] + cvt<E>(1e-9 * (double)y[0]);  // the next evaluation depends on this one
       }
+      acc = (double)accf;
     }
     __syncthreads();
   }
+  cl.sync();  // the last reduction's remote loads are done before any CTA leaves
   if (acc == sentinel) g_probe_sink = acc;
 }
 

@@ -237,8 +237,9 @@ def peak_fma(precision, iters=1 << 16, stream=None) -> dict:
 
 
 def probe_scan(nv, v_max, precision, cluster, threads, mode, reps=2000, stream=None) -> float:
-    """Microseconds per cluster reduction (mode 0) or per Newton iteration (mode 1) of the
-    persistent scan in one cluster of the given shape."""
+    """Microseconds per cluster reduction (mode 0), per Newton iteration (mode 1) or per
+    hardware cluster barrier (mode 2) of the persistent scan in one cluster of the given
+    shape."""
     us = C.c_float()
     _check(lib().sgs_probe_scan(nv, v_max, precision, cluster, threads, mode, reps, C.byref(us), _stream(stream)),
            "sgs_probe_scan")

@@ -71,3 +71,31 @@ def test_fast_operator_matches_the_fast_oracle(terms, tol):
     # its own precision
     w = (2 * L / N) ** 3
     assert abs(w * Qg.sum((1, 2, 3))).max() <= tol * w * np.abs(Qg).sum((1, 2, 3)).max()
+
+
+@pytest.mark.parametrize("terms,tol", [(3, 1e-3), (1, 8e-2)])
+def test_fast_operator_at_the_shock_grid(terms, tol):
+    """The full-size grid of the hard-sphere workload (32^3 on [-10, 10]^3, P = 48, K = 64: the
+    launch shapes the benchmark's fast case times), two cells against the fast oracle. Bounds
+    from a numpy emulation of the same passes with BF16 rounding on these two states: single
+    BF16 products 5.0e-2 and 6.0e-2 of max |Q| (the longer transforms of N = 32 round more
+    than N = 16's 2.4e-2), split products 6e-5 and 9e-5; the bounds leave about 30 % and a
+    factor 10 above them."""
+    import numpy as np
+    from oracle import fast_spectral as F
+
+    N, L, J = 32, 10.0, 2
+    b0 = 1.0 / (4.0 * np.pi)
+    f = hs_states(J, N, L, seed=9)
+    s = sgs.Solver(sgs.Problem(nx=J, nv=N, v_max=L, collision=sgs.HARD_SPHERE, b0=b0, eps=0.1))
+    fast = sgs.FastOperator(s, m_theta=8, m_phi=16, chunk=8)
+    fd = torch.from_numpy(f.reshape(-1)).cuda()
+    Q = s.field()
+    fast.collide(fd, Q, terms=terms)
+    torch.cuda.synchronize()
+    assert s.read_status()["status"] & sgs.ST_TIMEOUT == 0
+    Qg = Q.cpu().numpy().reshape(f.shape)
+    for j in range(J):
+        qo = F.qfsm_fast(f[j], L, b0, 8, 16)
+        err = float(np.abs(Qg[j] - qo).max() / np.abs(qo).max())
+        assert err <= tol, (j, err)
