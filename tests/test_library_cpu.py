@@ -172,3 +172,34 @@ def test_batch_inputs_follow_their_distributions():
     b2 = I.heat_batch(64, seed=0)
     assert [(w.J, w.N, w.eps) for w in b] == [(w.J, w.N, w.eps) for w in b2]
     assert len({w.seed for w in b}) == 64
+
+
+def test_fast_operator_and_macroscopic_on_host(L):
+    """Host-side validation of the fast operator's entry points and of sgs_macroscopic (no
+    device work is reached): hard spheres only, rule sizes, workspace growing with the chunk
+    of nodes, calls before binding refused."""
+    hs = sgs.Problem(nx=4, nv=16, v_max=8.0, collision=sgs.HARD_SPHERE, eps=0.1)
+    arr = (sgs._Problem * 1)(hs.c())
+    h, ws = C.c_void_p(), C.c_size_t()
+    assert L.sgs_setup(arr, 1, C.byref(h), C.byref(ws)) == sgs.OK
+    x, xb = C.c_void_p(), C.c_size_t()
+    assert L.sgs_fast_setup(h, 8, 16, 4, C.byref(x), C.byref(xb)) == sgs.OK and xb.value > 0
+    x8, xb8 = C.c_void_p(), C.c_size_t()
+    assert L.sgs_fast_setup(h, 8, 16, 8, C.byref(x8), C.byref(xb8)) == sgs.OK and xb8.value > xb.value
+    L.sgs_fast_destroy(x8)
+    dummy = C.c_void_p(256)
+    assert L.sgs_fast_collide(x, h, dummy, dummy, 3, None) == sgs.ERR_WORKSPACE  # nothing bound
+    assert L.sgs_fast_collide(x, h, dummy, dummy, 2, None) == sgs.ERR_ARG  # 1 or 3 products
+    assert L.sgs_fast_bind(x, C.c_void_p(256), 16) == sgs.ERR_WORKSPACE  # too small
+    L.sgs_fast_destroy(x)
+    for bad in ((0, 16, 4), (8, 0, 4), (8, 16, 0), (64, 65, 4)):
+        y = C.c_void_p()
+        assert L.sgs_fast_setup(h, *bad, C.byref(y), C.byref(xb)) == sgs.ERR_ARG, bad
+    assert L.sgs_macroscopic(h, dummy, dummy, None) == sgs.ERR_WORKSPACE
+    assert L.sgs_macroscopic(h, None, dummy, None) == sgs.ERR_ARG
+    L.sgs_destroy(h)
+    mx = (sgs._Problem * 1)(sgs.Problem(nx=4, nv=16).c())
+    assert L.sgs_setup(mx, 1, C.byref(h), C.byref(ws)) == sgs.OK
+    y = C.c_void_p()
+    assert L.sgs_fast_setup(h, 8, 16, 4, C.byref(y), C.byref(xb)) == sgs.ERR_UNSUPPORTED  # Maxwell molecules
+    L.sgs_destroy(h)
