@@ -567,7 +567,6 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   int buf = 0;
   unsigned long long c_inner = 0, c_newton = 0, c_solves = 0, c_fallback = 0;
   unsigned int status = 0;
-  bool have_th = false;
 
   const int s_end = min(a.s1, J);
   for (int s = a.s0; s < s_end; s++) {
@@ -624,14 +623,18 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       }
     }
 
-    // ---- M[g] of the stored value (warm start from the previous cell's M[g], whose
-    //      evaluation is still the last one)
+    // ---- M[g] of the stored value, from the collision step's Maxwellian of the same f (the
+    //      collision step that preceded this scan, or this group's, evaluated the stored
+    //      value: the Newton solve only confirms it); a stale start costs iterations, not
+    //      accuracy (the root is unique)
     {
-      int n0 = solve_mg<E>(sm, N, w, mom, have_th ? sm.thg : nullptr, have_th, L, ntol, I.newton_max, status);
+      double th0[5];
+#pragma unroll
+      for (int k = 0; k < 5; k++) th0[k] = a.theta[5 * (long long)(I.cell0 + j) + k];
+      int n0 = solve_mg<E>(sm, N, w, mom, th0, false, L, ntol, I.newton_max, status);
       if (n0 > 0) c_newton += n0;
       c_solves++;
     }
-    have_th = true;
 
     int it = 0;
     // decisions from the step-2 identity (double-float and FP64 scans) after the first update
