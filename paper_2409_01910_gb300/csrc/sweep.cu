@@ -176,6 +176,28 @@ __device__ inline void moments_from_sums(const E* S1, const E* S2, const E* S3, 
   for (int i = 0; i < 15; i++) Aa[i] = t[i];
 }
 
+// Moment k of the separable Maxwellian from its three 1-D sums, the same expression as
+// moments_from_sums gives for component k.
+template <typename E>
+__device__ inline E moment_k(const E* S1, const E* S2, const E* S3, int k) {
+  const E s23 = S2[0] * S3[0];
+  if (k == 0) return S1[0] * s23;
+  if (k == 1) return S1[1] * s23;
+  if (k == 2) return S1[0] * (S2[1] * S3[0]);
+  if (k == 3) return S1[0] * (S2[0] * S3[1]);
+  return S1[2] * s23 + S1[0] * (S2[2] * S3[0] + S2[0] * S3[2]);
+}
+
+// Component k of a five-element register array (static indices only).
+template <typename E>
+__device__ inline E pick5(const E (&v)[5], int k) {
+  E r = v[0];
+#pragma unroll
+  for (int q = 1; q < 5; q++)
+    if (k == q) r = v[q];
+  return r;
+}
+
 // Warp 0: residual F (E), Jacobian (FP32) and the scaled residual norm from the 1-D sums.
 // wmode 0: plain weights w; 1: w |v1|/dx; 2: w (|v1|/dx + |v2|/dy), a sum of two separable
 // terms.
@@ -575,6 +597,33 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     double* fj = a.f + cbase;
     const bool lw = j == 0, rw = j == J - 1;
 
+    // ---- r = (-v1^+ f_{j-1} + v1^- f_{j+1}) / dx - P_j / eps - b_j (neighbours: latest values);
+    //      a wall cell needs the wall density from reduction 1, every other cell forms r
+    //      before it, so that its loads and conversions overlap the reduction
+    auto form_r = [&](E rho_l, E rho_r) {
+      const double* Pj = a.P + cbase;
+      const double* bj = a.rhs ? a.rhs + cbase : nullptr;
+#pragma unroll
+      for (int t = 0; t < EPT; t++) {
+        E left = lw ? rho_l * wl12 * sm.W3[0][i30 + t] : cvt<E>(fj[t - K]);
+        E right = rw ? rho_r * wr12 * sm.W3[1][i30 + t] : cvt<E>(fj[t + K]);
+        E rv = vmd * right - vpd * left - cvt<E>(Pj[t]) * inv_eps;
+        if (bj) rv -= cvt<E>(bj[t]);
+        r[t] = rv;
+      }
+    };
+    const bool wall_cell = lw || rw;
+    if (own && !wall_cell) form_r(zero, zero);
+    // the cell's transport-plus-penalty coefficients (from its collision frequency), also
+    // ahead of the reduction (read after its barriers)
+    if (tid < N) {
+      const double Ad = a.nu[I.cell0 + j] / I.eps;
+      double c = fabs(node(tid, N, dv)) * inv_dx + Ad;
+      sm.c1A[tid] = cvt<E>(c);
+      sm.den[tid] = cvt<E>(1.0 / c);
+      if (tid == 0) sm.scal[2] = cvt<E>(Ad);
+    }
+
     // ---- reduction 1: moments of the stored value and the walls' outgoing fluxes
     E a0 = zero, a3 = zero, a4 = zero;
     if (own) {
@@ -594,34 +643,14 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     E mom[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) mom[k] = w * sm.red_tote[k];
-    if (tid < N) {
-      const double Ad = a.nu[I.cell0 + j] / I.eps;
-      double c = fabs(node(tid, N, dv)) * inv_dx + Ad;
-      sm.c1A[tid] = cvt<E>(c);
-      sm.den[tid] = cvt<E>(1.0 / c);
-      if (tid == 0) {
-        sm.scal[0] = cvt<E>(I.bc_kind[0] == SGS_INFLOW ? I.bc_rho[0] : -(wd * t7[5]) / I.wall_denom[0]);
-        sm.scal[1] = cvt<E>(I.bc_kind[1] == SGS_INFLOW ? I.bc_rho[1] : -(wd * t7[6]) / I.wall_denom[1]);
-        sm.scal[2] = cvt<E>(Ad);
-      }
+    if (tid == 0) {
+      sm.scal[0] = cvt<E>(I.bc_kind[0] == SGS_INFLOW ? I.bc_rho[0] : -(wd * t7[5]) / I.wall_denom[0]);
+      sm.scal[1] = cvt<E>(I.bc_kind[1] == SGS_INFLOW ? I.bc_rho[1] : -(wd * t7[6]) / I.wall_denom[1]);
     }
     __syncthreads();
     const E rho_l = sm.scal[0], rho_r = sm.scal[1], Acoef = sm.scal[2];
     const E c1A = sm.c1A[i1], den = sm.den[i1];
-
-    // ---- r = (-v1^+ f_{j-1} + v1^- f_{j+1}) / dx - P_j / eps - b_j (neighbours: latest values)
-    if (own) {
-      const double* Pj = a.P + cbase;
-      const double* bj = a.rhs ? a.rhs + cbase : nullptr;
-#pragma unroll
-      for (int t = 0; t < EPT; t++) {
-        E left = lw ? rho_l * wl12 * sm.W3[0][i30 + t] : cvt<E>(fj[t - K]);
-        E right = rw ? rho_r * wr12 * sm.W3[1][i30 + t] : cvt<E>(fj[t + K]);
-        E rv = vmd * right - vpd * left - cvt<E>(Pj[t]) * inv_eps;
-        if (bj) rv -= cvt<E>(bj[t]);
-        r[t] = rv;
-      }
-    }
+    if (own && wall_cell) form_r(rho_l, rho_r);
 
     // ---- M[g] of the stored value, from the collision step's Maxwellian of the same f (the
     //      collision step that preceded this scan, or this group's, evaluated the stored
@@ -758,33 +787,41 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       if (!lowp) {
         // ---- residual and step-1 target of the new iterate from the step-2 identity
         derived_sums<E>(sm);
-        if (tid == 0) {
-          E mw[5];
-          float Aa[15];
-          moments_from_sums<E>(sm.S1w, sm.S[1], sm.S[2], mw, Aa);  // sum phi (|v1|/dx) M[g]
-          const double Ad = tod(Acoef);
-          const double res = fabs(Ad) * sqrt(wd * tod(derived_norm2<E>(sm)));
-          bool stop;
-          if (I.inner_fixed > 0) {
-            stop = it >= I.inner_fixed;
-          } else {
-            stop = res < I.inner_tol || it >= I.inner_max;
-            if (stop && !(res < I.inner_tol)) status |= SGS_ST_INNER_CAP;
+        // warp 0 decides; its lanes form the five components of the step-1 target and the
+        // residual norm concurrently (a serial chain of double-float operations otherwise)
+        if (tid < 32) {
+          const int lane = tid;
+          E sk = zero;
+          if (lane < 5) {
+            const E mwk = moment_k<E>(sm.S1w, sm.S[1], sm.S[2], lane);  // sum phi (|v1|/dx) M[g]
+            sk = w * mwk - Acoef * pick5<E>(momP, lane) + Acoef * pick5<E>(mm, lane);
+            sm.svE[lane] = sk;
           }
-          if (!(res == res)) {
-            status |= SGS_ST_NONFINITE;
-            stop = true;
-          }
+          const double sdk = tod(sk);
+          double nrm = lane == 5 ? tod(derived_norm2<E>(sm)) : 0.0;
           double sd[5];
 #pragma unroll
-          for (int k = 0; k < 5; k++) {
-            E sk = w * mw[k] - Acoef * momP[k] + Acoef * mm[k];
-            sm.svE[k] = sk;
-            sd[k] = tod(sk);
+          for (int k = 0; k < 5; k++) sd[k] = __shfl_sync(0xffffffffu, sdk, k);
+          nrm = __shfl_sync(0xffffffffu, nrm, 5);
+          __syncwarp();  // the lanes' sm.svE before lane 0 may replace them (relaxed step 1)
+          if (lane == 0) {
+            const double Ad = tod(Acoef);
+            const double res = fabs(Ad) * sqrt(wd * nrm);
+            bool stop;
+            if (I.inner_fixed > 0) {
+              stop = it >= I.inner_fixed;
+            } else {
+              stop = res < I.inner_tol || it >= I.inner_max;
+              if (stop && !(res < I.inner_tol)) status |= SGS_ST_INNER_CAP;
+            }
+            if (!(res == res)) {
+              status |= SGS_ST_NONFINITE;
+              stop = true;
+            }
+            bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
+            if (pfp && !exists && relax) exists = relax_target<E>(sm, w, false, sd);
+            sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
           }
-          bool exists = pfp && sd[0] > 0.0 && sd[0] * sd[4] > sd[1] * sd[1] + sd[2] * sd[2] + sd[3] * sd[3];
-          if (pfp && !exists && relax) exists = relax_target<E>(sm, w, false, sd);
-          sm.ctl = (stop ? 1 : 0) | (exists ? 2 : 0);
         }
         __syncthreads();
 #pragma unroll
