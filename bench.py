@@ -957,7 +957,9 @@ def profile_case(which):
         # the fast spectral operator (hard spheres, tensor cores) on 64 cells of the shock's
         # 32^3 grid on [-10, 10]^3: one evaluation after a warm-up one
         J, N, L = 64, 32, 10.0
-        s = sgs.Solver(sgs.Problem(nx=J, nv=N, v_max=L, collision=sgs.HARD_SPHERE, eps=0.1))
+        # FP32 handle: its direct FP32 sum is the comparison (the fast operator ignores the
+        # handle's precision)
+        s = sgs.Solver(sgs.Problem(nx=J, nv=N, v_max=L, collision=sgs.HARD_SPHERE, eps=0.1, precision=sgs.FP32))
         fast = sgs.FastOperator(s, 8, 16, chunk=8)
         f = torch.from_numpy(I.initial_state(J, N, L, T=1.5).reshape(-1)).cuda()
         Q, P = s.field(), s.field()
