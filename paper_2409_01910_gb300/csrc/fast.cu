@@ -210,98 +210,144 @@ __device__ inline void store_pair(uint16_t* __restrict__ hi, uint16_t* __restric
   if (terms == 3) *reinterpret_cast<uint32_t*>(lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
 }
 
-// ---- pass 1 (k3 -> x3): rows (b, k1, k2), A = w_{s,a} fhat_c formed by the threads (both
-// rows contiguous in memory, every load issued before the first use), one product per tile
-// into TMEM; the epilogue writes the pass-2 operand Y1 (rows (b, x3, k1), K = (k2, re/im)).
+// Row of Y1 (the pass-2 operand) holding (b, x3, k1): per b, blocks of 4 k1 (k1 padded to
+// NP) by blocks of 8 x3, inside a block x3 major and k1 minor. A warp of pass 2 then holds 8
+// consecutive x3 by 4 consecutive k1 of one b, so that for each x2 its 32 stores of the
+// pass-3 operand fill one 128-byte core matrix (rows x3 .. x3 + 7, K entries of 4 k1):
+// whole sectors, coalesced.
+template <int NP, int P>
+__device__ inline long long y1_row(int b, int x3, int k1) {
+  return ((((long long)b * (NP / 4) + (k1 >> 2)) * (P / 8) + (x3 >> 3)) * 8 + (x3 & 7)) * 4 + (k1 & 3);
+}
+
+// ---- pass 1 (k3 -> x3): rows (b, k1, k2), A = w_{s,a} fhat_c formed by the threads from
+// two contiguous rows of L2-resident tables; the epilogue writes the pass-2 operand Y1 (rows
+// in y1_row order, K = (k2, re/im)). Software-pipelined: the loads of tile i + 1 are issued
+// into registers before the epilogue of tile i - 1, A is double-buffered in shared memory
+// and the accumulator in TMEM, so the loads' latency overlaps the epilogue and the MMAs.
 template <int NP, int PP>
 __global__ void __launch_bounds__(kTcRows) k_fast_pass1(FastArgs a) {
   extern __shared__ __align__(128) unsigned char smraw[];
   constexpr int K = 2 * NP, P = PP, np = NP, NB = 2 * P;
+  constexpr int TILE = kTcRows * K;
   const int n = a.n;
   uint16_t* Bhi = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Blo = Bhi + NB * K;
-  uint16_t* Ahi = Blo + NB * K;
-  uint16_t* Alo = Ahi + kTcRows * K;
-  __shared__ __align__(8) uint64_t bar;
+  uint16_t* Abuf = Blo + NB * K;  // [2 buffers][hi, lo][TILE]
+  __shared__ __align__(8) uint64_t bar_mma[2];
   __shared__ uint32_t tslot;
   const int t = threadIdx.x, warp = t >> 5;
-  if (warp == 0) tc::tmem_alloc(&tslot, 128);
+  if (warp == 0) tc::tmem_alloc(&tslot, 256);  // two accumulators of NB columns, 128 apart
   if (t == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar_mma[0], 1);
+    mbar_init(&bar_mma[1], 1);
     fence_mbar_init();
   }
   load_tile<K, NB>(a.bt12, NB, Bhi, Blo, 3);  // the DFT matrix, split once per CTA
-  const long long rows = (long long)a.C * a.S * 2 * n * np;
+  // rows (b, k1 < NP, k2): per b, blocks of 4 k1 by blocks of 8 k2, inside a block k2 major
+  // and k1 minor, so that for each x3 a warp's 32 epilogue stores fill two 64-byte runs of Y1
+  // (rows of 4 consecutive k1, 16 consecutive K entries); rows with k1 >= n are zero
+  const long long rows = (long long)a.C * a.S * 2 * NP * np;
   const long long tiles = (rows + kTcRows - 1) / kTcRows;
+  const int nt = tiles > blockIdx.x ? (int)((tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = tslot;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  uint32_t phase = 0;
-  int mma_next = 0, mma_wait = 0;
-  bool ok = true;
-  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const long long r = tile * kTcRows + t;  // this thread's row
-    const bool live = r < rows;
-    int b = 0, k1 = 0, k2 = 0;
-    if (live) {
-      b = (int)(r / (n * np));
-      const int rem = (int)(r % (n * np));
-      k1 = rem / np;
-      k2 = rem % np;
+  // this thread's row of tile i: (b, k1, k2); rows past the end read as zero
+  auto row_of = [&](int i, int& b, int& k1, int& k2) {
+    const long long r = (blockIdx.x + (long long)i * gridDim.x) * kTcRows + t;
+    b = k1 = k2 = 0;
+    if (r >= rows) return false;
+    b = (int)(r / (NP * np));
+    const int rem = (int)(r % (NP * np));  // ((k1 / 4) * (np / 8) + k2 / 8) * 32 + (k2 % 8) * 4 + k1 % 4
+    const int blk = rem >> 5, in = rem & 31;
+    k1 = (blk / (np / 8)) * 4 + (in & 3);
+    k2 = (blk % (np / 8)) * 8 + (in >> 2);
+    if (k1 >= n) {
+      b = k1 = k2 = 0;
+      return false;
     }
+    return true;
+  };
+  float4 fv[NP / 2], wv[NP / 4];
+  auto load_rows = [&](int i) {
+    int b, k1, k2;
+    const bool live = row_of(i, b, k1, k2);
     const int ab = b & 1, sl = (b >> 1) % a.S, c = (b >> 1) / a.S;
     const float4* fr = reinterpret_cast<const float4*>(a.fhat + (((long long)c * n + k1) * np + k2) * np * 2);
     const float4* wr =
         reinterpret_cast<const float4*>(a.wtab + ((((long long)(a.s0 + sl) * 2 + ab) * n + k1) * np + k2) * np);
-    float4 fv[NP / 2], wv[NP / 4];
 #pragma unroll
-    for (int i = 0; i < NP / 2; i++) fv[i] = live ? fr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < NP / 2; q++) fv[q] = live ? fr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int i = 0; i < NP / 4; i++) wv[i] = live ? wr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < NP / 4; q++) wv[q] = live ? wr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto epilogue = [&](int i) {
+    int b, k1, k2;
+    const bool live = row_of(i, b, k1, k2);
+    const uint32_t acc = taddr + lane_base + (uint32_t)((i & 1) * 128);
 #pragma unroll
-    for (int i = 0; i < NP / 2; i++) {  // K elements 4 i .. 4 i + 3: modes k3 = 2 i, 2 i + 1
-      const float4 w4 = wv[i / 2];
-      const float w0 = (i & 1) ? w4.z : w4.x, w1 = (i & 1) ? w4.w : w4.y;
-      put4(Ahi, Alo, t, 4 * i, K, make_float4(w0 * fv[i].x, w0 * fv[i].y, w1 * fv[i].z, w1 * fv[i].w), a.terms);
+    for (int c0 = 0; c0 < NB; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(acc + (uint32_t)c0, v);
+      if (live) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+          const int x3 = (c0 + q) >> 1;
+          store_pair(a.Y1h, a.Y1l, y1_row<NP, P>(b, x3, k1), 2 * k2, K, v[q], v[q + 1], a.terms);
+        }
+      }
+    }
+  };
+  int mma_next = 0, mma_wait = 0;
+  bool ok = true;
+  if (nt > 0) load_rows(0);
+  for (int i = 0; i < nt; i++) {
+    // A of tile i (its buffer was last read by MMA i - 2, waited for in iteration i - 1)
+    uint16_t* Ahi = Abuf + (size_t)(i & 1) * 2 * TILE;
+    uint16_t* Alo = Ahi + TILE;
+#pragma unroll
+    for (int q = 0; q < NP / 2; q++) {  // K elements 4 q .. 4 q + 3: modes k3 = 2 q, 2 q + 1
+      const float4 w4 = wv[q / 2];
+      const float w0 = (q & 1) ? w4.z : w4.x, w1 = (q & 1) ? w4.w : w4.y;
+      put4(Ahi, Alo, t, 4 * q, K, make_float4(w0 * fv[q].x, w0 * fv[q].y, w1 * fv[q].z, w1 * fv[q].w), a.terms);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (t == 0) {
-      issue_product(taddr, smem_addr(Ahi), smem_addr(Alo), smem_addr(Bhi), smem_addr(Blo), K, NB, a.terms);
-      tc::mma_commit(&bar);
+      issue_product(taddr + (uint32_t)((i & 1) * 128), smem_addr(Ahi), smem_addr(Alo), smem_addr(Bhi),
+                    smem_addr(Blo), K, NB, a.terms);
+      tc::mma_commit(&bar_mma[i & 1]);
     }
-    mma_next++;
-    ok = wait_uniform(&bar, phase, a.spin_max);
-    if (!ok) break;
-    mma_wait++;
-    phase ^= 1u;
-    // epilogue: (x3, re/im) of this thread's row into the pass-2 operand
-#pragma unroll
-    for (int c0 = 0; c0 < NB; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(taddr + lane_base + (uint32_t)c0, v);
-      if (live) {
-#pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          const int x3 = (c0 + i) >> 1;
-          store_pair(a.Y1h, a.Y1l, ((long long)b * P + x3) * n + k1, 2 * k2, K, v[i], v[i + 1], a.terms);
-        }
-      }
+    mma_next = i + 1;
+    if (i + 1 < nt) load_rows(i + 1);  // in flight during the epilogue below
+    if (i >= 1) {
+      ok = wait_uniform(&bar_mma[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1), a.spin_max);
+      if (!ok) break;
+      mma_wait = i;
+      epilogue(i - 1);
+      tc::fence_before_sync();
+      __syncthreads();
     }
-    tc::fence_before_sync();
-    __syncthreads();
+  }
+  if (ok && nt > 0) {
+    ok = wait_uniform(&bar_mma[(nt - 1) & 1], (uint32_t)(((nt - 1) >> 1) & 1), a.spin_max);
+    if (ok) {
+      mma_wait = nt;
+      epilogue(nt - 1);
+    }
   }
   if (!ok) {
     if (t == 0) atomicOr(a.status, SGS_ST_TIMEOUT);
-    for (int q = mma_wait; q < mma_next; q++) mbar_wait(&bar, phase, a.spin_max);
+    drain(bar_mma, mma_wait, mma_next, a.spin_max);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(taddr, 128);
+  if (warp == 0) tc::tmem_free(taddr, 256);
 }
 
 // ---- pass 2 (k2 -> x2): A tiles of Y1 (rows (b, x3, k1)) streamed by bulk copies into
@@ -313,7 +359,6 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass2(FastArgs a) {
   extern __shared__ __align__(128) unsigned char smraw[];
   constexpr int K = 2 * NP, P = PP, NB = 2 * P;
   constexpr int TILE = kTcRows * K;  // elements of one operand plane tile
-  const int n = a.n;
   uint16_t* Bhi = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Blo = Bhi + NB * K;
   uint16_t* Abuf = Blo + NB * K;  // [2 buffers][hi, lo][TILE]
@@ -329,7 +374,7 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass2(FastArgs a) {
     fence_mbar_init();
   }
   load_tile<K, NB>(a.bt12, NB, Bhi, Blo, 3);
-  const long long rows = (long long)a.C * a.S * 2 * P * n;
+  const long long rows = (long long)a.C * a.S * 2 * NP * P;  // rows (b, k1 < NP, x3) in y1_row order
   const long long tiles = (rows + kTcRows - 1) / kTcRows;
   const int nt = tiles > blockIdx.x ? (int)((tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;  // this CTA's tiles
   tc::fence_async_smem();
@@ -351,10 +396,11 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass2(FastArgs a) {
     const bool live = r < rows;
     int b = 0, x3 = 0, k1 = 0;
     if (live) {
-      b = (int)(r / (P * n));
-      const int rem = (int)(r % (P * n));
-      x3 = rem / n;
-      k1 = rem % n;
+      b = (int)(r / (NP * P));
+      const int rem = (int)(r % (NP * P));  // ((k1 / 4) * (P / 8) + x3 / 8) * 32 + (x3 % 8) * 4 + k1 % 4
+      const int blk = rem >> 5, in = rem & 31;
+      k1 = (blk / (P / 8)) * 4 + (in & 3);
+      x3 = (blk % (P / 8)) * 8 + (in >> 2);
     }
     const uint32_t acc = taddr + lane_base + (uint32_t)((i & 1) * 128);
 #pragma unroll
@@ -657,13 +703,13 @@ static cudaError_t launch_passes_t(int pass, const FastArgs& a, cudaStream_t st)
   int grid = 0;
   cudaError_t e;
   if (pass == 1) {
-    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * 2 * PP * K + (size_t)2 * TILE);
-    const long long tiles = (B * a.n * NP + kTcRows - 1) / kTcRows;
-    e = pass_grid((const void*)k_fast_pass1<NP, PP>, smem, 128, tiles, &grid);
+    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * 2 * PP * K + (size_t)2 * 2 * TILE);
+    const long long tiles = (B * NP * NP + kTcRows - 1) / kTcRows;
+    e = pass_grid((const void*)k_fast_pass1<NP, PP>, smem, 256, tiles, &grid);
     if (e == cudaSuccess) k_fast_pass1<NP, PP><<<grid, kTcRows, smem, st>>>(a);
   } else if (pass == 2) {
     constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * 2 * PP * K + (size_t)2 * 2 * TILE);
-    const long long tiles = (B * PP * a.n + kTcRows - 1) / kTcRows;
+    const long long tiles = (B * PP * NP + kTcRows - 1) / kTcRows;
     e = pass_grid((const void*)k_fast_pass2<NP, PP>, smem, 256, tiles, &grid);
     if (e == cudaSuccess) k_fast_pass2<NP, PP><<<grid, kTcRows, smem, st>>>(a);
   } else {

@@ -244,8 +244,8 @@ struct FastArgs {
   const float* bt12;            // [2P][2 npad]: passes 1 and 2
   const float* bt3;             // [P][2 npad]: pass 3 (real part)
   // the pass-2 and pass-3 operands as BF16 planes (hi; lo for 3 terms) of 128-row tiles in the
-  // K-major core-matrix layout (K = 2 npad): Y1 rows (b, x3, k1), K (k2, re/im); Y2 rows
-  // (b, x2, x3), K (k1, re/im); the last Y1 tile padded to 128 rows
+  // K-major core-matrix layout (K = 2 npad): Y1 rows (b, x3, k1 < npad) in blocks of 8 x3 by
+  // 4 k1 (the order of fast.cu's y1_row), K (k2, re/im); Y2 rows (b, x2, x3), K (k1, re/im)
   uint16_t* Y1h;
   uint16_t* Y1l;
   uint16_t* Y2h;

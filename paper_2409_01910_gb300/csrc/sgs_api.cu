@@ -1754,9 +1754,9 @@ int sgs_fast_setup(const sgs_handle* h, int m_theta, int m_phi, int chunk, sgs_f
   x->off.bt12 = take(sizeof(float) * x->bt12.size());
   x->off.bt3 = take(sizeof(float) * x->bt3.size());
   x->off.tw = take(sizeof(float2) * x->tw.size());
-  // BF16 operand planes of 128-row tiles (K = 2 np); Y1's last tile padded
+  // BF16 operand planes of 128-row tiles (K = 2 np); Y1 rows (b, k1 < np, x3), k1 padded
   const size_t tile = (size_t)128 * 2 * np;
-  const size_t y1_tiles = (Bc * P * n + 127) / 128, y2_tiles = Bc * P * P / 128;
+  const size_t y1_tiles = (Bc * P * np + 127) / 128, y2_tiles = Bc * P * P / 128;
   x->off.Y1h = take(sizeof(uint16_t) * y1_tiles * tile);
   x->off.Y1l = take(sizeof(uint16_t) * y1_tiles * tile);
   x->off.Y2h = take(sizeof(uint16_t) * y2_tiles * tile);
