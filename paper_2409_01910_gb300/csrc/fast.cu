@@ -308,11 +308,22 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass1(FastArgs a) {
     // A of tile i (its buffer was last read by MMA i - 2, waited for in iteration i - 1)
     uint16_t* Ahi = Abuf + (size_t)(i & 1) * 2 * TILE;
     uint16_t* Alo = Ahi + TILE;
+    // K elements 4 q .. 4 q + 3 hold modes k3 = 2 q, 2 q + 1. Lanes of one row position in the
+    // core matrices (t, t + 8, t + 16, t + 24) share shared-memory banks; the odd groups of 8
+    // lanes store the two halves of each 16-byte chunk in the other order (selected values and
+    // addresses, no branch), which halves the bank conflicts of these stores.
+    const bool swap = (t >> 3) & 1;
 #pragma unroll
-    for (int q = 0; q < NP / 2; q++) {  // K elements 4 q .. 4 q + 3: modes k3 = 2 q, 2 q + 1
-      const float4 w4 = wv[q / 2];
-      const float w0 = (q & 1) ? w4.z : w4.x, w1 = (q & 1) ? w4.w : w4.y;
-      put4(Ahi, Alo, t, 4 * q, K, make_float4(w0 * fv[q].x, w0 * fv[q].y, w1 * fv[q].z, w1 * fv[q].w), a.terms);
+    for (int q = 0; q < NP / 2; q += 2) {
+      float4 x[2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const float4 w4 = wv[(q + u) / 2];
+        const float w0 = u ? w4.z : w4.x, w1 = u ? w4.w : w4.y;
+        x[u] = make_float4(w0 * fv[q + u].x, w0 * fv[q + u].y, w1 * fv[q + u].z, w1 * fv[q + u].w);
+      }
+      put4(Ahi, Alo, t, 4 * (q + (swap ? 1 : 0)), K, swap ? x[1] : x[0], a.terms);
+      put4(Ahi, Alo, t, 4 * (q + (swap ? 0 : 1)), K, swap ? x[0] : x[1], a.terms);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
