@@ -225,15 +225,16 @@ __device__ inline long long y1_row(int b, int x3, int k1) {
 // in y1_row order, K = (k2, re/im)). Software-pipelined: the loads of tile i + 1 are issued
 // into registers before the epilogue of tile i - 1, A is double-buffered in shared memory
 // and the accumulator in TMEM, so the loads' latency overlaps the epilogue and the MMAs.
-template <int NP, int PP>
+template <int NP, int PP, int TERMS>
 __global__ void __launch_bounds__(kTcRows) k_fast_pass1(FastArgs a) {
+  constexpr int NPL = TERMS == 3 ? 2 : 1;  // BF16 planes of an operand (hi; lo for 3 products)
   extern __shared__ __align__(128) unsigned char smraw[];
   constexpr int K = 2 * NP, P = PP, np = NP, NB = 2 * P;
   constexpr int TILE = kTcRows * K;
   const int n = a.n;
   uint16_t* Bhi = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Blo = Bhi + NB * K;
-  uint16_t* Abuf = Blo + NB * K;  // [2 buffers][hi, lo][TILE]
+  uint16_t* Abuf = Blo + NB * K;  // [2 buffers][NPL planes][TILE]
   __shared__ __align__(8) uint64_t bar_mma[2];
   __shared__ uint32_t tslot;
   const int t = threadIdx.x, warp = t >> 5;
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass1(FastArgs a) {
 #pragma unroll
         for (int q = 0; q < 16; q += 2) {
           const int x3 = (c0 + q) >> 1;
-          store_pair(a.Y1h, a.Y1l, y1_row<NP, P>(b, x3, k1), 2 * k2, K, v[q], v[q + 1], a.terms);
+          store_pair(a.Y1h, a.Y1l, y1_row<NP, P>(b, x3, k1), 2 * k2, K, v[q], v[q + 1], TERMS);
         }
       }
     }
@@ -306,8 +307,8 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass1(FastArgs a) {
   if (nt > 0) load_rows(0);
   for (int i = 0; i < nt; i++) {
     // A of tile i (its buffer was last read by MMA i - 2, waited for in iteration i - 1)
-    uint16_t* Ahi = Abuf + (size_t)(i & 1) * 2 * TILE;
-    uint16_t* Alo = Ahi + TILE;
+    uint16_t* Ahi = Abuf + (size_t)(i & 1) * NPL * TILE;
+    uint16_t* Alo = Ahi + (NPL - 1) * TILE;
     // K elements 4 q .. 4 q + 3 hold modes k3 = 2 q, 2 q + 1. Lanes of one row position in the
     // core matrices (t, t + 8, t + 16, t + 24) share shared-memory banks; the odd groups of 8
     // lanes store the two halves of each 16-byte chunk in the other order (selected values and
@@ -322,8 +323,8 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass1(FastArgs a) {
         const float w0 = u ? w4.z : w4.x, w1 = u ? w4.w : w4.y;
         x[u] = make_float4(w0 * fv[q + u].x, w0 * fv[q + u].y, w1 * fv[q + u].z, w1 * fv[q + u].w);
       }
-      put4(Ahi, Alo, t, 4 * (q + (swap ? 1 : 0)), K, swap ? x[1] : x[0], a.terms);
-      put4(Ahi, Alo, t, 4 * (q + (swap ? 0 : 1)), K, swap ? x[0] : x[1], a.terms);
+      put4(Ahi, Alo, t, 4 * (q + (swap ? 1 : 0)), K, swap ? x[1] : x[0], TERMS);
+      put4(Ahi, Alo, t, 4 * (q + (swap ? 0 : 1)), K, swap ? x[0] : x[1], TERMS);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass1(FastArgs a) {
     tc::fence_after_sync();
     if (t == 0) {
       issue_product(taddr + (uint32_t)((i & 1) * 128), smem_addr(Ahi), smem_addr(Alo), smem_addr(Bhi),
-                    smem_addr(Blo), K, NB, a.terms);
+                    smem_addr(Blo), K, NB, TERMS);
       tc::mma_commit(&bar_mma[i & 1]);
     }
     mma_next = i + 1;
@@ -365,14 +366,15 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass1(FastArgs a) {
 // double-buffered operand buffers; two TMEM accumulators, so that the copy of tile i + 1 and
 // the MMAs of tile i run while the epilogue of tile i - 1 writes the pass-3 operand Y2 (rows
 // (b, x2, x3), K = (k1, re/im)).
-template <int NP, int PP>
+template <int NP, int PP, int TERMS>
 __global__ void __launch_bounds__(kTcRows) k_fast_pass2(FastArgs a) {
+  constexpr int NPL = TERMS == 3 ? 2 : 1;  // BF16 planes of an operand (hi; lo for 3 products)
   extern __shared__ __align__(128) unsigned char smraw[];
   constexpr int K = 2 * NP, P = PP, NB = 2 * P;
   constexpr int TILE = kTcRows * K;  // elements of one operand plane tile
   uint16_t* Bhi = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Blo = Bhi + NB * K;
-  uint16_t* Abuf = Blo + NB * K;  // [2 buffers][hi, lo][TILE]
+  uint16_t* Abuf = Blo + NB * K;  // [2 buffers][NPL planes][TILE]
   __shared__ __align__(8) uint64_t bar_ld[2], bar_mma[2];
   __shared__ uint32_t tslot;
   const int t = threadIdx.x, warp = t >> 5;
@@ -397,10 +399,10 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass2(FastArgs a) {
   const uint32_t plane_bytes = TILE * sizeof(uint16_t);
   auto issue_ld = [&](int i) {  // thread 0: the operand planes of this CTA's i-th tile
     const long long tile = blockIdx.x + (long long)i * gridDim.x;
-    uint16_t* dst = Abuf + (size_t)(i & 1) * 2 * TILE;
-    mbar_arrive_expect_tx(&bar_ld[i & 1], plane_bytes * (a.terms == 3 ? 2 : 1));
+    uint16_t* dst = Abuf + (size_t)(i & 1) * NPL * TILE;
+    mbar_arrive_expect_tx(&bar_ld[i & 1], plane_bytes * NPL);
     bulk_g2s(dst, a.Y1h + tile * TILE, plane_bytes, &bar_ld[i & 1]);
-    if (a.terms == 3) bulk_g2s(dst + TILE, a.Y1l + tile * TILE, plane_bytes, &bar_ld[i & 1]);
+    if (TERMS == 3) bulk_g2s(dst + TILE, a.Y1l + tile * TILE, plane_bytes, &bar_ld[i & 1]);
   };
   auto epilogue = [&](int i) {
     const long long r = (blockIdx.x + (long long)i * gridDim.x) * kTcRows + t;
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass2(FastArgs a) {
 #pragma unroll
         for (int q = 0; q < 16; q += 2) {
           const int x2 = (c0 + q) >> 1;
-          store_pair(a.Y2h, a.Y2l, ((long long)b * P + x2) * P + x3, 2 * k1, K, v[q], v[q + 1], a.terms);
+          store_pair(a.Y2h, a.Y2l, ((long long)b * P + x2) * P + x3, 2 * k1, K, v[q], v[q + 1], TERMS);
         }
       }
     }
@@ -437,9 +439,9 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass2(FastArgs a) {
     if (!ok) break;
     ld_wait = i + 1;
     if (t == 0) {
-      uint16_t* A = Abuf + (size_t)(i & 1) * 2 * TILE;
-      issue_product(taddr + (uint32_t)((i & 1) * 128), smem_addr(A), smem_addr(A + TILE), smem_addr(Bhi),
-                    smem_addr(Blo), K, NB, a.terms);
+      uint16_t* A = Abuf + (size_t)(i & 1) * NPL * TILE;
+      issue_product(taddr + (uint32_t)((i & 1) * 128), smem_addr(A), smem_addr(A + (NPL - 1) * TILE), smem_addr(Bhi),
+                    smem_addr(Blo), K, NB, TERMS);
       tc::mma_commit(&bar_mma[i & 1]);
     }
     mma_next = i + 1;
@@ -479,15 +481,16 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass2(FastArgs a) {
 // double-buffered operand buffers; its two products (real part of the transform) go to a
 // TMEM accumulator pair, double-buffered like pass 2; the epilogue multiplies the two sides,
 // weights the slot and sums the slots of the tile in registers, then adds the sum to G.
-template <int NP, int PP>
+template <int NP, int PP, int TERMS>
 __global__ void __launch_bounds__(kTcRows) k_fast_pass3(FastArgs a) {
+  constexpr int NPL = TERMS == 3 ? 2 : 1;  // BF16 planes of an operand (hi; lo for 3 products)
   extern __shared__ __align__(128) unsigned char smraw[];
   constexpr int K = 2 * NP, P = PP, NB = P;
   constexpr int TILE = kTcRows * K;
   constexpr int TPC = P * P / kTcRows;  // tiles per cell (P^2 is a multiple of 128)
   uint16_t* Bhi = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Blo = Bhi + NB * K;
-  uint16_t* Abuf = Blo + NB * K;  // [2 buffers][side 2][hi, lo][TILE]
+  uint16_t* Abuf = Blo + NB * K;  // [2 buffers][side 2][NPL planes][TILE]
   __shared__ __align__(8) uint64_t bar_ld[2], bar_mma[2];
   __shared__ uint32_t tslot;
   const int t = threadIdx.x, warp = t >> 5;
@@ -515,12 +518,12 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass3(FastArgs a) {
     const long long tile = blockIdx.x + (long long)(u / S) * gridDim.x;
     const int s = u % S;
     const long long c = tile / TPC, tin = tile % TPC;
-    uint16_t* dst = Abuf + (size_t)(u & 1) * 4 * TILE;
-    mbar_arrive_expect_tx(&bar_ld[u & 1], plane_bytes * (a.terms == 3 ? 4 : 2));
+    uint16_t* dst = Abuf + (size_t)(u & 1) * 2 * NPL * TILE;
+    mbar_arrive_expect_tx(&bar_ld[u & 1], plane_bytes * 2 * NPL);
     for (int ab = 0; ab < 2; ab++) {
       const long long src = ((c * S + s) * 2 + ab) * TPC + tin;  // tile of b = (c, s, ab)
-      bulk_g2s(dst + (size_t)ab * 2 * TILE, a.Y2h + src * TILE, plane_bytes, &bar_ld[u & 1]);
-      if (a.terms == 3) bulk_g2s(dst + (size_t)ab * 2 * TILE + TILE, a.Y2l + src * TILE, plane_bytes, &bar_ld[u & 1]);
+      bulk_g2s(dst + (size_t)ab * NPL * TILE, a.Y2h + src * TILE, plane_bytes, &bar_ld[u & 1]);
+      if (TERMS == 3) bulk_g2s(dst + (size_t)ab * NPL * TILE + TILE, a.Y2l + src * TILE, plane_bytes, &bar_ld[u & 1]);
     }
   };
   float g[P];
@@ -564,10 +567,11 @@ __global__ void __launch_bounds__(kTcRows) k_fast_pass3(FastArgs a) {
     if (!ok) break;
     ld_wait = u + 1;
     if (t == 0) {
-      uint16_t* A = Abuf + (size_t)(u & 1) * 4 * TILE;
+      uint16_t* A = Abuf + (size_t)(u & 1) * 2 * NPL * TILE;
       for (int ab = 0; ab < 2; ab++)
-        issue_product(taddr + (uint32_t)((u & 1) * 128 + ab * P), smem_addr(A + (size_t)ab * 2 * TILE),
-                      smem_addr(A + (size_t)ab * 2 * TILE + TILE), smem_addr(Bhi), smem_addr(Blo), K, NB, a.terms);
+        issue_product(taddr + (uint32_t)((u & 1) * 128 + ab * P), smem_addr(A + (size_t)ab * NPL * TILE),
+                      smem_addr(A + (size_t)ab * NPL * TILE + (NPL - 1) * TILE), smem_addr(Bhi), smem_addr(Blo), K,
+                      NB, TERMS);
       tc::mma_commit(&bar_mma[u & 1]);
     }
     mma_next = u + 1;
@@ -707,30 +711,36 @@ static cudaError_t pass_grid(const void* kern, size_t smem, int tmem_cols, long 
   return cudaSuccess;
 }
 
-template <int NP, int PP>
+template <int NP, int PP, int TERMS>
 static cudaError_t launch_passes_t(int pass, const FastArgs& a, cudaStream_t st) {
   constexpr int K = 2 * NP, TILE = kTcRows * K;
+  constexpr int NPL = TERMS == 3 ? 2 : 1;  // operand planes: 1 product needs no lo buffers
   const long long B = (long long)a.C * a.S * 2;
   int grid = 0;
   cudaError_t e;
   if (pass == 1) {
-    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * 2 * PP * K + (size_t)2 * 2 * TILE);
+    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * 2 * PP * K + (size_t)2 * NPL * TILE);
     const long long tiles = (B * NP * NP + kTcRows - 1) / kTcRows;
-    e = pass_grid((const void*)k_fast_pass1<NP, PP>, smem, 256, tiles, &grid);
-    if (e == cudaSuccess) k_fast_pass1<NP, PP><<<grid, kTcRows, smem, st>>>(a);
+    e = pass_grid((const void*)k_fast_pass1<NP, PP, TERMS>, smem, 256, tiles, &grid);
+    if (e == cudaSuccess) k_fast_pass1<NP, PP, TERMS><<<grid, kTcRows, smem, st>>>(a);
   } else if (pass == 2) {
-    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * 2 * PP * K + (size_t)2 * 2 * TILE);
+    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * 2 * PP * K + (size_t)2 * NPL * TILE);
     const long long tiles = (B * PP * NP + kTcRows - 1) / kTcRows;
-    e = pass_grid((const void*)k_fast_pass2<NP, PP>, smem, 256, tiles, &grid);
-    if (e == cudaSuccess) k_fast_pass2<NP, PP><<<grid, kTcRows, smem, st>>>(a);
+    e = pass_grid((const void*)k_fast_pass2<NP, PP, TERMS>, smem, 256, tiles, &grid);
+    if (e == cudaSuccess) k_fast_pass2<NP, PP, TERMS><<<grid, kTcRows, smem, st>>>(a);
   } else {
-    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * PP * K + (size_t)2 * 4 * TILE);
+    constexpr size_t smem = sizeof(uint16_t) * ((size_t)2 * PP * K + (size_t)2 * 2 * NPL * TILE);
     const long long tiles = (long long)a.C * PP * PP / kTcRows;
-    e = pass_grid((const void*)k_fast_pass3<NP, PP>, smem, 256, tiles, &grid);
-    if (e == cudaSuccess) k_fast_pass3<NP, PP><<<grid, kTcRows, smem, st>>>(a);
+    e = pass_grid((const void*)k_fast_pass3<NP, PP, TERMS>, smem, 256, tiles, &grid);
+    if (e == cudaSuccess) k_fast_pass3<NP, PP, TERMS><<<grid, kTcRows, smem, st>>>(a);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+template <int NP, int PP>
+static cudaError_t launch_passes_t(int pass, const FastArgs& a, cudaStream_t st) {
+  return a.terms == 3 ? launch_passes_t<NP, PP, 3>(pass, a, st) : launch_passes_t<NP, PP, 1>(pass, a, st);
 }
 
 cudaError_t launch_fast_pass(int pass, const FastArgs& a, cudaStream_t st) {
