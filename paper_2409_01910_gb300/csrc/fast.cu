@@ -118,12 +118,15 @@ __global__ void __launch_bounds__(kTcRows) k_tc_selftest(const float* __restrict
 // X_{s,a} = w_{s,a} fhat_c (a = 0, 1) are transformed to a zero-padded P^3 grid by three
 // separable passes, each a GEMM on the tensor cores against the DFT matrix
 // E[x, k] = exp(2 pi i x (k - h) / P) written as a real 2 x 2 block matrix:
-//   pass 1 (k3 -> x3): rows (b, k1, k2), K = (k3, re/im), out (x3, re/im) -> Y1[b][x3][k1][k2]
-//   pass 2 (k2 -> x2): rows (b, x3, k1), K = (k2, re/im), out (x2, re/im) -> Y2[b][x2][x3][k1]
+//   pass 1 (k3 -> x3): rows (b, k1, k2), K = (k3, re/im), out (x3, re/im) -> Y1 rows (b, x3, k1)
+//   pass 2 (k2 -> x2): rows (b, x3, k1), K = (k2, re/im), out (x2, re/im) -> Y2 rows (b, x2, x3)
 //   pass 3 (k1 -> x1): rows (c, x2, x3), K = (k1, re/im), out x1 (real part) for a = 0 and
 //     a = 1, multiplied and summed over the slots with their weights into G[c][x2][x3][x1]
-// b = (c, s, a). Operands are FP32 in memory, split into BF16 hi + lo on the way into shared
-// memory (terms 3: hi hi + lo hi + hi lo; terms 1: hi hi), accumulated in FP32 in TMEM.
+// b = (c, s, a). Pass 1 forms its operand from the FP32 spectra and weights and splits it into
+// BF16 hi + lo (terms 3: products hi hi + lo hi + hi lo; terms 1: hi hi), accumulated in FP32
+// in TMEM; the pass-2 and pass-3 operands (Y1, Y2) are stored by the previous pass's epilogue
+// as BF16 planes already in the shared-memory layout of the tensor core and streamed by bulk
+// copies; the DFT matrices are split once per CTA.
 // ---------------------------------------------------------------------------------------
 
 // Four consecutive values (k % 4 == 0) of one row: one 8-byte shared store per BF16 tile.
